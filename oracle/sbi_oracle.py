@@ -1,0 +1,343 @@
+"""Plain FP64 CPU oracle of the enhanced spectral boundary integral (ESBI) hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this module:
+only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference
+legs of ``bench.py`` use it.  It shares no code with the CUDA library.
+
+What it computes (Wang, "An enhanced spectral boundary integral method for
+modeling highly nonlinear water waves in variable depth", arXiv 2310.19840):
+
+* ``vertical_velocity``: the surface vertical velocity V = sqrt(1+|grad eta|^2)
+  dphi/dn (definition under Eq. (prognostic), Sec. 2.2) from the surface
+  elevation eta, the surface potential phi~ and the bottom variation delta, by the
+  successive approximation of Sec. 2.4: V = sum_{l=1..M} V_l (Eq. app-V) with
+  the bottom potential varphi~ = sum_{l=1..M-1} varphi_l (Eq. app-phi).  The
+  order-l terms are taken from the explicit forms of Appendix C (Eqs. v2..v7),
+  written with the index pattern of the general recursion (Eqs. app-V-scs,
+  app-phi-scs) where the two agree; where they disagree the appendix is followed
+  (readings R1-R3 below).
+* ``surface_rhs``: the kinematic and dynamic free-surface conditions in the
+  Zakharov form of Eq. (prognostic): eta_t = V and
+  phi~_t = -g eta + 1/2 [(V + grad eta . grad phi~)^2 / (1+|grad eta|^2) - |grad phi~|^2] - p_d,
+  with the optional damping pressure p_d of Eq. (pd).
+* ``rk4_step``: classical fourth-order Runge-Kutta with a fixed step on the
+  physical-space pair (eta, phi~) (the paper's Sec. 2.2 uses an integrating-factor
+  RK5(4); this oracle follows the fixed-step RK4 workload definition).
+* ``invariants``: mass int eta dA and total energy E = 1/2 int (V phi~ + g eta^2) dA
+  (Eq. energy, written dimensionally).
+
+Readings of passages where the paper is silent, ambiguous or inconsistent:
+
+R1  F{V_l}: the general recursion puts tanh(kh) on the grad-phi~ term for every
+    l, Appendix C has it only for odd l (V2 and V4 carry none).  Appendix C is
+    followed: the factor is T_l = tanh(kh) for odd l, 1 for even l.
+R2  F{varphi_l}: the general recursion omits the eta^{l-1} grad phi~ term and
+    gives every delta^j term a minus sign; Appendix C has -sech(kh) k^{l-3}/(l-1)!
+    ik.F{eta^{l-1} grad phi~} for odd l and a sign (-1)^j on the delta^j terms.
+    Appendix C is followed.
+R3  <j/2> is the remainder of j divided by 2, so tanh^{<j/2>} is tanh for odd j
+    and 1 for even j, and <j/2> sech is sech for odd j and 0 for even j.
+R4  k = 0: every multiplier that carries ik or a positive power of k vanishes
+    there; k^{-1} tanh(kh) ik also vanishes (its limit is h ik -> 0).  Hence
+    F{V_l}(0) = 0 and the mean of eta is conserved exactly.
+R5  Dealiasing ("2/(l+1)-rule", Sec. 2.4): a rectangular mask that keeps the
+    Fourier modes with |m| < alpha nx/2 and |n| < alpha ny/2 (strict, after the
+    submerged-bar section's "waves longer than 4 grid cells are alias free"),
+    alpha = 0.5 by default.  The mask is applied to F{phi~}, to every order
+    F{V_l}, F{varphi_l}, to the dynamic-condition right-hand side and to the
+    state after each full step.  The Nyquist modes are always removed.
+R6  Reference depth h0 is an explicit input, delta = h0 - h(x, y).  sech(kh0) is
+    evaluated as 2 e^{-kh0} / (1 + e^{-2kh0}); h0 = inf gives deep water.
+R7  Damping pressure (Eq. pd): p_d = nu F^{-1}{ ik/(-k^2) . F{w grad phi~} },
+    zero at k = 0, with a user weight w(x, y) and strength nu [1/s].  It enters
+    the dynamic condition with a minus sign (a surface pressure).
+R8  Low-pass filter (Eq. filter): Lambda = exp(-|k/(beta1 k_ref)|^beta2), applied
+    to the spectra of eta and phi~ after each full step when beta1 > 0.
+R9  Order truncation: the scheme is explicit with a fixed maximum order M <= 7.
+    An optional tolerance stops at the first l whose increment satisfies
+    ||F{V_l}||_2 <= tol ||sum_{m<=l} F{V_m}||_2.
+
+Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
+has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
+components [x] (1-D) or [x, y] (2-D).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+MAX_ORDER = 7
+
+
+@dataclass(frozen=True)
+class Grid:
+    nx: int
+    ny: int
+    Lx: float
+    Ly: float = 1.0
+
+    @property
+    def dim(self) -> int:
+        return 1 if self.ny == 1 else 2
+
+    @property
+    def dA(self) -> float:
+        return (self.Lx / self.nx) * (self.Ly / self.ny)
+
+
+# --------------------------------------------------------------------------
+# Spectral primitives (Sec. 2.2: F{.} is evaluated by the FFT)
+# --------------------------------------------------------------------------
+
+def fft(f):
+    return np.fft.fft2(f)
+
+
+def ifft(F):
+    return np.real(np.fft.ifft2(F))
+
+
+def wavenumbers(grid: Grid):
+    """Angular wavenumbers (kx, ky) on the full FFT grid and |k|."""
+    kx = 2.0 * np.pi * np.fft.fftfreq(grid.nx, d=grid.Lx / grid.nx)
+    if grid.ny == 1:
+        ky = np.zeros(1)
+    else:
+        ky = 2.0 * np.pi * np.fft.fftfreq(grid.ny, d=grid.Ly / grid.ny)
+    KX, KY = np.meshgrid(kx, ky)
+    return KX, KY, np.sqrt(KX * KX + KY * KY)
+
+
+def dealias_mask(grid: Grid, alpha: float = 0.5):
+    """Reading R5: keep |m| < alpha nx/2 and |n| < alpha ny/2 (Nyquist always off)."""
+    m = np.abs(np.fft.fftfreq(grid.nx, d=1.0 / grid.nx))
+    keep_x = (m < alpha * grid.nx / 2) & (m < grid.nx / 2)
+    if grid.ny == 1:
+        keep_y = np.ones(1, dtype=bool)
+    else:
+        n = np.abs(np.fft.fftfreq(grid.ny, d=1.0 / grid.ny))
+        keep_y = (n < alpha * grid.ny / 2) & (n < grid.ny / 2)
+    return (keep_y[:, None] & keep_x[None, :]).astype(np.float64)
+
+
+def depth_multipliers(K, h0: float):
+    """tanh(k h0) and sech(k h0) (reading R6; h0 = inf -> deep water)."""
+    with np.errstate(invalid="ignore", over="ignore"):
+        kh = np.where(K > 0, K * h0, 0.0)
+    e = np.exp(-kh)
+    t = np.tanh(kh)
+    s = 2.0 * e / (1.0 + e * e)
+    return t, s
+
+
+def gradient(f_hat, KX, KY, dim):
+    """grad f = F^{-1}{ik f^} (component list)."""
+    comps = [ifft(1j * KX * f_hat)]
+    if dim == 2:
+        comps.append(ifft(1j * KY * f_hat))
+    return comps
+
+
+def ik_dot(vec, KX, KY):
+    """ik . F{vec} = i kx F{vec_x} + i ky F{vec_y}."""
+    out = 1j * KX * fft(vec[0])
+    if len(vec) == 2:
+        out = out + 1j * KY * fft(vec[1])
+    return out
+
+
+# --------------------------------------------------------------------------
+# Diagnostic: successive approximation of V (Sec. 2.4, Appendix C)
+# --------------------------------------------------------------------------
+
+def vertical_velocity(eta, phi, delta, h0, grid: Grid, order: int = MAX_ORDER,
+                      alpha: float = 0.5, tol: float = 0.0, return_terms: bool = False):
+    """V from (eta, phi~, delta) by the successive approximation of Sec. 2.4.
+
+    delta may be None (flat bottom: every delta term drops out).  With
+    ``return_terms`` the per-order lists [V_1..V_M] and [varphi_1..varphi_{M-1}]
+    (physical space) and the number of orders used are returned as well.
+    """
+    if not 1 <= order <= MAX_ORDER:
+        raise ValueError("order must be in 1..7")
+    eta = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)
+    flat = delta is None or not np.any(delta)
+    if not flat:
+        delta = np.asarray(delta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    t, s = depth_multipliers(K, h0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k_inv_t = np.where(K > 0, t / np.where(K > 0, K, 1.0), 0.0)   # R4
+    dim = grid.dim
+
+    def T(j):  # R3
+        return t if j % 2 == 1 else 1.0
+
+    def S(j):  # R3
+        return s if j % 2 == 1 else 0.0
+
+    def kpow(p):  # k^p for p >= 0
+        return K ** p if p > 0 else np.ones_like(K)
+
+    phi_hat = mask * fft(phi)
+    grad_phi_s = gradient(phi_hat, KX, KY, dim)            # grad phi~
+
+    # Order 1 (Sec. 2.4): F{V_1} = k tanh(kh) F{phi~}, F{varphi_1} = sech(kh) F{phi~}
+    V_hat = [None, K * t * phi_hat]
+    V = [None, ifft(V_hat[1])]
+    grad_b = [None]
+    if not flat:
+        b_hat1 = s * phi_hat
+        grad_b.append(gradient(b_hat1, KX, KY, dim))
+        b_phys = [None, ifft(b_hat1)]
+    total_hat = V_hat[1].copy()
+    used = 1
+    for l in range(2, order + 1):
+        # F{V_l}: Eq. app-V-scs with Appendix C's T_l on the grad phi~ term (R1)
+        acc = np.zeros_like(phi_hat)
+        for j in range(1, l):
+            acc -= kpow(j) / math.factorial(j) * T(j) * fft(eta ** j * V[l - j])
+        prod = [eta ** (l - 1) * g for g in grad_phi_s]
+        acc -= T(l) * kpow(l - 2) / math.factorial(l - 1) * ik_dot(prod, KX, KY)
+        if not flat:
+            for j in range(1, l, 2):   # S_j = 0 for even j
+                prod = [delta ** j * g for g in grad_b[l - j]]
+                acc += kpow(j - 1) / math.factorial(j) * s * ik_dot(prod, KX, KY)
+        V_hat.append(mask * acc)
+        V.append(ifft(V_hat[l]))
+        # F{varphi_l}: Appendix C (R2); needed for l <= order-1 only
+        if not flat and l <= order - 1:
+            bcc = np.zeros_like(phi_hat)
+            for j in range(1, l, 2):
+                bcc -= kpow(j - 1) / math.factorial(j) * s * fft(eta ** j * V[l - j])
+            if l % 2 == 1:
+                prod = [eta ** (l - 1) * g for g in grad_phi_s]
+                bcc -= s * kpow(l - 3) / math.factorial(l - 1) * ik_dot(prod, KX, KY)
+            for j in range(1, l):
+                prod = [delta ** j * g for g in grad_b[l - j]]
+                if j == 1:
+                    coef = -k_inv_t                     # (-1)^1 k^{-1} tanh / 1!
+                elif j % 2 == 1:
+                    coef = -kpow(j - 2) / math.factorial(j) * t
+                else:
+                    coef = kpow(j - 2) / math.factorial(j)
+                bcc += coef * ik_dot(prod, KX, KY)
+            b_hat = mask * bcc
+            grad_b.append(gradient(b_hat, KX, KY, dim))
+            b_phys.append(ifft(b_hat))
+        total_hat = total_hat + V_hat[l]
+        used = l
+        if tol > 0.0:
+            inc = np.sqrt(np.sum(np.abs(V_hat[l]) ** 2))
+            tot = np.sqrt(np.sum(np.abs(total_hat) ** 2))
+            if inc <= tol * tot:
+                break
+    Vsum = ifft(total_hat)
+    if return_terms:
+        terms = {"V": V[1:used + 1], "used": used}
+        if not flat:
+            terms["varphi"] = b_phys[1:]
+        return Vsum, terms
+    return Vsum
+
+
+# --------------------------------------------------------------------------
+# Prognostic right-hand side (Sec. 2.2) and damping pressure (Eq. pd)
+# --------------------------------------------------------------------------
+
+def damping_pressure(phi, weight, nu, grid: Grid, alpha: float = 0.5):
+    """R7: p_d = nu F^{-1}{ mask ik/(-k^2) . F{w grad phi~} }."""
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    phi_hat = mask * fft(np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx))
+    w = np.asarray(weight, dtype=np.float64).reshape(grid.ny, grid.nx)
+    prod = [w * g for g in gradient(phi_hat, KX, KY, grid.dim)]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(K > 0, -1.0 / np.where(K > 0, K * K, 1.0), 0.0)
+    return nu * ifft(mask * inv * ik_dot(prod, KX, KY))
+
+
+def dynamic_rhs(eta, phi, V, gravity, grid: Grid, alpha: float = 0.5):
+    """phi~_t without the damping pressure: the second line of Eq. (prognostic)
+    written in physical space, -g eta + 1/2[(V + grad eta.grad phi~)^2/(1+|grad eta|^2)
+    - |grad phi~|^2], dealiased (R5)."""
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    eta = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)
+    ge = gradient(mask * fft(eta), KX, KY, grid.dim)
+    gp = gradient(mask * fft(phi), KX, KY, grid.dim)
+    dot = sum(a * b for a, b in zip(ge, gp))
+    ge2 = sum(a * a for a in ge)
+    gp2 = sum(a * a for a in gp)
+    n2 = -gravity * eta + 0.5 * ((V + dot) ** 2 / (1.0 + ge2) - gp2)
+    return ifft(mask * fft(n2))
+
+
+@dataclass
+class Problem:
+    grid: Grid
+    gravity: float
+    h0: float
+    delta: np.ndarray | None = None
+    order: int = MAX_ORDER
+    alpha: float = 0.5
+    sponge_w: np.ndarray | None = None
+    sponge_nu: float = 0.0
+    filt_beta1: float = 0.0
+    filt_beta2: float = 0.0
+    k_ref: float = 1.0
+
+
+def surface_rhs(pb: Problem, eta, phi):
+    """(eta_t, phi~_t) of Eq. (prognostic) in physical space."""
+    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha)
+    phi_t = dynamic_rhs(eta, phi, V, pb.gravity, pb.grid, pb.alpha)
+    if pb.sponge_w is not None and pb.sponge_nu != 0.0:
+        phi_t = phi_t - damping_pressure(phi, pb.sponge_w, pb.sponge_nu, pb.grid, pb.alpha)
+    return V, phi_t
+
+
+def project(pb: Problem, f):
+    """Dealias (R5) and, when enabled, low-pass filter (R8) a state field."""
+    KX, KY, K = wavenumbers(pb.grid)
+    m = dealias_mask(pb.grid, pb.alpha)
+    if pb.filt_beta1 > 0.0:
+        m = m * np.exp(-np.abs(K / (pb.filt_beta1 * pb.k_ref)) ** pb.filt_beta2)
+    return ifft(m * fft(np.asarray(f, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)))
+
+
+def rk4_step(f, y, dt):
+    """Classical RK4 for y' = f(y); y is a tuple of arrays."""
+    def axpy(a, x, b):
+        return tuple(xi + a * bi for xi, bi in zip(x, b))
+    k1 = f(y)
+    k2 = f(axpy(0.5 * dt, y, k1))
+    k3 = f(axpy(0.5 * dt, y, k2))
+    k4 = f(axpy(dt, y, k3))
+    return tuple(yi + dt / 6.0 * (a + 2.0 * b + 2.0 * c + d)
+                 for yi, a, b, c, d in zip(y, k1, k2, k3, k4))
+
+
+def step(pb: Problem, eta, phi, dt: float, n: int = 1):
+    """n RK4 steps of (eta, phi~), each followed by the projection of R5/R8."""
+    y = (np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx),
+         np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx))
+    for _ in range(n):
+        y = rk4_step(lambda s: surface_rhs(pb, s[0], s[1]), y, dt)
+        y = (project(pb, y[0]), project(pb, y[1]))
+    return y
+
+
+def invariants(pb: Problem, eta, phi):
+    """Mass int eta dA and energy 1/2 int (V phi~ + g eta^2) dA (Eq. energy)."""
+    eta = np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
+    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha)
+    mass = float(np.sum(eta) * pb.grid.dA)
+    energy = float(0.5 * np.sum(V * phi + pb.gravity * eta * eta) * pb.grid.dA)
+    return mass, energy

@@ -1,0 +1,302 @@
+"""Pins of the FP64 oracle against results fixed by the paper and by mathematics
+(no GPU).  Each test names the property and the passage it comes from.
+
+Plausible mistakes and the pin that catches them:
+* a wrong coefficient, sign, power of k, tanh/sech factor or (-1)^j in any
+  order of V_l or varphi_l  -> constant-(eta, delta) Taylor pin (per order).
+* a misplaced product (F{eta^j} F{V} instead of F{eta^j V}), a gradient on the
+  wrong factor, a transposed kx/ky  -> Laplace-solver convergence pin (1-D) and
+  the oblique 2-D embedding pin.
+* a wrong term in the dynamic condition  -> Bernoulli pin.
+* a wrong RK4 weight  -> linear amplification-factor pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sbi_oracle as O
+from laplace_dtn import exact_vertical_velocity
+import workloads as W
+
+
+def _dft2(f):
+    ny, nx = f.shape
+    m = np.arange(nx)
+    n = np.arange(ny)
+    Ex = np.exp(-2j * np.pi * np.outer(m, m) / nx)
+    Ey = np.exp(-2j * np.pi * np.outer(n, n) / ny)
+    return Ey @ f @ Ex.T
+
+
+def test_fft_matches_brute_force_dft():
+    rng = np.random.default_rng(1)
+    for shape in ((8, 16), (1, 32), (4, 8)):
+        f = rng.standard_normal(shape)
+        F = O.fft(f)
+        D = _dft2(f)
+        assert np.max(np.abs(F - D)) <= 1e-13 * np.max(np.abs(D)) * shape[0] * shape[1]
+        assert np.max(np.abs(O.ifft(F) - f)) < 1e-14
+
+
+def test_dealias_mask_reading():
+    # Reading R5: strict |m| < alpha n/2.  64 points keep m = 0..15 (16 modes on
+    # each side), as in the paper's "first 16 Fourier modes" of 64 points.
+    g = O.Grid(64, 1, 1.0)
+    mk = O.dealias_mask(g, 0.5)[0]
+    kept = np.nonzero(mk)[0]
+    m = np.fft.fftfreq(64, d=1.0 / 64)[kept]
+    assert set(np.abs(m).astype(int)) == set(range(16))
+    # alpha = 1 removes only the Nyquist mode
+    assert O.dealias_mask(g, 1.0).sum() == 63
+    g2 = O.Grid(16, 8, 1.0, 1.0)
+    assert O.dealias_mask(g2, 0.5).sum() == 7 * 3
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("h0", [0.3, 1.0, np.inf])
+def test_linear_operator_closed_form(dim, h0):
+    # eta = 0, delta = 0: V = F^{-1}{k tanh(kh) F{phi~}} (Sec. 2.4, order 1).
+    nx, ny = 32, (1 if dim == 1 else 16)
+    g = O.Grid(nx, ny, 5.0, 3.0 if dim == 2 else 1.0)
+    phi = W.random_field(nx, ny, seed=3, band=0.5)
+    V = O.vertical_velocity(np.zeros((ny, nx)), phi, None, h0, g)
+    KX, KY, K = O.wavenumbers(g)
+    mult = K * (np.tanh(K * h0) if np.isfinite(h0) else 1.0)
+    ref = np.real(np.fft.ifft2(mult * np.fft.fft2(phi)))
+    assert np.max(np.abs(V - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def _taylor_tables(max_deg=6):
+    """Homogeneous parts (degree d in (a, b)) of k tanh(k(h+a-b)) and
+    sech(k(h+a-b)), as sympy lambdas of (a, b, k, h)."""
+    sp = pytest.importorskip("sympy")
+    a, b, k, h, s = sp.symbols("a b k h s")
+    V = sp.series(k * sp.tanh(k * (h + s * (a - b))), s, 0, max_deg + 1).removeO()
+    B = sp.series(sp.sech(k * (h + s * (a - b))), s, 0, max_deg + 1).removeO()
+    vfun = [sp.lambdify((a, b, k, h), sp.simplify(V.coeff(s, d))) for d in range(max_deg + 1)]
+    bfun = [sp.lambdify((a, b, k, h), sp.simplify(B.coeff(s, d))) for d in range(max_deg + 1)]
+    return vfun, bfun
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_constant_elevation_and_depth_match_taylor_per_order(dim):
+    # With constant eta = a and delta = b a single Fourier mode of phi~ has the
+    # exact V = k tanh(k(h0+a-b)) phi^ and bottom potential sech(k(h0+a-b)) phi^
+    # (the constant-delta idea of the applicability section).  V_l of the
+    # successive scheme is O(eps^m zeta^{l-m}), so it must equal the Taylor part of
+    # total degree l-1 in (a, b); varphi_l likewise for sech.
+    vfun, bfun = _taylor_tables()
+    if dim == 1:
+        g = O.Grid(32, 1, 2 * np.pi)
+        modes = [(1, 0), (3, 0), (6, 0)]
+    else:
+        g = O.Grid(32, 16, 2 * np.pi, 2 * np.pi)
+        modes = [(1, 1), (3, 2), (2, 5)]
+    x = np.arange(g.nx) * g.Lx / g.nx
+    y = np.arange(g.ny) * g.Ly / g.ny
+    X, Y = np.meshgrid(x, y)
+    for (a, b, h0) in [(0.05, 0.0, 1.0), (0.03, 0.04, 0.7), (-0.02, 0.05, 1.3), (0.04, -0.03, 0.5)]:
+        for (mx, my) in modes:
+            kx, ky = 2 * np.pi * mx / g.Lx, 2 * np.pi * my / g.Ly
+            kk = math.hypot(kx, ky)
+            carrier = np.cos(kx * X + ky * Y)
+            eta = np.full((g.ny, g.nx), a)
+            delta = np.full((g.ny, g.nx), b) if b != 0 else None
+            _, terms = O.vertical_velocity(eta, carrier, delta, h0, g, alpha=1.0,
+                                           return_terms=True)
+            for l, Vl in enumerate(terms["V"], start=1):
+                amp = np.sum(Vl * carrier) / np.sum(carrier * carrier)
+                ref = vfun[l - 1](a, b, kk, h0)
+                assert abs(amp - ref) < 1e-12 * max(1.0, kk), (l, a, b, mx, my)
+                assert np.max(np.abs(Vl - amp * carrier)) < 1e-12 * max(1.0, kk)
+            if delta is not None:
+                for l, Bl in enumerate(terms["varphi"], start=1):
+                    amp = np.sum(Bl * carrier) / np.sum(carrier * carrier)
+                    ref = bfun[l - 1](a, b, kk, h0)
+                    assert abs(amp - ref) < 1e-12, (l, a, b, mx, my)
+
+
+@pytest.mark.parametrize("order,ratio", [(3, 8.0), (5, 32.0), (7, 128.0)])
+@pytest.mark.parametrize("variable", [False, True])
+def test_truncation_error_scaling_vs_laplace_solver(order, ratio, variable):
+    # Sec. 2.4: the omitted terms are O(eps^m zeta^{M+1-m}).  Scaling eta and delta
+    # by s at fixed phi~, the error of the order-M sum against the exact
+    # Dirichlet-Neumann operator (independent Laplace solve) falls as s^M.
+    L, nx, h0 = 2 * np.pi, 64, 1.0
+    x = np.arange(nx) * L / nx
+    eta0 = 0.3 * np.cos(x) + 0.2 * np.sin(2 * x + 0.4)
+    del0 = 0.25 * np.cos(x + 0.5) + 0.15 * np.sin(3 * x)
+    phi = np.cos(x) + 0.5 * np.sin(2 * x + 0.3)
+    g = O.Grid(nx, 1, L)
+    errs = []
+    for s in (0.4, 0.2, 0.1):
+        d = s * del0 if variable else None
+        Ve = exact_vertical_velocity(s * eta0, phi, d, h0, L, n_sigma=32)
+        Vo = O.vertical_velocity(s * eta0, phi, d, h0, g, order=order, alpha=1.0)
+        errs.append(np.linalg.norm(Vo - Ve) / np.linalg.norm(Ve))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 0.7 * ratio < r2 < 1.4 * ratio, errs
+    assert 0.6 * ratio < r1 < 1.5 * ratio, errs
+    if order == 7:
+        assert errs[0] < 1e-5
+
+
+def test_oblique_2d_matches_1d():
+    # A 2-D field varying only along the grid direction (2, 1) must give the 1-D
+    # result with the same wavenumbers (checks ik. on both components).
+    n, L, h0 = 32, 2 * np.pi, 0.8
+    # x carries harmonic p at index 2p: 64 points keep degree-7 products unaliased
+    g2 = O.Grid(2 * n, n, L, L)
+    L1 = L / math.sqrt(5.0)
+    g1 = O.Grid(n, 1, L1)
+    s1 = np.arange(n) * L1 / n
+
+    def f1(c):  # 1-D functions of the coordinate along the direction
+        return c[0] * np.cos(2 * np.pi * s1 / L1) + c[1] * np.sin(4 * np.pi * s1 / L1 + 0.3)
+
+    x = np.arange(2 * n) * L / (2 * n)
+    y = np.arange(n) * L / n
+    X, Y = np.meshgrid(x, y)
+    arg = 2 * np.pi * (2 * X + Y) / L      # phase of mode (2,1)
+
+    def f2(c):
+        return c[0] * np.cos(arg) + c[1] * np.sin(2 * arg + 0.3)
+
+    ce, cd, cp = (0.12, 0.05), (0.1, -0.06), (1.0, 0.4)
+    V1 = O.vertical_velocity(f1(ce)[None, :], f1(cp)[None, :], f1(cd)[None, :], h0, g1, alpha=1.0)
+    V2 = O.vertical_velocity(f2(ce), f2(cp), f2(cd), h0, g2, alpha=1.0)
+    # compare Fourier coefficients of harmonics p = 1..6 along the direction
+    F1 = np.fft.fft(V1[0]) / n
+    F2 = np.fft.fft2(V2) / (2 * n * n)
+    for p in range(1, 7):
+        assert abs(F1[p] - F2[p % n, (2 * p) % (2 * n)]) < 1e-12 * np.max(np.abs(F1)), p
+
+
+def test_dynamic_condition_matches_bernoulli():
+    # phi~_t of Eq. (prognostic) equals -g eta - |u|^2/2 - w^2/2 + w V (Bernoulli at
+    # the surface plus the chain rule), with u, w taken from the Laplace solution.
+    L, nx, h0, grav = 2 * np.pi, 64, 1.0, 9.81
+    x = np.arange(nx) * L / nx
+    eta = 0.06 * np.cos(x) + 0.03 * np.sin(2 * x + 0.4)
+    phi = np.cos(x) + 0.5 * np.sin(2 * x + 0.3)
+    delta = 0.1 * np.cos(x + 0.5)
+    Ve, u, w = exact_vertical_velocity(eta, phi, delta, h0, L, return_phi_grad=True)
+    g = O.Grid(nx, 1, L)
+    got = O.dynamic_rhs(eta[None, :], phi[None, :], Ve[None, :], grav, g, alpha=1.0)[0]
+    ref = -grav * eta - 0.5 * (u * u + w * w) + w * Ve
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def test_rk4_linear_amplification_factor():
+    # For an infinitesimal single mode the system is linear,
+    # d/dt (eta^, phi^) = A (eta^, phi^), A = [[0, k t], [-g, 0]], and one classical
+    # RK4 step multiplies by I + Ad + (Ad)^2/2 + (Ad)^3/6 + (Ad)^4/24 exactly.
+    nx, L, h0, grav, dt = 32, 10.0, 0.7, 9.81, 0.05
+    g = O.Grid(nx, 1, L)
+    pb = O.Problem(g, grav, h0)
+    x = np.arange(nx) * L / nx
+    m = 3
+    k = 2 * np.pi * m / L
+    a = 1e-9
+    eta = a * np.cos(k * x)
+    phi = 0.3 * a * np.sin(k * x)
+    e1, p1 = O.step(pb, eta, phi, dt, 1)
+    A = np.array([[0.0, k * math.tanh(k * h0)], [-grav, 0.0]]) * dt
+    R = np.eye(2) + A + A @ A / 2 + A @ A @ A / 6 + A @ A @ A @ A / 24
+    ce, se = 1.0, 0.0     # eta = ce cos + se sin (in units of a)
+    cp, sp_ = 0.0, 0.3
+    new_c = R @ np.array([ce, cp])
+    new_s = R @ np.array([se, sp_])
+    ref_eta = a * (new_c[0] * np.cos(k * x) + new_s[0] * np.sin(k * x))
+    ref_phi = a * (new_c[1] * np.cos(k * x) + new_s[1] * np.sin(k * x))
+    assert np.max(np.abs(e1[0] - ref_eta)) < 1e-6 * a
+    assert np.max(np.abs(p1[0] - ref_phi)) < 1e-6 * a
+
+
+def test_linear_dispersion_relation():
+    # omega^2 = g k tanh(k h) at small amplitude: a standing-free progressive mode
+    # returns to its phase after one period up to O((omega dt)^4).
+    nx, L, h0, grav = 32, 8.0, 0.5, 9.81
+    g = O.Grid(nx, 1, L)
+    pb = O.Problem(g, grav, h0)
+    m = 2
+    k = 2 * np.pi * m / L
+    om = math.sqrt(grav * k * math.tanh(k * h0))
+    T = 2 * np.pi / om
+    nsteps = 200
+    dt = T / nsteps
+    x = np.arange(nx) * L / nx
+    a = 1e-6
+    eta = a * np.cos(k * x)
+    phi = (grav * a / om) * np.sin(k * x)
+    e, p = O.step(pb, eta, phi, dt, nsteps)
+    assert np.max(np.abs(e[0] - eta)) < 1e-6 * a * 10
+
+
+def test_mass_conserved_exactly():
+    # R4: F{V_l}(0) = 0, so int eta dA is constant to round-off.
+    g = O.Grid(16, 8, 3.0, 2.0)
+    pb = O.Problem(g, 9.81, 0.5, delta=W.random_field(16, 8, 11, amplitude=0.05))
+    eta = W.random_field(16, 8, 12, amplitude=0.03) + 0.01
+    phi = W.random_field(16, 8, 13, amplitude=0.1)
+    m0, _ = O.invariants(pb, eta, phi)
+    e, p = O.step(pb, eta, phi, 0.01, 5)
+    m1, _ = O.invariants(pb, e, p)
+    assert abs(m1 - m0) < 1e-14 * np.sum(np.abs(eta)) * g.dA * 10
+
+
+def test_sponge_constant_weight_closed_form():
+    # R7: with a constant weight w the damping pressure reduces to nu w phi~.
+    g = O.Grid(32, 1, 4.0)
+    phi = W.random_field(32, 1, 5)
+    pd = O.damping_pressure(phi, np.full((1, 32), 0.7), 2.0, g)
+    assert np.max(np.abs(pd - 1.4 * phi)) < 1e-13
+
+
+@pytest.mark.slow
+def test_solitary_wave_energy_and_speed():
+    # Sec. 3.1: the total energy of a solitary wave stays constant (the paper
+    # reports |E-E0|/E0 ~ 1e-5); the crest moves at about sqrt(g (h + a)).
+    wl = W.solitary_1d()
+    m = wl.members[0]
+    g = O.Grid(m.nx, 1, m.Lx)
+    pb = O.Problem(g, wl.gravity, m.h0)
+    eta = O.project(pb, m.eta)
+    phi = O.project(pb, m.phi)
+    _, E0 = O.invariants(pb, eta, phi)
+    nsteps = 400
+    e, p = O.step(pb, eta, phi, wl.dt, nsteps)
+    _, E1 = O.invariants(pb, e, p)
+    assert abs(E1 - E0) / E0 < 1e-4
+    # crest position by a parabolic fit around the maximum
+    def crest(f):
+        f = f[0]
+        i = int(np.argmax(f))
+        fm, f0, fp = f[i - 1], f[i], f[(i + 1) % f.size]
+        off = 0.5 * (fm - fp) / (fm - 2 * f0 + fp)
+        return (i + off) * m.Lx / m.nx
+    speed = (crest(e) - crest(eta)) / (nsteps * wl.dt)
+    c = wl.notes["c"]
+    assert abs(speed - c) / c < 0.03
+
+
+def test_translating_stokes_wave():
+    # A wave of permanent form eta(x - c t) has V = eta_t = -c eta_x exactly.  The
+    # third-order Stokes initial condition leaves an absolute residual O(eps^4)
+    # (relative O(eps^3)); by the parity of the Stokes expansion the first and
+    # third harmonics of the residual are O(eps^5).
+    res, h1, h3 = [], [], []
+    for eps in (0.1, 0.05):
+        eta, phi, c, k = W.stokes_1d(64, 2 * np.pi, 1, 1.0, eps)
+        g = O.Grid(64, 1, 2 * np.pi)
+        V = O.vertical_velocity(eta[None, :], phi[None, :], None, 1.0, g, alpha=1.0)[0]
+        kx = 2 * np.pi * np.fft.fftfreq(64, d=2 * np.pi / 64)
+        eta_x = np.real(np.fft.ifft(1j * kx * np.fft.fft(eta)))
+        r = V + c * eta_x
+        res.append(np.linalg.norm(r) / np.linalg.norm(V))
+        F = np.abs(np.fft.fft(r))
+        h1.append(F[1])
+        h3.append(F[3])
+    assert res[0] / res[1] > 6.5, res
+    assert h1[0] / h1[1] > 20.0 and h3[0] / h3[1] > 20.0, (h1, h3)
