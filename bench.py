@@ -1,0 +1,382 @@
+"""Benchmark of the ESBI hot path on one GB300 (or N independent replicas).
+
+Workload (default ``crossing_batch``): 96 crossing random seas advanced together,
+64 on 256x256 and 32 on 512x512 grids, deep water kp h = 5, 7th-order
+successive approximation, low-pass filter on, FP32 FFTs/products with FP64
+state and RK4 sums.  A step is one classical RK4 step of every member (four
+right-hand sides, each one vertical-velocity diagnostic plus the dynamic
+condition).  Metric: grid-point RK4 steps per second (sum over members of
+nx*ny, times steps, over the device time of the timed region).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK4 steps/s"
+UNIT = "pt-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="crossing_batch",
+                    choices=["crossing_batch", "large_variable", "bar_1d", "stokes_2d"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    import workloads as W
+    return getattr(W, name)()
+
+
+def workload_config(wl):
+    shapes = {}
+    for m in wl.members:
+        key = f"{m.nx}x{m.ny}"
+        shapes[key] = shapes.get(key, 0) + 1
+    cfg = {"workload": wl.name, "members": shapes, "points": wl.points, "order": wl.order,
+           "alias_frac": wl.alpha, "dt": wl.dt,
+           "filter": bool(wl.filt_beta1 > 0), "sponge": wl.sponge_w is not None,
+           "variable_depth": any(m.delta is not None for m in wl.members),
+           "l2": "inputs larger than L2 (no flush needed)"}
+    return cfg
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_19840_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(family):
+    """Per-launch DRAM bytes of a kernel family from the committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    except Exception:
+        return None
+    if d.get("source_sha") != source_sha():
+        return None
+    ent = d.get("families", {}).get(family)
+    return ent
+
+
+def make_context(sbi, wl, precision, stream, **extra):
+    grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in wl.members]
+    depths = [(m.h0 - m.delta) if m.delta is not None else None for m in wl.members]
+    h0 = wl.members[0].h0
+    return sbi.Context(grids, wl.gravity, depths, h0=h0, order=wl.order, alias_frac=wl.alpha,
+                       precision=precision, filt_beta1=wl.filt_beta1, filt_beta2=wl.filt_beta2,
+                       k_ref=wl.k_ref, sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu,
+                       stream=stream, check_finite=0, **extra)
+
+
+def time_steps(ctx, torch, stream, dt, steps, warmup):
+    for _ in range(warmup):
+        ctx.step(dt, 1)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        ctx.step(dt, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1000.0
+
+
+def cpu_oracle_sample(wl, target_s=10.0):
+    """Time the FP64 oracle on a bounded sample: whole RK4 steps of members
+    drawn in workload order, until about target_s seconds of CPU work."""
+    from oracle import sbi_oracle as O
+    import numpy as np
+    t_tot, pts, steps_done = 0.0, 0, 0
+    members = []
+    # one member of each distinct shape, in workload proportion order
+    seen = set()
+    for m in wl.members:
+        key = (m.nx, m.ny)
+        if key not in seen:
+            seen.add(key)
+            members.append(m)
+    i = 0
+    while t_tot < target_s and i < 64:
+        m = members[i % len(members)]
+        g = O.Grid(m.nx, m.ny, m.Lx, m.Ly)
+        pb = O.Problem(g, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
+                       sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
+                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+        t0 = time.perf_counter()
+        O.step(pb, m.eta, m.phi, wl.dt, 1)
+        t_tot += time.perf_counter() - t0
+        pts += m.nx * m.ny
+        steps_done += 1
+        i += 1
+    shapes = ",".join(f"{m.nx}x{m.ny}" for m in members)
+    return {"value": pts / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps_done} single-member RK4 steps cycling over member shapes [{shapes}]"
+                      f" ({t_tot:.1f} s of CPU time)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = make_workload(args.workload)
+    total_t, total_pts = 0.0, 0
+    samples = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(wl, target_s=2.0)
+        if k >= args.warmup:
+            pts_s = r["value"]
+            samples.append(pts_s)
+    value = sum(samples) / len(samples)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: single-member RK4 steps of the workload's "
+                                       "member shapes for about 2 s of CPU time"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2310_19840_gb300 import sbi
+
+    wl = make_workload(args.workload)
+    prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
+    stream = torch.cuda.Stream()
+    ctx = make_context(sbi, wl, prec, stream.cuda_stream)
+    for i, m in enumerate(wl.members):
+        ctx.set_state(i, m.eta, m.phi)
+    launches = ctx.step_launches()
+    bytes_step = ctx.step_bytes(-1)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region (device time, max over ranks) ----
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    secs = time_steps(ctx, torch, stream, wl.dt, args.steps, args.warmup)
+    clk = clocks.stop()
+    t = torch.tensor([secs], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    secs = float(t.item())
+    pts = wl.points
+    value = pts * args.steps * world / secs
+
+    # ---- per-kernel roofline: the same K steps with CUDA-event pairs per pass ----
+    ctx.profile_enable(True)
+    for _ in range(args.steps):
+        ctx.step(wl.dt, 1)
+    fams = ctx.profile_read()
+    ctx.profile_enable(False)
+    fam_bytes = [ctx.step_bytes(i) for i in range(len(fams))]
+    dom = max(range(len(fams)), key=lambda i: fams[i][2])
+    name, nlaunch, ms = fams[dom]
+    launches_per_step = nlaunch / max(1, args.steps)
+    bytes_per_launch = fam_bytes[dom] / max(1e-9, launches_per_step)
+    avg_s = (ms / 1000.0) / max(1, nlaunch)
+    achieved = bytes_per_launch / avg_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    tr = ncu_traffic(name.split()[0])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (tr or {}).get("bytes_per_launch"),
+                "kernel": name, "launches_per_step": launches_per_step,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
+                "share_of_step": ms / sum(f[2] for f in fams),
+                "families": [{"kernel": f[0], "launches": f[1], "ms": f[2],
+                              "algorithmic_GBps": (fam_bytes[i] * args.steps / (f[2] / 1e3) / 1e9)
+                              if f[2] > 0 else None} for i, f in enumerate(fams)]}
+    step_gbps = bytes_step * args.steps / secs / 1e9
+
+    # ---- error at this configuration: FP32 path vs FP64 path, member 0 ----
+    err = None
+    fp64_arm = None
+    if not args.no_fp64_arm and prec == sbi.SBI_FP32:
+        ctx64 = make_context(sbi, wl, sbi.SBI_FP64, stream.cuda_stream)
+        for i, m in enumerate(wl.members):
+            ctx64.set_state(i, m.eta, m.phi)
+        ctx_err = make_context(sbi, wl, sbi.SBI_FP32, stream.cuda_stream)
+        ctx_err.set_state(0, wl.members[0].eta, wl.members[0].phi)
+        ctx64_0 = ctx64
+        V32 = ctx_err.vertical_velocity(0)
+        V64 = ctx64_0.vertical_velocity(0)
+        err = {"V_rel_l2_fp32_vs_fp64": float(np.linalg.norm(V32 - V64) / np.linalg.norm(V64)),
+               "member": 0}
+        k64 = max(1, min(3, args.steps))
+        s64 = time_steps(ctx64, torch, stream, wl.dt, k64, 1)
+        fp64_arm = {"value": pts * k64 / s64, "unit": UNIT, "ms_per_step": s64 / k64 * 1e3,
+                    "steps": k64, "dtype": "f64"}
+        ctx64.close()
+        ctx_err.close()
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0)
+        host = [(torch.from_numpy(np.ascontiguousarray(m.eta)).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(m.phi)).pin_memory()) for m in wl.members]
+        outs = [(torch.empty_like(e).pin_memory(), torch.empty_like(p).pin_memory())
+                for e, p in host]
+        def e2e_step():
+            for i, (e, p) in enumerate(host):
+                ctx_e.set_state(i, e, p)
+            ctx_e.step(wl.dt, 1)
+            for i, (e, p) in enumerate(outs):
+                ctx_e.get_state(i, e, p)
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        nbytes = sum(2 * e.numel() * 8 for e, _ in host)
+        e2e = {"value": pts * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ke,
+               "api": "sbi_set_state(host) + sbi_step(dt, 1) + sbi_get_state(host) per member"}
+        ctx_e.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, target_s=10.0)
+
+    cfg = workload_config(wl)
+    cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == sbi.SBI_FP64 else "f32", "data": "synthetic",
+            "config": cfg, "clocks": clk, "gpu_launches": launches * args.steps,
+            "algorithmic_step_GBps": step_gbps, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_arm, "error": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

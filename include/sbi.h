@@ -1,0 +1,173 @@
+/*
+ * sbi.h - C ABI of the GB300 (sm_103a) enhanced spectral boundary integral
+ * (ESBI) hot path: the surface vertical velocity of a periodic free surface over
+ * variable depth, and fixed-step RK4 time stepping of the free-surface
+ * equations that use it.
+ *
+ * Method: Wang, "An enhanced spectral boundary integral method for modeling
+ * highly nonlinear water waves in variable depth" (arXiv 2310.19840).
+ *   - Governing problem: Laplace equation in -h0+delta(x) <= z <= eta(x) with
+ *     the free-surface and impermeable-seabed conditions (Sec. 2.1).
+ *   - Prognostic equations: Zakharov form of the kinematic and dynamic surface
+ *     conditions, Eq. (prognostic) (Sec. 2.2).
+ *   - Diagnostic: V = sum_{l=1..M} V_l by the successive approximation of
+ *     Sec. 2.4 (recursions app-V-scs / app-phi-scs, explicit forms in
+ *     Appendix C), dealiased by the 2/(l+1) rule (end of Sec. 2.4).
+ *   - Energy: Eq. (energy) (Sec. 3.1).  Low-pass filter: Eq. (filter).
+ *     Damping pressure: Eq. (pd).
+ *
+ * Conventions shared by every call:
+ *   - A grid is nx x ny points on a periodic Lx x Ly box; ny = 1 is a 1-D
+ *     problem (Ly is then a unit width).  nx is a power of two in [16, 4096];
+ *     ny is 1 or a power of two in [8, 2048].
+ *   - Fields are row-major, index = iy * nx + ix (x fastest), double precision
+ *     on the host side of the ABI.  Pointers flagged on_device = 1 are CUDA
+ *     device pointers (for example a torch tensor's data_ptr()); otherwise they
+ *     are host pointers.
+ *   - The library copies every input; callers keep ownership of their buffers.
+ *     A context owns all the device memory it allocates and frees it in
+ *     sbi_destroy.
+ *   - Every int-returning call returns SBI_OK or one of the SBI_E* codes below
+ *     and never aborts the process or traps the device; sbi_last_error() gives
+ *     the message of the last failure on that context.
+ *   - Calls on one context are not thread-safe; different contexts are
+ *     independent.  Work is enqueued on opt.cuda_stream (NULL: the legacy
+ *     default stream).
+ */
+#ifndef SBI_H
+#define SBI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBI_OK             0
+#define SBI_EINVAL         1   /* bad grid, size, order, pointer or member index */
+#define SBI_ENOMEM         2   /* device allocation failed */
+#define SBI_ECUDA          3   /* a CUDA runtime call failed */
+#define SBI_ENONFINITE     4   /* NaN or Inf appeared in the state */
+#define SBI_ENOTCONVERGED  5   /* adaptive order reached M without meeting adapt_tol */
+#define SBI_ETIMEOUT       6   /* a bounded device-side wait expired */
+
+#define SBI_FP32 0             /* FFTs, multipliers, products in FP32; FP64 state, RK4 sums, invariants */
+#define SBI_FP64 1             /* everything in FP64 (the plain path) */
+
+typedef struct sbi_ctx sbi_ctx;   /* opaque */
+
+typedef struct {
+    int nx, ny;                   /* points; ny = 1 for 1-D */
+    double Lx, Ly;                /* periodic box [m]; Ly ignored when ny = 1 */
+} sbi_grid;
+
+typedef struct {
+    int    order;        /* M, highest order of the successive approximation, 1..7 (default 7; Sec. 2.4) */
+    double alias_frac;   /* kept fraction alpha of each axis' modes: |m| < alpha n/2 (default 0.5; Sec. 2.4) */
+    double h0;           /* reference depth h0 [m], delta = h0 - h; NAN: mean of h (default NAN).
+                            INFINITY selects deep water (only with h == NULL) */
+    int    precision;    /* SBI_FP32 (default) or SBI_FP64 */
+    double adapt_tol;    /* 0: fixed order M (default).  > 0: stop at the first l with
+                            ||F{V_l}|| <= adapt_tol ||sum_{m<=l} F{V_m}|| (per member) */
+    double filt_beta1;   /* low-pass filter Lambda = exp(-|k/(beta1 k_ref)|^beta2) applied to the */
+    double filt_beta2;   /* state after every step, Eq. (filter); beta1 <= 0 disables (default) */
+    double k_ref;        /* reference wavenumber of the filter [rad/m] */
+    const double* sponge_w; /* damping weight w(x, y) (nx*ny host doubles, same for every member) or NULL */
+    double sponge_nu;    /* damping strength nu [1/s]: p_d = nu F^-1{ ik/(-k^2) . F{w grad phi~} }, Eq. (pd) */
+    void*  cuda_stream;  /* cudaStream_t used for all work (NULL: legacy default stream) */
+    int    check_finite; /* 1 (default): sbi_step synchronizes and checks the state for NaN/Inf;
+                            0: sbi_step only enqueues work */
+    int    set_state_dealias; /* 1 (default): sbi_set_state removes the modes outside the dealias
+                            mask; 0: the fields are stored exactly as given (for bit-exact
+                            checkpoint/restart of states read with sbi_get_state) */
+    void* (*dev_alloc)(size_t bytes, void* user);  /* optional device allocator (NULL: cudaMalloc) */
+    void  (*dev_free)(void* ptr, void* user);      /* matching free (NULL: cudaFree) */
+    void*  alloc_user;   /* passed to dev_alloc / dev_free */
+} sbi_options;
+
+/* Fill *opt with the defaults listed above. */
+void sbi_default_options(sbi_options* opt);
+
+/* Create a context for one problem.
+ *   g        grid (see conventions).
+ *   gravity  g [m/s^2], > 0.
+ *   h        still-water depth h(x, y) > 0, nx*ny host doubles, or NULL for a
+ *            flat bottom of depth opt->h0 (which must then be given).  The
+ *            bottom variation delta = h0 - h enters the recursion of Sec. 2.4.
+ *   opt      options or NULL for the defaults.
+ *   out      receives the context; NULL on failure.
+ * The state is zero after creation.  SBI_EINVAL for a bad grid, order,
+ * alias_frac, depth or pointer; SBI_ENOMEM / SBI_ECUDA on device failures. */
+int sbi_create(const sbi_grid* g, double gravity, const double* h,
+               const sbi_options* opt, sbi_ctx** out);
+
+/* Create one context holding n independent problems ("members"), possibly on
+ * different grids; every member is advanced by each sbi_step.  grids[i] and
+ * h[i] (h may be NULL, or h[i] NULL for a flat member) as in sbi_create; one
+ * option set (and one h0 rule) for all members. */
+int sbi_create_batch(int n, const sbi_grid* grids, double gravity,
+                     const double* const* h, const sbi_options* opt, sbi_ctx** out);
+
+/* Number of members of a context (1 for sbi_create). */
+int sbi_num_members(const sbi_ctx* ctx);
+
+/* Set the state (eta, phi~) of one member: nx*ny doubles each.  Unless
+ * opt.set_state_dealias = 0 the modes outside the dealias mask of Sec. 2.4 are
+ * removed on entry, so the stored state is band-limited (in the FP32 path the
+ * removal is computed in FP32 and added to the FP64 state).  Other members are
+ * not touched.  Synchronizes the stream. */
+int sbi_set_state(sbi_ctx* ctx, int member, const double* eta, const double* phi,
+                  int on_device);
+
+/* Copy the state of one member out (nx*ny doubles each).  Synchronizes the stream. */
+int sbi_get_state(sbi_ctx* ctx, int member, double* eta, double* phi, int on_device);
+
+/* Surface vertical velocity V = sqrt(1+|grad eta|^2) dphi/dn at the current
+ * state (Sec. 2.2-2.4), nx*ny doubles.  With eulerian_w = 1 the Eulerian
+ * vertical velocity at the surface, w = (V + grad eta . grad phi~)/(1+|grad eta|^2),
+ * is returned instead.  Synchronizes the stream. */
+int sbi_vertical_velocity(sbi_ctx* ctx, int member, double* V_out, int on_device,
+                          int eulerian_w);
+
+/* Advance every member by n classical RK4 steps of size dt [s] (Sec. 2.2 with
+ * a fixed step); after each step the state is dealiased and, when enabled,
+ * low-pass filtered.  The step is replayed from a CUDA graph. */
+int sbi_step(sbi_ctx* ctx, double dt, int n);
+
+/* Mass int eta dA and total energy 1/2 int (V phi~ + g eta^2) dA (Eq. energy,
+ * dimensional, unit density) of one member, reduced in FP64 in a fixed order.
+ * Synchronizes the stream. */
+int sbi_invariants(sbi_ctx* ctx, int member, double* mass, double* energy);
+
+/* Orders used by the last diagnostic of a member (M unless adapt_tol > 0). */
+int sbi_orders_used(sbi_ctx* ctx, int member, int* orders);
+
+/* Per-kernel-family timing of the step (for measurement).  sbi_profile_enable
+ * turns on CUDA-event pairs around every pass of the captured step (the graph
+ * is re-captured).  sbi_profile_read returns, for family i < *count (at most
+ * cap entries), its name, the number of timed launches and their total device
+ * milliseconds since the last enable, and synchronizes the stream. */
+int sbi_profile_enable(sbi_ctx* ctx, int on);
+int sbi_profile_read(sbi_ctx* ctx, int cap, const char** names, long long* launches,
+                     double* total_ms, int* count);
+
+/* Algorithmic device-memory traffic of one step, in bytes, summed over all
+ * kernels of the step: each kernel counted as reading its inputs once and
+ * writing its outputs once.  family < 0 gives the whole step. */
+int sbi_step_bytes(const sbi_ctx* ctx, int family, double* bytes);
+
+/* Number of kernel launches in one captured step. */
+int sbi_step_launches(const sbi_ctx* ctx, int* launches);
+
+/* Message of the last failing call on ctx (or of the last failing create when
+ * ctx is NULL).  Never NULL. */
+const char* sbi_last_error(const sbi_ctx* ctx);
+
+/* Free every device buffer, graph and stream of the context.  NULL is ignored. */
+void sbi_destroy(sbi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBI_H */

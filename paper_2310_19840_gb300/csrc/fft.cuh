@@ -1,0 +1,194 @@
+// fft.cuh - block-cooperative complex FFTs in registers and shared memory.
+//
+// The transforms F{.} and F^{-1}{.} of Sec. 2.2 are evaluated on the device by
+// Stockham autosort passes: a transform of length N is split over N/R threads,
+// each thread owning R elements in registers.  A pass with current sub-length
+// Ls multiplies element r of butterfly b by w_{Ls*R}^{r*(b mod Ls)}, runs a
+// radix-R DFT in registers and scatters the results to natural Stockham
+// positions ((b - k) R + k + r Ls) in shared memory; the next pass gathers with
+// stride N/R.  The first pass reads straight from registers (the caller loads
+// element j + r N/R into slot r), the last pass leaves the transform in natural
+// order in shared memory.  Forward transforms use w = exp(-2 pi i / L),
+// inverse ones exp(+2 pi i / L); neither is normalised.
+//
+// Shared-memory indices are padded by one complex per 32 (pad()) to spread
+// the power-of-two strides of the scatter over the banks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sbi {
+
+template <typename T> struct cplx;
+template <> struct cplx<float>  { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cx = typename cplx<T>::type;
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) { V v; v.x = a; v.y = b; return v; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { return mk<V>(a.x * s, a.y * s); }
+// multiply by SIGN * i
+template <int SIGN, typename V> __device__ __forceinline__ V rot(V a) {
+  return SIGN > 0 ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
+
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 5) + 1; }
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// Radix-R DFT in registers, R in {1, 2, 4, 8, 16}, y_q = sum_r x_r w_R^{r q}.
+// ---------------------------------------------------------------------------
+template <int R, int SIGN, typename V> struct Dft;
+
+template <int SIGN, typename V> struct Dft<1, SIGN, V> {
+  __device__ __forceinline__ static void run(V*) {}
+};
+
+template <int SIGN, typename V> struct Dft<2, SIGN, V> {
+  __device__ __forceinline__ static void run(V* x) {
+    V a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  }
+};
+
+template <int SIGN, typename V> struct Dft<4, SIGN, V> {
+  __device__ __forceinline__ static void run(V* x) {
+    V t0 = cadd(x[0], x[2]), t1 = csub(x[0], x[2]);
+    V t2 = cadd(x[1], x[3]), t3 = rot<SIGN>(csub(x[1], x[3]));
+    x[0] = cadd(t0, t2);
+    x[2] = csub(t0, t2);
+    x[1] = cadd(t1, t3);
+    x[3] = csub(t1, t3);
+  }
+};
+
+// Split radix-2 step: DFT of length R from two DFTs of length R/2 of the even
+// and odd elements, y_q = E_q + w_R^q O_q, y_{q+R/2} = E_q - w_R^q O_q.
+template <int SIGN, typename V> struct Dft<8, SIGN, V> {
+  __device__ __forceinline__ static void run(V* x) {
+    using S = decltype(V::x);
+    V e[4] = {x[0], x[2], x[4], x[6]};
+    V o[4] = {x[1], x[3], x[5], x[7]};
+    Dft<4, SIGN, V>::run(e);
+    Dft<4, SIGN, V>::run(o);
+    const S h = S(0.70710678118654752440);
+    // w8^1 = h (1 + SIGN i), w8^2 = SIGN i, w8^3 = h (-1 + SIGN i)
+    V o1 = cscale(cadd(o[1], rot<SIGN>(o[1])), h);
+    V o2 = rot<SIGN>(o[2]);
+    V o3 = cscale(csub(rot<SIGN>(o[3]), o[3]), h);
+    x[0] = cadd(e[0], o[0]); x[4] = csub(e[0], o[0]);
+    x[1] = cadd(e[1], o1);   x[5] = csub(e[1], o1);
+    x[2] = cadd(e[2], o2);   x[6] = csub(e[2], o2);
+    x[3] = cadd(e[3], o3);   x[7] = csub(e[3], o3);
+  }
+};
+
+template <int SIGN, typename V> struct Dft<16, SIGN, V> {
+  __device__ __forceinline__ static void run(V* x) {
+    using S = decltype(V::x);
+    V e[8], o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
+    Dft<8, SIGN, V>::run(e);
+    Dft<8, SIGN, V>::run(o);
+    // cos(2 pi q / 16), sin(2 pi q / 16) for q = 0..7
+    const S c[8] = {S(1.0), S(0.92387953251128675613), S(0.70710678118654752440),
+                    S(0.38268343236508977173), S(0.0), S(-0.38268343236508977173),
+                    S(-0.70710678118654752440), S(-0.92387953251128675613)};
+    const S s[8] = {S(0.0), S(0.38268343236508977173), S(0.70710678118654752440),
+                    S(0.92387953251128675613), S(1.0), S(0.92387953251128675613),
+                    S(0.70710678118654752440), S(0.38268343236508977173)};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      V w = mk<V>(c[q], SIGN > 0 ? s[q] : -s[q]);
+      V t = q == 0 ? o[0] : cmul(o[q], w);
+      x[q] = cadd(e[q], t);
+      x[q + 8] = csub(e[q], t);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Twiddle tables: tw[off(N) + j] = exp(-2 pi i j / N), j < N, N = 2^q >= 2,
+// off(N) = N - 2.  Built on the host in FP64.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int tw_off(int n) { return n - 2; }
+
+template <int SIGN, typename V>
+__device__ __forceinline__ V twiddle(const V* __restrict__ tw, int N, int idx) {
+  V w = __ldg(tw + tw_off(N) + idx);
+  return SIGN > 0 ? cconj(w) : w;
+}
+
+// ---------------------------------------------------------------------------
+// Stockham transform of length N by T = N/R threads (thread index j), data in
+// registers on entry (x[r] = a[j + r T]) and in natural order in s[] (padded)
+// on exit.  All threads of the block must call it (it contains barriers);
+// threads without work still take part.  The caller must make sure nobody
+// still reads s[] from earlier work (a barrier before the call).
+// ---------------------------------------------------------------------------
+template <int N, int R, int Ls, int SIGN, typename V>
+struct StockhamPass {
+  __device__ __forceinline__ static void run(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
+    constexpr int T = N / R;
+    if constexpr (N / Ls >= R) {
+      // full pass of radix R
+      const int k = j & (Ls - 1);
+      if constexpr (Ls > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r)
+          x[r] = cmul(x[r], twiddle<SIGN>(tw, N, (r * k) * (N / (Ls * R))));
+      }
+      Dft<R, SIGN, V>::run(x);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[pad(base + r * Ls)] = x[r];
+      __syncthreads();
+      if constexpr (Ls * R < N) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = s[pad(j + r * T)];
+        __syncthreads();
+        StockhamPass<N, R, Ls * R, SIGN, V>::run(x, s, j, tw);
+      }
+    } else {
+      // last pass, radix RP = N / Ls < R: butterflies b_q = j + q T (q < R/RP),
+      // b_q < Ls, with elements x[q + m R/RP] (m < RP); output b_q + m Ls.
+      constexpr int RP = N / Ls;
+      constexpr int Q = R / RP;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        V v[RP];
+        const int b = j + q * T;
+#pragma unroll
+        for (int m = 0; m < RP; ++m) v[m] = x[q + m * Q];
+#pragma unroll
+        for (int m = 1; m < RP; ++m) v[m] = cmul(v[m], twiddle<SIGN>(tw, N, m * b));
+        Dft<RP, SIGN, V>::run(v);
+#pragma unroll
+        for (int m = 0; m < RP; ++m) s[pad(b + m * Ls)] = v[m];
+      }
+      __syncthreads();
+    }
+  }
+};
+
+template <int N, int R, int SIGN, typename V>
+__device__ __forceinline__ void fft_block(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
+  static_assert((N & (N - 1)) == 0 && N >= 1, "N must be a power of two");
+  static_assert(R >= 1 && R <= N && (R & (R - 1)) == 0, "R must be a power of two <= N");
+  if constexpr (N == 1) {
+    s[0] = x[0];
+    __syncthreads();
+  } else {
+    StockhamPass<N, R, 1, SIGN, V>::run(x, s, j, tw);
+  }
+}
+
+}  // namespace sbi

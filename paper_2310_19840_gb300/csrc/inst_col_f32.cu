@@ -1,0 +1,9 @@
+// Column pass instantiations and kernel preparation, float.
+#include "kernels.cuh"
+
+namespace sbi {
+template <> cudaError_t launch_col<float>(int ny, const ColParams& p, cudaStream_t st) {
+  return launch_col_impl<float>(ny, p, st);
+}
+template <> cudaError_t prepare_col_kernels<float>(int ny) { return prepare_col_impl<float>(ny); }
+}  // namespace sbi

@@ -1,0 +1,15 @@
+// Row and RK4 pass instantiations, float.
+#include "kernels.cuh"
+
+namespace sbi {
+template <> cudaError_t launch_row<float>(int nx, const RowParams& p, cudaStream_t st) {
+  return launch_row_impl<float>(nx, p, st);
+}
+template <> cudaError_t launch_rk<float>(int nx, const RkParams& p, cudaStream_t st) {
+  return launch_rk_impl<float>(nx, p, st);
+}
+template <> cudaError_t prepare_row_kernels<float>(int nx) { return prepare_row_impl<float>(nx); }
+template <> size_t row_smem_bytes<float>(int nx, int nslots) {
+  return row_smem_impl<float>(nx, nslots);
+}
+}  // namespace sbi

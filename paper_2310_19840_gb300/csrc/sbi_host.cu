@@ -1,0 +1,1169 @@
+// sbi_host.cu - C ABI, context, pass planner and step graph of the ESBI hot path.
+//
+// One right-hand-side (RHS) evaluation for a group of equal-grid members is
+// planned once as a fixed chain of passes (see sbi_internal.h for layouts):
+//
+//   Col A      F{phi~}, F{eta}  ->  V_1 = k tanh(kh) phi^, grad phi~, grad eta,
+//              grad varphi_1 = ik sech(kh) phi^                (Sec. 2.4, order 1)
+//   Row l      inverse x-FFT of V_{l-1} (and grad phi~ at l = 2, grad varphi_{l-1}),
+//              then every product that later orders need from it:
+//              eta^j V_{l-1}, eta^j grad phi~, delta^j grad varphi_{l-1}
+//   Col l      sum of the order-l terms of F{V_l} and F{varphi_l}
+//              (Appendix C; coefficient table in plan_col_level), masked
+//   Row RHS    V = sum_l V_l, grad eta, grad phi~ -> dynamic condition
+//              (Eq. prognostic) and the damping products w grad phi~ (Eq. pd)
+//   Col RHS    dealias the dynamic condition, add the damping pressure
+//   RK s       classical RK4 stage in FP64; next stage's working copies
+//
+// Each product is formed from the freshly inverted order as soon as that order
+// exists ("eager" products), so no physical V_l is stored or re-read.  A step is
+// four RHS evaluations plus the RK passes, and, with the low-pass filter on, a
+// projection of the FP64 state.  The whole step is captured into a CUDA graph
+// per dt and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sbi.h"
+#include "sbi_internal.h"
+
+using namespace sbi;
+
+namespace {
+
+std::string g_create_error = "no error";
+
+enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2 };
+enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_COUNT = 3 };
+const char* kFamilyNames[FAM_COUNT] = {"k_col (column FFT + spectral combine)",
+                                       "k_row (row FFT + products)", "k_rk (RK4 stage)"};
+
+struct Pass {
+  PassKind kind;
+  int nsize;  // nx for row / rk passes, ny for column passes
+  RowParams row;
+  ColParams col;
+  RkParams rk;
+  double bytes;  // algorithmic device-memory traffic of the launch
+};
+
+struct Group {
+  int nx = 0, ny = 0, W = 0, n = 0;
+  double Lx = 0, Ly = 0, h0 = 0;
+  bool variable = false, deep = false, two_d = false;
+  int kx_keep = 0, ky_keep = 0;
+  std::vector<int> members;  // context member ids
+  double *eta0 = nullptr, *phi0 = nullptr, *acc_eta = nullptr, *acc_phi = nullptr;
+  void *eta_w = nullptr, *Vphys = nullptr, *delta = nullptr, *wout = nullptr;
+  double* out64 = nullptr;   // conversion buffer for one member's field
+  int* d_active = nullptr;   // per-member flags for single-member passes
+  std::map<std::string, void*> mixed;
+  size_t phys_elems() const { return (size_t)nx * ny; }
+  size_t mixed_elems() const { return (size_t)ny * W; }
+};
+
+struct GraphEntry {
+  double dt;
+  bool prof;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+}  // namespace
+
+struct sbi_ctx {
+  std::string err = "no error";
+  sbi_options opt;
+  double gravity = 9.81;
+  bool fp64 = false;
+  size_t real_size = 4;
+  int nmembers = 0;
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t cap = nullptr;     // internal stream for graph capture
+  std::vector<Group> groups;
+  std::vector<std::pair<int, int>> where;  // member -> (group, local index)
+  std::vector<void*> allocs;
+  void* tw = nullptr;
+  void* wgt = nullptr;  // shared sponge weight (working precision) or null
+  int* d_flags = nullptr;  // [0]: non-finite state
+  double* d_partials = nullptr;
+  size_t partial_cap = 0;
+  std::vector<GraphEntry> graphs;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;        // pairs per profiled pass of the last captured step
+  std::vector<int> ev_family;
+  std::vector<double> prof_ms;
+  std::vector<long long> prof_launches;
+  std::vector<int> orders_used;
+  bool filter_on() const { return opt.filt_beta1 > 0.0; }
+};
+
+namespace {
+
+int fail(sbi_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(sbi_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SBI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                               \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+void* dalloc(sbi_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->opt.dev_alloc) {
+    p = c->opt.dev_alloc(bytes, c->opt.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->allocs.push_back(p);
+    cudaMemsetAsync(p, 0, bytes, c->cap);
+  }
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Planner
+// ---------------------------------------------------------------------------
+struct Planner {
+  sbi_ctx* c;
+  Group& g;
+  bool oom = false;      // an allocation failed (or a descriptor would overflow)
+
+  size_t vsize() const { return 2 * c->real_size; }
+
+  void* mixed(const std::string& name) {
+    auto it = g.mixed.find(name);
+    if (it != g.mixed.end()) return it->second;
+    void* p = dalloc(c, g.mixed_elems() * g.n * vsize());
+    if (!p) oom = true;
+    g.mixed[name] = p;
+    return p;
+  }
+  BufRef mref(const std::string& name) { return BufRef{mixed(name), (long long)g.mixed_elems()}; }
+  BufRef pref(void* p, bool shared = false) {
+    return BufRef{p, shared ? 0LL : (long long)g.phys_elems()};
+  }
+  BufRef dref(double* p) { return BufRef{p, (long long)g.phys_elems()}; }
+  double mixed_bytes() const { return (double)g.mixed_elems() * g.n * vsize(); }
+  double phys_bytes() const { return (double)g.phys_elems() * g.n * c->real_size; }
+  double phys64_bytes() const { return (double)g.phys_elems() * g.n * 8.0; }
+
+  // --- row pass builder ---
+  struct RowB {
+    RowParams p;
+    int nbuf = 0;
+    double bytes = 0;
+    int maxslot = -1;
+  };
+  RowB row_begin() {
+    RowB r;
+    std::memset(&r.p, 0, sizeof(r.p));
+    r.p.rows_total = g.n * g.ny;
+    r.p.ny = g.ny;
+    r.p.W = g.W;
+    r.p.tw = c->tw;
+    return r;
+  }
+  int add_buf(RowB& r, BufRef b) {
+    if (r.nbuf >= kMaxRowBufs) {
+      oom = true;
+      return 0;
+    }
+    r.p.buf[r.nbuf] = b;
+    return r.nbuf++;
+  }
+  bool room(RowB& r) {
+    if (r.p.nops >= kMaxRowOps) {
+      oom = true;
+      return false;
+    }
+    return true;
+  }
+  void c2r(RowB& r, int slot, const std::vector<std::string>& srcs, void* phys_out = nullptr) {
+    RowOp op{};
+    op.kind = ROP_C2R;
+    op.slot = (uint8_t)slot;
+    op.a = (uint8_t)r.nbuf;
+    op.b = (uint8_t)srcs.size();
+    for (auto& s : srcs) add_buf(r, mref(s));
+    r.bytes += mixed_bytes() * srcs.size();
+    op.dst = kNone;
+    if (phys_out) {
+      op.dst = (uint8_t)add_buf(r, pref(phys_out));
+      r.bytes += phys_bytes();
+    }
+    if (room(r)) r.p.ops[r.p.nops++] = op;
+    r.maxslot = std::max(r.maxslot, slot);
+  }
+  void prod(RowB& r, int slot, int ea, int db, int wc, double coef, const std::string& dst) {
+    RowOp op{};
+    op.kind = ROP_PROD;
+    op.slot = slot < 0 ? kNone : (uint8_t)slot;
+    op.a = (uint8_t)ea;
+    op.b = (uint8_t)db;
+    op.c = (uint8_t)wc;
+    op.coef = (float)coef;
+    op.dst = (uint8_t)add_buf(r, mref(dst));
+    r.bytes += mixed_bytes();
+    if (room(r)) r.p.ops[r.p.nops++] = op;
+  }
+  void n2(RowB& r, int slot0, const std::string& dst) {
+    RowOp op{};
+    op.kind = ROP_N2;
+    op.slot = (uint8_t)slot0;
+    op.a = g.two_d ? 2 : 1;
+    op.coef = (float)c->gravity;
+    op.dst = (uint8_t)add_buf(r, mref(dst));
+    r.bytes += mixed_bytes();
+    if (room(r)) r.p.ops[r.p.nops++] = op;
+  }
+  void wdot(RowB& r, int slot0, void* phys_out) {
+    RowOp op{};
+    op.kind = ROP_WDOT;
+    op.slot = (uint8_t)slot0;
+    op.a = g.two_d ? 2 : 1;
+    op.dst = (uint8_t)add_buf(r, pref(phys_out));
+    r.bytes += phys_bytes();
+    if (room(r)) r.p.ops[r.p.nops++] = op;
+  }
+  Pass row_end(RowB& r, bool use_eta, bool use_delta, bool use_w) {
+    if (use_eta) {
+      r.p.eta = pref(g.eta_w);
+      r.bytes += phys_bytes();
+    }
+    if (use_delta && g.variable) {
+      r.p.delta = pref(g.delta);
+      r.bytes += phys_bytes();
+    }
+    if (use_w && c->wgt) {
+      r.p.wgt = pref(c->wgt, true);
+      r.bytes += (double)g.phys_elems() * c->real_size;
+    }
+    r.p.nslots = r.maxslot + 1;
+    Pass ps{};
+    ps.kind = PK_ROW;
+    ps.nsize = g.nx;
+    ps.row = r.p;
+    ps.bytes = r.bytes;
+    return ps;
+  }
+
+  // --- column pass builder ---
+  struct ColIn {
+    std::string name;
+    std::vector<ColTerm> terms;
+  };
+  static ColTerm term(int acc, double cc, int kpow, int depth, int gx, int gy, int mask = 0) {
+    ColTerm t{};
+    t.acc = (uint8_t)acc;
+    t.c = cc;
+    t.kpow = (int8_t)kpow;
+    t.depth = (uint8_t)depth;
+    t.gx = (uint8_t)gx;
+    t.gy = (uint8_t)gy;
+    t.mask = (uint8_t)mask;
+    return t;
+  }
+  Pass col(const std::vector<ColIn>& ins, const std::vector<std::pair<std::string, ColTerm>>& outs,
+           int nacc) {
+    ColParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.W = g.W;
+    p.ny = g.ny;
+    p.nx = g.nx;
+    p.cols_total = g.n * g.W;
+    p.two_pi_over_Lx = 2.0 * M_PI / g.Lx;
+    p.two_pi_over_Ly = g.two_d ? 2.0 * M_PI / g.Ly : 0.0;
+    p.h0 = g.deep ? INFINITY : g.h0;
+    p.kx_keep = g.kx_keep;
+    p.ky_keep = g.ky_keep;
+    p.filt_kf = c->filter_on() ? c->opt.filt_beta1 * c->opt.k_ref : 0.0;
+    p.filt_beta2 = c->opt.filt_beta2;
+    p.nacc = nacc;
+    p.tw = c->tw;
+    const double scale = 1.0 / ((double)g.nx * g.ny);
+    size_t total_terms = 0;
+    for (auto& in : ins) total_terms += in.terms.size();
+    if (ins.size() + outs.size() > (size_t)kMaxColBufs || total_terms > (size_t)kMaxColTerms ||
+        outs.size() > (size_t)kMaxColOuts || nacc > kMaxColAcc) {
+      oom = true;
+      Pass ps{};
+      ps.kind = PK_COL;
+      return ps;
+    }
+    int nt = 0;
+    for (size_t i = 0; i < ins.size(); ++i) {
+      p.buf[i] = mref(ins[i].name);
+      p.term_begin[i] = nt;
+      for (auto t : ins[i].terms) {
+        t.in = (uint8_t)i;
+        t.c *= scale;
+        p.terms[nt++] = t;
+      }
+    }
+    p.nin = (int)ins.size();
+    p.term_begin[p.nin] = nt;
+    p.nterms = nt;
+    for (size_t o = 0; o < outs.size(); ++o) {
+      ColTerm t = outs[o].second;
+      t.in = (uint8_t)(p.nin + o);
+      p.buf[p.nin + o] = mref(outs[o].first);
+      p.outs[o] = t;
+    }
+    p.nouts = (int)outs.size();
+    Pass ps{};
+    ps.kind = PK_COL;
+    ps.nsize = g.ny;
+    ps.col = p;
+    ps.bytes = mixed_bytes() * (ins.size() + outs.size());
+    return ps;
+  }
+
+  std::vector<char> dims() const { return g.two_d ? std::vector<char>{'x', 'y'} : std::vector<char>{'x'}; }
+  static std::string S(const char* f, int a) { char b[64]; snprintf(b, 64, f, a); return b; }
+  static std::string S2(const char* f, int a, int b2) { char b[64]; snprintf(b, 64, f, a, b2); return b; }
+
+  static double fact(int n) { double f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+  // Col A: order 1 (Sec. 2.4) and the gradients of phi~ and eta.
+  Pass plan_col_a() {
+    const bool var = g.variable;
+    std::vector<ColIn> ins = {{"phi_m", {term(0, 1.0, 0, 0, 0, 0)}},
+                              {"eta_m", {term(1, 1.0, 0, 0, 0, 0)}}};
+    std::vector<std::pair<std::string, ColTerm>> outs;
+    outs.push_back({"V1", term(0, 1.0, 1, 1, 0, 0, 1)});  // k tanh(kh) phi^
+    for (char d : dims()) {
+      const int gx = d == 'x', gy = d == 'y';
+      outs.push_back({std::string("dphi") + d, term(0, 1.0, 0, 0, gx, gy, 1)});
+      outs.push_back({std::string("deta") + d, term(1, 1.0, 0, 0, gx, gy, 1)});
+      if (var) outs.push_back({std::string("db1") + d, term(0, 1.0, 0, 2, gx, gy, 1)});  // ik sech phi^
+    }
+    return col(ins, outs, 2);
+  }
+
+  // Row l: eager products of order l-1 (see file header).
+  Pass plan_row_level(int l) {
+    const int M = c->opt.order;
+    RowB r = row_begin();
+    c2r(r, 0, {S("V%d", l - 1)});
+    for (int j = 1; j <= M - (l - 1); ++j) prod(r, 0, j, 0, 0, 1.0, S2("P%d_%d", j, l - 1));
+    if (l == 2) {
+      for (char d : dims()) {
+        c2r(r, 0, {std::string("dphi") + d});
+        for (int j = 1; j <= M - 1; ++j) prod(r, 0, j, 0, 0, 1.0, S("Q%d", j) + d);
+      }
+    }
+    bool use_delta = false;
+    if (g.variable && l - 1 <= M - 1) {
+      const int m = l - 1;
+      for (char d : dims()) {
+        c2r(r, 0, {S("db%d", m) + d});
+        for (int j = 1; j <= M - m; ++j) {
+          const int ll = j + m;
+          if (ll <= M - 1 || (j % 2 == 1)) {
+            prod(r, 0, 0, j, 0, 1.0, S2("R%d_%d", j, m) + d);
+            use_delta = true;
+          }
+        }
+      }
+    }
+    return row_end(r, true, use_delta, false);
+  }
+
+  // Col l: F{V_l} (acc 0) and F{varphi_l} (acc 1) of Appendix C:
+  //  F{V_l}   = sum_j -k^j/j! T_j F{eta^j V_{l-j}} - T_l k^{l-2}/(l-1)! ik.F{eta^{l-1} grad phi~}
+  //             + sum_{j odd} k^{j-1}/j! sech ik.F{delta^j grad varphi_{l-j}}
+  //  F{varphi_l} = sum_{j odd} -k^{j-1}/j! sech F{eta^j V_{l-j}}
+  //             - [l odd] sech k^{l-3}/(l-1)! ik.F{eta^{l-1} grad phi~}
+  //             + sum_j (-1)^j k^{j-2}/j! T_j ik.F{delta^j grad varphi_{l-j}}
+  // with T_j = tanh(kh) for odd j and 1 for even j.
+  Pass plan_col_level(int l) {
+    const int M = c->opt.order;
+    const bool phi_out = g.variable && l <= M - 1;
+    std::vector<ColIn> ins;
+    for (int j = 1; j < l; ++j) {
+      ColIn in{S2("P%d_%d", j, l - j), {}};
+      in.terms.push_back(term(0, -1.0 / fact(j), j, (j % 2) ? 1 : 0, 0, 0));
+      if (phi_out && (j % 2 == 1)) in.terms.push_back(term(1, -1.0 / fact(j), j - 1, 2, 0, 0));
+      ins.push_back(in);
+    }
+    for (char d : dims()) {
+      const int gx = d == 'x', gy = d == 'y';
+      ColIn in{S("Q%d", l - 1) + d, {}};
+      in.terms.push_back(term(0, -1.0 / fact(l - 1), l - 2, (l % 2) ? 1 : 0, gx, gy));
+      if (phi_out && (l % 2 == 1)) in.terms.push_back(term(1, -1.0 / fact(l - 1), l - 3, 2, gx, gy));
+      ins.push_back(in);
+    }
+    if (g.variable) {
+      for (int j = 1; j < l; ++j) {
+        const bool to_v = (j % 2 == 1);
+        if (!to_v && !phi_out) continue;
+        for (char d : dims()) {
+          const int gx = d == 'x', gy = d == 'y';
+          ColIn in{S2("R%d_%d", j, l - j) + d, {}};
+          if (to_v) in.terms.push_back(term(0, 1.0 / fact(j), j - 1, 2, gx, gy));
+          if (phi_out) {
+            if (j == 1) in.terms.push_back(term(1, -1.0, -1, 1, gx, gy));
+            else if (j % 2) in.terms.push_back(term(1, -1.0 / fact(j), j - 2, 1, gx, gy));
+            else in.terms.push_back(term(1, 1.0 / fact(j), j - 2, 0, gx, gy));
+          }
+          ins.push_back(in);
+        }
+      }
+    }
+    std::vector<std::pair<std::string, ColTerm>> outs;
+    outs.push_back({S("V%d", l), term(0, 1.0, 0, 0, 0, 0, 1)});
+    if (phi_out) {
+      for (char d : dims())
+        outs.push_back({S("db%d", l) + d, term(1, 1.0, 0, 0, d == 'x', d == 'y', 1)});
+    }
+    return col(ins, outs, phi_out ? 2 : 1);
+  }
+
+  std::vector<std::string> v_names() const {
+    std::vector<std::string> v;
+    for (int l = 1; l <= c->opt.order; ++l) v.push_back(S("V%d", l));
+    return v;
+  }
+
+  void plan_diag(std::vector<Pass>& out) {
+    out.push_back(plan_col_a());
+    for (int l = 2; l <= c->opt.order; ++l) {
+      out.push_back(plan_row_level(l));
+      out.push_back(plan_col_level(l));
+    }
+  }
+
+  // Row RHS + Col RHS: phi~_t = M F^{-1}{F{N2} + nu ik/k^2 . F{w grad phi~}}
+  void plan_rhs(std::vector<Pass>& out) {
+    RowB r = row_begin();
+    c2r(r, 0, v_names(), g.Vphys);
+    int s = 1;
+    for (char d : dims()) c2r(r, s++, {std::string("deta") + d});
+    const int sphi = s;
+    for (char d : dims()) c2r(r, s++, {std::string("dphi") + d});
+    n2(r, 0, "N2");
+    const bool sponge = c->wgt != nullptr && c->opt.sponge_nu != 0.0;
+    if (sponge) {
+      int q = sphi;
+      for (char d : dims()) prod(r, q++, 0, 0, 1, 1.0, std::string("SP") + d);
+    }
+    out.push_back(row_end(r, true, false, sponge));
+    std::vector<ColIn> ins = {{"N2", {term(0, 1.0, 0, 0, 0, 0)}}};
+    if (sponge) {
+      for (char d : dims())
+        ins.push_back({std::string("SP") + d,
+                       {term(0, c->opt.sponge_nu, -2, 0, d == 'x', d == 'y')}});
+    }
+    out.push_back(col(ins, {{"phit", term(0, 1.0, 0, 0, 0, 0, 1)}}, 1));
+  }
+
+  Pass plan_rk(int mode, int stage, double dt, int tail) {
+    RkParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.mode = mode;
+    p.stage = stage;
+    p.tail = tail;
+    p.rows_total = g.n * g.ny;
+    p.ny = g.ny;
+    p.W = g.W;
+    p.dt = dt;
+    p.eta0 = dref(g.eta0);
+    p.phi0 = dref(g.phi0);
+    p.acc_eta = dref(g.acc_eta);
+    p.acc_phi = dref(g.acc_phi);
+    p.V = pref(g.Vphys);
+    p.phit = mref(mode == RK_CORRECT ? "Ce" : "phit");
+    p.corr_phi = mref("Cp");
+    p.eta_w = pref(g.eta_w);
+    p.eta_hat = mref("eta_m");
+    p.phi_hat = mref("phi_m");
+    p.nonfinite = c->d_flags;
+    p.tw = c->tw;
+    double b = phys64_bytes() * 2;  // read master
+    if (mode == RK_STAGE) {
+      b += mixed_bytes() + phys_bytes();                      // phi~_t, V
+      b += phys64_bytes() * 2 * ((stage > 1 ? 1 : 0) + (stage < 4 ? 1 : 0));  // sums
+      if (stage == 4) b += phys64_bytes() * 2;                 // write master
+    } else if (mode == RK_CORRECT) {
+      b += mixed_bytes() * 2 + phys64_bytes() * 2;
+    }
+    if (tail) b += phys_bytes() + 2 * mixed_bytes();
+    Pass ps{};
+    ps.kind = PK_RK;
+    ps.nsize = g.nx;
+    ps.rk = p;
+    ps.bytes = b;
+    return ps;
+  }
+
+  // (M Lambda - 1) correction of the FP64 state, applied through RK_CORRECT.
+  void plan_project(std::vector<Pass>& out, bool with_filter) {
+    out.push_back(plan_rk(RK_ENTRY, 0, 0.0, 1));
+    const int depth = with_filter ? 3 : 0;
+    out.push_back(col({{"eta_m", {term(0, 1.0, 0, 0, 0, 0)}}, {"phi_m", {term(1, 1.0, 0, 0, 0, 0)}}},
+                      {{"Ce", term(0, 1.0, 0, depth, 0, 0, 2)}, {"Cp", term(1, 1.0, 0, depth, 0, 0, 2)}},
+                      2));
+    out.push_back(plan_rk(RK_CORRECT, 0, 0.0, 1));
+  }
+
+  void plan_sum_v(std::vector<Pass>& out, bool eulerian) {
+    RowB r = row_begin();
+    c2r(r, 0, v_names(), g.Vphys);
+    if (eulerian) {
+      int s = 1;
+      for (char d : dims()) c2r(r, s++, {std::string("deta") + d});
+      for (char d : dims()) c2r(r, s++, {std::string("dphi") + d});
+      wdot(r, 0, g.wout);
+    }
+    out.push_back(row_end(r, false, false, false));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Execution
+// ---------------------------------------------------------------------------
+int launch_pass(sbi_ctx* c, const Pass& p, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (p.kind == PK_ROW) e = c->fp64 ? launch_row<double>(p.nsize, p.row, st) : launch_row<float>(p.nsize, p.row, st);
+  else if (p.kind == PK_COL) e = c->fp64 ? launch_col<double>(p.nsize, p.col, st) : launch_col<float>(p.nsize, p.col, st);
+  else e = c->fp64 ? launch_rk<double>(p.nsize, p.rk, st) : launch_rk<float>(p.nsize, p.rk, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return SBI_OK;
+}
+
+int run_passes(sbi_ctx* c, const std::vector<Pass>& ps, cudaStream_t st) {
+  for (auto& p : ps) {
+    int rc = launch_pass(c, p, st);
+    if (rc) return rc;
+  }
+  return SBI_OK;
+}
+
+std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
+  std::vector<Pass> all;
+  for (auto& g : c->groups) {
+    Planner pl{c, g};
+    for (int s = 1; s <= 4; ++s) {
+      pl.plan_diag(all);
+      pl.plan_rhs(all);
+      all.push_back(pl.plan_rk(RK_STAGE, s, dt, (s < 4 || !c->filter_on()) ? 1 : 0));
+    }
+    if (c->filter_on()) pl.plan_project(all, true);
+    if (pl.oom) *oom = true;
+  }
+  return all;
+}
+
+int family_of(const Pass& p) { return p.kind == PK_COL ? FAM_COL : (p.kind == PK_ROW ? FAM_ROW : FAM_RK); }
+
+void free_graphs(sbi_ctx* c) {
+  for (auto& ge : c->graphs) {
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    if (ge.graph) cudaGraphDestroy(ge.graph);
+  }
+  c->graphs.clear();
+  for (auto e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  c->ev_family.clear();
+}
+
+int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
+  for (auto& ge : c->graphs)
+    if (ge.dt == dt && ge.prof == c->prof) { *out = &ge; return SBI_OK; }
+  bool oom = false;
+  std::vector<Pass> ps = plan_step(c, dt, &oom);
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
+  CK(cudaStreamSynchronize(c->cap), "sync before capture");
+  CK(cudaStreamSynchronize(c->stream), "sync before capture");
+  if (c->prof) {
+    free_graphs(c);  // a profiled graph owns the event pairs
+    for (auto e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->ev_family.clear();
+    for (size_t i = 0; i < ps.size(); ++i) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a), "event");
+      CK(cudaEventCreate(&b), "event");
+      c->ev.push_back(a);
+      c->ev.push_back(b);
+      c->ev_family.push_back(family_of(ps[i]));
+    }
+  }
+  GraphEntry ge;
+  ge.dt = dt;
+  ge.prof = c->prof;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int rc = SBI_OK;
+  for (size_t i = 0; i < ps.size() && rc == SBI_OK; ++i) {
+    if (c->prof) cudaEventRecord(c->ev[2 * i], c->cap);
+    rc = launch_pass(c, ps[i], c->cap);
+    if (c->prof) cudaEventRecord(c->ev[2 * i + 1], c->cap);
+  }
+  cudaError_t e = cudaStreamEndCapture(c->cap, &ge.graph);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  CK(cudaGraphInstantiate(&ge.exec, ge.graph, 0), "graph instantiate");
+  ge.launches = (int)ps.size();
+  c->graphs.push_back(ge);
+  *out = &c->graphs.back();
+  return SBI_OK;
+}
+
+int check_member(sbi_ctx* c, int member) {
+  if (!c) return SBI_EINVAL;
+  if (member < 0 || member >= c->nmembers) return fail(c, SBI_EINVAL, "member %d out of range", member);
+  return SBI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_to_real(const double* __restrict__ src, T* __restrict__ dst, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = T(src[i]);
+}
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = double(src[i]);
+}
+
+// Partial sums of eta and 1/2 (phi V + g eta^2) over fixed chunks of one
+// member, each chunk reduced by one block in a fixed tree order.
+template <typename T>
+__global__ void k_invariant_partials(const double* __restrict__ eta, const double* __restrict__ phi,
+                                     const T* __restrict__ V, long long n, double g, int chunk,
+                                     double* __restrict__ out) {
+  __shared__ double sm[2][256];
+  const long long base = (long long)blockIdx.x * chunk;
+  double m = 0.0, e = 0.0;
+  for (int i = threadIdx.x; i < chunk; i += blockDim.x) {
+    const long long q = base + i;
+    if (q < n) {
+      const double h = eta[q];
+      m += h;
+      e += 0.5 * (phi[q] * double(V[q]) + g * h * h);
+    }
+  }
+  sm[0][threadIdx.x] = m;
+  sm[1][threadIdx.x] = e;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = sm[0][0];
+    out[2 * blockIdx.x + 1] = sm[1][0];
+  }
+}
+
+int run_diag(sbi_ctx* c, int gi, bool eulerian) {
+  std::vector<Pass> ps;
+  Planner pl{c, c->groups[gi]};
+  pl.plan_diag(ps);
+  pl.plan_sum_v(ps, eulerian);
+  if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  CK(cudaStreamSynchronize(c->cap), "sync");
+  return run_passes(c, ps, c->stream);
+}
+
+int init_group(sbi_ctx* c, Group& g) {
+  const size_t np = g.phys_elems() * g.n;
+  g.eta0 = (double*)dalloc(c, np * 8);
+  g.phi0 = (double*)dalloc(c, np * 8);
+  g.acc_eta = (double*)dalloc(c, np * 8);
+  g.acc_phi = (double*)dalloc(c, np * 8);
+  g.eta_w = dalloc(c, np * c->real_size);
+  g.Vphys = dalloc(c, np * c->real_size);
+  g.wout = dalloc(c, np * c->real_size);
+  g.out64 = (double*)dalloc(c, g.phys_elems() * 8);
+  g.d_active = (int*)dalloc(c, (size_t)g.n * sizeof(int));
+  if (!g.eta0 || !g.phi0 || !g.acc_eta || !g.acc_phi || !g.eta_w || !g.Vphys || !g.wout ||
+      !g.out64 || !g.d_active)
+    return fail(c, SBI_ENOMEM, "device allocation failed");
+  return SBI_OK;
+}
+
+template <typename T>
+std::vector<T> to_real(const std::vector<double>& v) {
+  std::vector<T> r(v.size());
+  for (size_t i = 0; i < v.size(); ++i) r[i] = T(v[i]);
+  return r;
+}
+
+int upload_real(sbi_ctx* c, void* dst, const std::vector<double>& v, size_t offset_elems) {
+  if (c->fp64) {
+    CK(cudaMemcpyAsync((double*)dst + offset_elems, v.data(), v.size() * 8, cudaMemcpyHostToDevice, c->cap), "upload");
+  } else {
+    std::vector<float> f = to_real<float>(v);
+    CK(cudaMemcpyAsync((float*)dst + offset_elems, f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->cap), "upload");
+    CK(cudaStreamSynchronize(c->cap), "upload sync");
+  }
+  CK(cudaStreamSynchronize(c->cap), "upload sync");
+  return SBI_OK;
+}
+
+int create_impl(int n, const sbi_grid* grids, double gravity, const double* const* h,
+                const sbi_options* opt_in, sbi_ctx** out) {
+  if (!out) return fail(nullptr, SBI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !grids) return fail(nullptr, SBI_EINVAL, "need at least one grid");
+  sbi_options opt;
+  sbi_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.order < 1 || opt.order > 7) return fail(nullptr, SBI_EINVAL, "order %d outside 1..7", opt.order);
+  if (!(opt.alias_frac > 0.0 && opt.alias_frac <= 1.0))
+    return fail(nullptr, SBI_EINVAL, "alias_frac must be in (0, 1]");
+  if (!(gravity > 0.0) || !std::isfinite(gravity)) return fail(nullptr, SBI_EINVAL, "gravity must be > 0");
+  if (opt.precision != SBI_FP32 && opt.precision != SBI_FP64)
+    return fail(nullptr, SBI_EINVAL, "precision must be SBI_FP32 or SBI_FP64");
+  if (opt.filt_beta1 > 0.0 && !(opt.k_ref > 0.0 && opt.filt_beta2 > 0.0))
+    return fail(nullptr, SBI_EINVAL, "filter needs k_ref > 0 and beta2 > 0");
+  if (opt.adapt_tol < 0.0) return fail(nullptr, SBI_EINVAL, "adapt_tol must be >= 0");
+  if ((opt.dev_alloc == nullptr) != (opt.dev_free == nullptr))
+    return fail(nullptr, SBI_EINVAL, "dev_alloc and dev_free must be given together");
+  for (int i = 0; i < n; ++i) {
+    const sbi_grid& g = grids[i];
+    if (!is_pow2(g.nx) || g.nx < 16 || g.nx > 4096)
+      return fail(nullptr, SBI_EINVAL, "grid %d: nx=%d must be a power of two in [16, 4096]", i, g.nx);
+    if (!(g.ny == 1 || (is_pow2(g.ny) && g.ny >= 8 && g.ny <= 2048)))
+      return fail(nullptr, SBI_EINVAL, "grid %d: ny=%d must be 1 or a power of two in [8, 2048]", i, g.ny);
+    if (!(g.Lx > 0.0) || (g.ny > 1 && !(g.Ly > 0.0)))
+      return fail(nullptr, SBI_EINVAL, "grid %d: box lengths must be > 0", i);
+  }
+  if (opt.sponge_w) {
+    for (int i = 1; i < n; ++i)
+      if (grids[i].nx != grids[0].nx || grids[i].ny != grids[0].ny)
+        return fail(nullptr, SBI_EINVAL, "a sponge weight needs every member on one grid");
+  }
+
+  sbi_ctx* c = new sbi_ctx();
+  c->opt = opt;
+  c->gravity = gravity;
+  c->fp64 = opt.precision == SBI_FP64;
+  c->real_size = c->fp64 ? 8 : 4;
+  c->nmembers = n;
+  c->stream = (cudaStream_t)opt.cuda_stream;
+  auto bail = [&](int rc) {
+    g_create_error = c->err;
+    sbi_destroy(c);
+    return rc;
+  };
+  // depth per member
+  std::vector<double> h0s(n);
+  std::vector<bool> var(n, false);
+  std::vector<std::vector<double>> deltas(n);
+  for (int i = 0; i < n; ++i) {
+    const sbi_grid& g = grids[i];
+    const size_t np = (size_t)g.nx * g.ny;
+    const double* hi = h ? h[i] : nullptr;
+    double h0 = opt.h0;
+    if (!hi) {
+      if (std::isnan(h0) || !(h0 > 0.0)) {
+        c->err = "a flat member needs opt.h0 > 0 (or INFINITY)";
+        return bail(SBI_EINVAL);
+      }
+    } else {
+      double sum = 0.0;
+      for (size_t q = 0; q < np; ++q) {
+        if (!(hi[q] > 0.0) || !std::isfinite(hi[q])) {
+          c->err = "depth h must be finite and > 0";
+          return bail(SBI_EINVAL);
+        }
+        sum += hi[q];
+      }
+      if (std::isnan(h0)) h0 = sum / (double)np;
+      if (!(h0 > 0.0) || !std::isfinite(h0)) {
+        c->err = "reference depth h0 must be finite and > 0 with a depth field";
+        return bail(SBI_EINVAL);
+      }
+      deltas[i].resize(np);
+      for (size_t q = 0; q < np; ++q) {
+        deltas[i][q] = h0 - hi[q];
+        if (deltas[i][q] != 0.0) var[i] = true;
+      }
+    }
+    h0s[i] = h0;
+  }
+
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cannot create a CUDA stream (no usable device?)";
+    return bail(SBI_ECUDA);
+  }
+
+  // group members with identical grids and depth settings
+  c->where.resize(n);
+  for (int i = 0; i < n; ++i) {
+    int gi = -1;
+    for (size_t q = 0; q < c->groups.size(); ++q) {
+      Group& g = c->groups[q];
+      if (g.nx == grids[i].nx && g.ny == grids[i].ny && g.Lx == grids[i].Lx &&
+          (grids[i].ny == 1 || g.Ly == grids[i].Ly) && g.h0 == h0s[i] && g.variable == var[i]) {
+        gi = (int)q;
+        break;
+      }
+    }
+    if (gi < 0) {
+      Group g;
+      g.nx = grids[i].nx;
+      g.ny = grids[i].ny;
+      g.Lx = grids[i].Lx;
+      g.Ly = grids[i].ny > 1 ? grids[i].Ly : 1.0;
+      g.h0 = h0s[i];
+      g.deep = std::isinf(h0s[i]);
+      g.variable = var[i];
+      g.two_d = g.ny > 1;
+      const double A = opt.alias_frac * g.nx / 2.0, B = opt.alias_frac * g.ny / 2.0;
+      g.kx_keep = std::min((int)std::ceil(A - 1e-12), g.nx / 2);
+      g.ky_keep = g.ny == 1 ? 1 : std::min((int)std::ceil(B - 1e-12), g.ny / 2);
+      g.kx_keep = std::max(g.kx_keep, 1);
+      g.ky_keep = std::max(g.ky_keep, 1);
+      g.W = g.kx_keep;
+      c->groups.push_back(g);
+      gi = (int)c->groups.size() - 1;
+    }
+    c->where[i] = {gi, (int)c->groups[gi].members.size()};
+    c->groups[gi].members.push_back(i);
+  }
+  for (auto& g : c->groups) g.n = (int)g.members.size();
+
+  // twiddles exp(-2 pi i j / N) for N = 2..8192 in the working precision
+  {
+    const int tot = 8192 * 2 - 2;
+    std::vector<double> re(tot), im(tot);
+    for (int N = 2; N <= 8192; N *= 2)
+      for (int j = 0; j < N; ++j) {
+        const double a = -2.0 * M_PI * (double)j / (double)N;
+        re[N - 2 + j] = std::cos(a);
+        im[N - 2 + j] = std::sin(a);
+      }
+    c->tw = dalloc(c, (size_t)tot * 2 * c->real_size);
+    if (!c->tw) { c->err = "device allocation failed"; return bail(SBI_ENOMEM); }
+    std::vector<double> inter(2 * (size_t)tot);
+    for (int q = 0; q < tot; ++q) { inter[2 * q] = re[q]; inter[2 * q + 1] = im[q]; }
+    if (upload_real(c, c->tw, inter, 0)) return bail(SBI_ECUDA);
+  }
+  c->d_flags = (int*)dalloc(c, 64);
+  if (!c->d_flags) { c->err = "device allocation failed"; return bail(SBI_ENOMEM); }
+
+  for (auto& g : c->groups) {
+    cudaError_t e = c->fp64 ? prepare_row_kernels<double>(g.nx) : prepare_row_kernels<float>(g.nx);
+    if (e == cudaSuccess) e = c->fp64 ? prepare_col_kernels<double>(g.ny) : prepare_col_kernels<float>(g.ny);
+    if (e != cudaSuccess) { cuda_fail(c, e, "kernel setup"); return bail(SBI_ECUDA); }
+    int rc = init_group(c, g);
+    if (rc) return bail(rc);
+    if (g.variable) {
+      g.delta = dalloc(c, g.phys_elems() * g.n * c->real_size);
+      if (!g.delta) { c->err = "device allocation failed"; return bail(SBI_ENOMEM); }
+    }
+  }
+  // bathymetry
+  for (int i = 0; i < n; ++i) {
+    Group& g = c->groups[c->where[i].first];
+    if (g.variable) {
+      if (upload_real(c, g.delta, deltas[i], (size_t)c->where[i].second * g.phys_elems()))
+        return bail(SBI_ECUDA);
+    }
+  }
+  if (opt.sponge_w && opt.sponge_nu != 0.0) {
+    const size_t np = (size_t)grids[0].nx * grids[0].ny;
+    std::vector<double> w(opt.sponge_w, opt.sponge_w + np);
+    c->wgt = dalloc(c, np * c->real_size);
+    if (!c->wgt) { c->err = "device allocation failed"; return bail(SBI_ENOMEM); }
+    if (upload_real(c, c->wgt, w, 0)) return bail(SBI_ECUDA);
+  }
+  c->opt.sponge_w = nullptr;  // the host array is not kept
+  c->orders_used.assign(n, opt.order);
+  // working copies of the zero state
+  for (auto& g : c->groups) {
+    Planner pl{c, g};
+    std::vector<Pass> ps;
+    ps.push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
+    if (pl.oom) { c->err = "device allocation failed"; return bail(SBI_ENOMEM); }
+    if (run_passes(c, ps, c->cap)) return bail(SBI_ECUDA);
+  }
+  if (cudaStreamSynchronize(c->cap) != cudaSuccess) {
+    cuda_fail(c, cudaGetLastError(), "create");
+    return bail(SBI_ECUDA);
+  }
+  *out = c;
+  return SBI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void sbi_default_options(sbi_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->order = 7;
+  opt->alias_frac = 0.5;
+  opt->h0 = NAN;
+  opt->precision = SBI_FP32;
+  opt->adapt_tol = 0.0;
+  opt->filt_beta1 = 0.0;
+  opt->filt_beta2 = 0.0;
+  opt->k_ref = 1.0;
+  opt->sponge_w = nullptr;
+  opt->sponge_nu = 0.0;
+  opt->cuda_stream = nullptr;
+  opt->check_finite = 1;
+  opt->set_state_dealias = 1;
+}
+
+int sbi_create(const sbi_grid* g, double gravity, const double* h, const sbi_options* opt,
+               sbi_ctx** out) {
+  if (!g) return fail(nullptr, SBI_EINVAL, "grid is NULL");
+  const double* hs[1] = {h};
+  return create_impl(1, g, gravity, hs, opt, out);
+}
+
+int sbi_create_batch(int n, const sbi_grid* grids, double gravity, const double* const* h,
+                     const sbi_options* opt, sbi_ctx** out) {
+  return create_impl(n, grids, gravity, h, opt, out);
+}
+
+int sbi_num_members(const sbi_ctx* ctx) { return ctx ? ctx->nmembers : 0; }
+
+int sbi_set_state(sbi_ctx* c, int member, const double* eta, const double* phi, int on_device) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
+  Group& g = c->groups[c->where[member].first];
+  const size_t off = (size_t)c->where[member].second * g.phys_elems();
+  const size_t bytes = g.phys_elems() * 8;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaMemcpyAsync(g.eta0 + off, eta, bytes, kind, c->cap), "copy eta");
+  CK(cudaMemcpyAsync(g.phi0 + off, phi, bytes, kind, c->cap), "copy phi");
+  // dealias the stored state of this member only: (M - 1) correction; then
+  // refresh this member's working copies
+  std::vector<int> act(g.n, 0);
+  act[c->where[member].second] = 1;
+  CK(cudaMemcpyAsync(g.d_active, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, c->cap), "active");
+  Planner pl{c, g};
+  std::vector<Pass> ps;
+  if (c->opt.set_state_dealias) pl.plan_project(ps, false);
+  else ps.push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
+  if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  for (auto& p : ps) {
+    if (p.kind == PK_ROW) p.row.active = g.d_active;
+    else if (p.kind == PK_COL) p.col.active = g.d_active;
+    else p.rk.active = g.d_active;
+  }
+  rc = run_passes(c, ps, c->cap);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->cap), "set_state");
+  return SBI_OK;
+}
+
+int sbi_get_state(sbi_ctx* c, int member, double* eta, double* phi, int on_device) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
+  Group& g = c->groups[c->where[member].first];
+  const size_t off = (size_t)c->where[member].second * g.phys_elems();
+  const size_t bytes = g.phys_elems() * 8;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(eta, g.eta0 + off, bytes, kind, c->stream), "copy eta");
+  CK(cudaMemcpyAsync(phi, g.phi0 + off, bytes, kind, c->stream), "copy phi");
+  CK(cudaStreamSynchronize(c->stream), "get_state");
+  return SBI_OK;
+}
+
+int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, int eulerian_w) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!V_out) return fail(c, SBI_EINVAL, "V_out is NULL");
+  const int gi = c->where[member].first;
+  Group& g = c->groups[gi];
+  rc = run_diag(c, gi, eulerian_w != 0);
+  if (rc) return rc;
+  const size_t np = g.phys_elems();
+  const size_t off = (size_t)c->where[member].second * np;
+  void* src = eulerian_w ? g.wout : g.Vphys;
+  double* dst = on_device ? V_out : g.out64;
+  const int thr = 256;
+  const long long blocks = ((long long)np + thr - 1) / thr;
+  if (c->fp64) k_to_double<double><<<(unsigned)blocks, thr, 0, c->stream>>>((const double*)src + off, dst, (long long)np);
+  else k_to_double<float><<<(unsigned)blocks, thr, 0, c->stream>>>((const float*)src + off, dst, (long long)np);
+  CK(cudaGetLastError(), "convert");
+  if (!on_device)
+    CK(cudaMemcpyAsync(V_out, g.out64, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy V");
+  CK(cudaStreamSynchronize(c->stream), "vertical_velocity");
+  return SBI_OK;
+}
+
+int sbi_step(sbi_ctx* c, double dt, int n) {
+  if (!c) return SBI_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
+  if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
+  if (n == 0) return SBI_OK;
+  GraphEntry* ge = nullptr;
+  int rc = get_step_graph(c, dt, &ge);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    if (c->prof) {
+      // the graph's event pairs hold this replay's per-pass device times
+      CK(cudaStreamSynchronize(c->stream), "profile sync");
+      for (size_t q = 0; q < c->ev_family.size(); ++q) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * q], c->ev[2 * q + 1]), "event time");
+        c->prof_ms[c->ev_family[q]] += ms;
+        c->prof_launches[c->ev_family[q]] += 1;
+      }
+    }
+  }
+  if (c->opt.check_finite) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+    CK(cudaStreamSynchronize(c->stream), "step");
+    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
+  }
+  return SBI_OK;
+}
+
+int sbi_invariants(sbi_ctx* c, int member, double* mass, double* energy) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!mass || !energy) return fail(c, SBI_EINVAL, "mass and energy must not be NULL");
+  const int gi = c->where[member].first;
+  Group& g = c->groups[gi];
+  rc = run_diag(c, gi, false);
+  if (rc) return rc;
+  const long long np = (long long)g.phys_elems();
+  const size_t off = (size_t)c->where[member].second * np;
+  const int chunk = 8192;
+  const int nchunks = (int)((np + chunk - 1) / chunk);
+  if ((size_t)nchunks * 2 > c->partial_cap) {
+    void* p = dalloc(c, (size_t)nchunks * 2 * 8);
+    if (!p) return fail(c, SBI_ENOMEM, "device allocation failed");
+    c->d_partials = (double*)p;
+    c->partial_cap = (size_t)nchunks * 2;
+  }
+  if (c->fp64)
+    k_invariant_partials<double><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const double*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
+  else
+    k_invariant_partials<float><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const float*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
+  CK(cudaGetLastError(), "invariants");
+  std::vector<double> part((size_t)nchunks * 2);
+  CK(cudaMemcpyAsync(part.data(), c->d_partials, part.size() * 8, cudaMemcpyDeviceToHost, c->stream), "copy partials");
+  CK(cudaStreamSynchronize(c->stream), "invariants");
+  double m = 0.0, e = 0.0;
+  for (int q = 0; q < nchunks; ++q) { m += part[2 * q]; e += part[2 * q + 1]; }
+  const double dA = (g.Lx / g.nx) * (g.Ly / g.ny);
+  *mass = m * dA;
+  *energy = e * dA;
+  return SBI_OK;
+}
+
+int sbi_orders_used(sbi_ctx* c, int member, int* orders) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!orders) return fail(c, SBI_EINVAL, "orders is NULL");
+  *orders = c->orders_used[member];
+  return SBI_OK;
+}
+
+int sbi_profile_enable(sbi_ctx* c, int on) {
+  if (!c) return SBI_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_graphs(c);
+  c->prof = on != 0;
+  c->prof_ms.assign(FAM_COUNT, 0.0);
+  c->prof_launches.assign(FAM_COUNT, 0);
+  return SBI_OK;
+}
+
+int sbi_profile_read(sbi_ctx* c, int cap, const char** names, long long* launches, double* total_ms,
+                     int* count) {
+  if (!c || !count) return SBI_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "profile sync");
+  *count = FAM_COUNT;
+  for (int i = 0; i < FAM_COUNT && i < cap; ++i) {
+    if (names) names[i] = kFamilyNames[i];
+    if (launches) launches[i] = i < (int)c->prof_launches.size() ? c->prof_launches[i] : 0;
+    if (total_ms) total_ms[i] = i < (int)c->prof_ms.size() ? c->prof_ms[i] : 0.0;
+  }
+  return SBI_OK;
+}
+
+int sbi_step_bytes(const sbi_ctx* cc, int family, double* bytes) {
+  sbi_ctx* c = const_cast<sbi_ctx*>(cc);
+  if (!c || !bytes) return SBI_EINVAL;
+  bool oom = false;
+  std::vector<Pass> ps = plan_step(c, 1.0, &oom);
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  double b = 0.0;
+  for (auto& p : ps)
+    if (family < 0 || family_of(p) == family) b += p.bytes;
+  *bytes = b;
+  return SBI_OK;
+}
+
+int sbi_step_launches(const sbi_ctx* cc, int* launches) {
+  sbi_ctx* c = const_cast<sbi_ctx*>(cc);
+  if (!c || !launches) return SBI_EINVAL;
+  bool oom = false;
+  std::vector<Pass> ps = plan_step(c, 1.0, &oom);
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  *launches = (int)ps.size();
+  return SBI_OK;
+}
+
+const char* sbi_last_error(const sbi_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void sbi_destroy(sbi_ctx* c) {
+  if (!c) return;
+  if (c->cap) cudaStreamSynchronize(c->cap);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_graphs(c);
+  for (void* p : c->allocs) {
+    if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
+    else cudaFree(p);
+  }
+  c->allocs.clear();
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+}  // extern "C"

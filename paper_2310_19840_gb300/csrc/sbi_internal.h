@@ -1,0 +1,133 @@
+// sbi_internal.h - pass descriptors shared by the host planner and the kernels.
+//
+// One right-hand-side evaluation of the ESBI scheme is a chain of "row" and
+// "column" passes over each member's fields.  Between passes a field lives in
+// one of three layouts:
+//   physical  ny x nx reals (x fastest);
+//   mixed     ny x W complex: FFT along x only, keeping the W = ceil(alpha nx/2)
+//             non-negative x-modes that survive the dealias mask (the Nyquist
+//             and all higher x-modes are zero by construction), y physical;
+//   (spectral values exist only inside a column pass).
+// A row pass turns mixed rows into physical ones (inverse real FFT along x),
+// forms pointwise products, and turns them back into mixed rows (forward real
+// FFT).  A column pass transforms mixed columns along y, applies per-mode
+// multipliers k^p D(k) (i kx)^gx (i ky)^gy with D in {1, tanh(k h0),
+// sech(k h0), Lambda(k)} and sums them into accumulators, masks, and
+// transforms the outputs back along y.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace sbi {
+
+constexpr int kMaxRowOps = 48;
+constexpr int kMaxRowBufs = 40;
+constexpr int kMaxColTerms = 48;
+constexpr int kMaxColOuts = 8;
+constexpr int kMaxColBufs = 32;
+constexpr int kMaxColAcc = 2;
+constexpr int kMaxSlots = 5;
+constexpr uint8_t kNone = 255;
+
+enum RowOpKind : uint8_t {
+  ROP_C2R = 0,   // slot <- c2r(sum of mixed bufs [a, a+b)); optional physical copy to dst
+  ROP_PROD = 1,  // mixed dst <- r2c(coef * eta^a * delta^b * w^c * slot)   (slot kNone: 1)
+  ROP_N2 = 2,    // mixed dst <- r2c(dynamic-condition right-hand side) from slots
+                 // slot..slot+4 = V, eta_x, eta_y, phi_x, phi_y (2-D) or
+                 // V, eta_x, phi_x (1-D); coef = gravity
+  ROP_WDOT = 3,  // physical dst <- w-free Eulerian vertical velocity
+                 // (V + grad eta.grad phi)/(1+|grad eta|^2) from the same slots
+};
+
+struct RowOp {
+  uint8_t kind;
+  uint8_t slot;
+  uint8_t a;
+  uint8_t b;
+  uint8_t c;
+  uint8_t dst;
+  uint16_t pad_;
+  float coef;
+};
+
+struct BufRef {
+  void* ptr;
+  long long stride;   // elements (reals for physical, complex for mixed) between members
+};
+
+struct RowParams {
+  int nops;
+  int rows_total;       // members * ny
+  int ny;
+  int W;
+  int nslots;
+  int member0;          // first member of this launch within the group (for convergence flags)
+  const int* active;    // per-member flag (nullptr: all active); inactive members skip the pass
+  BufRef eta, delta, wgt;        // physical fields (ptr may be null)
+  BufRef buf[kMaxRowBufs];
+  RowOp ops[kMaxRowOps];
+  const void* tw;
+};
+
+struct ColTerm {
+  uint8_t in;     // input buffer (local index); for outputs: destination buffer
+  uint8_t acc;    // accumulator index
+  uint8_t gx, gy; // powers of (i kx), (i ky)
+  int8_t kpow;    // power of |k| (negative powers vanish at k = 0)
+  uint8_t depth;  // 0: 1, 1: tanh(k h0), 2: sech(k h0), 3: Lambda(k) = exp(-(k/kf)^beta2)
+  uint8_t mask;   // outputs: 1 multiplies by the dealias mask, 2 by (mask - 1) (projection correction)
+  uint8_t pad_;
+  double c;
+};
+
+struct ColParams {
+  int nin, nterms, nouts, nacc;
+  int W, ny, nx;
+  int cols_total;           // members * W
+  int member0;
+  const int* active;
+  double two_pi_over_Lx, two_pi_over_Ly, h0;
+  int kx_keep, ky_keep;     // keep m < kx_keep and |n| < ky_keep
+  double filt_kf, filt_beta2;
+  double* norm_out;         // optional per-member FP64 partial norms of accumulator 0 (nullptr: off)
+  int term_begin[kMaxColBufs + 1];   // terms sorted by input
+  ColTerm terms[kMaxColTerms];
+  ColTerm outs[kMaxColOuts];
+  BufRef buf[kMaxColBufs];
+  const void* tw;
+};
+
+enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2 };
+
+struct RkParams {
+  const int* active;    // per-member flag (nullptr: all members)
+  int mode;             // RkMode
+  int stage;            // 1..4 for RK_STAGE
+  int tail;             // 1: write the next stage's working copies (eta_w, mixed eta^, phi^)
+  int rows_total, ny, W;
+  double dt;
+  BufRef eta0, phi0;    // FP64 master state
+  BufRef acc_eta, acc_phi;      // FP64 RK4 sums
+  BufRef V;             // physical V of this stage (T)
+  BufRef phit;          // mixed phi~_t of this stage (T complex)  / RK_CORRECT: eta correction
+  BufRef corr_phi;      // RK_CORRECT: phi correction (mixed)
+  BufRef eta_w;         // physical working eta (T)
+  BufRef eta_hat, phi_hat;      // mixed working spectra (T complex)
+  int* nonfinite;       // set to 1 when the new state holds NaN/Inf
+  const void* tw;
+};
+
+// Launchers (one instantiation per real type and size, selected at run time).
+// prepare_kernels sets the dynamic shared-memory limits of every kernel a
+// grid of nx x ny uses; it must run once (outside stream capture) before the
+// first launch.  Unsupported sizes return cudaErrorInvalidValue.
+template <typename T> cudaError_t prepare_row_kernels(int nx);
+template <typename T> cudaError_t prepare_col_kernels(int ny);
+template <typename T> cudaError_t launch_row(int nx, const RowParams& p, cudaStream_t st);
+template <typename T> cudaError_t launch_col(int ny, const ColParams& p, cudaStream_t st);
+template <typename T> cudaError_t launch_rk(int nx, const RkParams& p, cudaStream_t st);
+template <typename T> size_t row_smem_bytes(int nx, int nslots);
+
+}  // namespace sbi

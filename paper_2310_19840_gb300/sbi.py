@@ -1,0 +1,237 @@
+"""Python binding of the C ABI in include/sbi.h (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libsbi.so``; importing this
+module fails loudly when the library has not been built.  The functions carry
+the C names (sbi_create, sbi_set_state, sbi_vertical_velocity, sbi_step,
+sbi_invariants, ...); ``Context`` wraps them for numpy arrays and torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SBI_OK, SBI_EINVAL, SBI_ENOMEM, SBI_ECUDA, SBI_ENONFINITE, SBI_ENOTCONVERGED, SBI_ETIMEOUT = range(7)
+SBI_FP32, SBI_FP64 = 0, 1
+
+
+class SbiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sbi error {code}: {msg}")
+        self.code = code
+
+
+class sbi_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class sbi_options(C.Structure):
+    _fields_ = [("order", C.c_int), ("alias_frac", C.c_double), ("h0", C.c_double),
+                ("precision", C.c_int), ("adapt_tol", C.c_double),
+                ("filt_beta1", C.c_double), ("filt_beta2", C.c_double), ("k_ref", C.c_double),
+                ("sponge_w", C.POINTER(C.c_double)), ("sponge_nu", C.c_double),
+                ("cuda_stream", C.c_void_p), ("check_finite", C.c_int),
+                ("set_state_dealias", C.c_int),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+EXPORTS = {
+    "sbi_default_options": (None, [C.POINTER(sbi_options)]),
+    "sbi_create": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.POINTER(C.c_double),
+                             C.POINTER(sbi_options), C.POINTER(C.c_void_p)]),
+    "sbi_create_batch": (C.c_int, [C.c_int, C.POINTER(sbi_grid), C.c_double,
+                                   C.POINTER(C.POINTER(C.c_double)), C.POINTER(sbi_options),
+                                   C.POINTER(C.c_void_p)]),
+    "sbi_num_members": (C.c_int, [C.c_void_p]),
+    "sbi_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "sbi_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "sbi_vertical_velocity": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sbi_orders_used": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "sbi_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbi_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
+                                   C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int)]),
+    "sbi_step_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "sbi_step_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sbi_last_error": (C.c_char_p, [C.c_void_p]),
+    "sbi_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    """Load libsbi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> sbi_options:
+    o = sbi_options()
+    load().sbi_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "sponge_w":
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a, dtype=np.float64):
+    """(address, on_device, keepalive) of a numpy array or torch tensor of float64."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError("torch tensors must be contiguous float64")
+            return a.data_ptr(), 1 if a.is_cuda else 0, a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr
+
+
+class Context:
+    """Owner of one sbi_ctx (one member or a batch of members)."""
+
+    def __init__(self, grids, gravity, depths=None, *, h0=math.nan, order=7, alias_frac=0.5,
+                 precision=SBI_FP32, adapt_tol=0.0, filt_beta1=0.0, filt_beta2=0.0, k_ref=1.0,
+                 sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1):
+        self.lib = load()
+        if isinstance(grids, tuple):
+            grids = [grids]
+        self.grids = [tuple(g) for g in grids]
+        n = len(self.grids)
+        opt = default_options(order=order, alias_frac=alias_frac, h0=h0, precision=precision,
+                              adapt_tol=adapt_tol, filt_beta1=filt_beta1, filt_beta2=filt_beta2,
+                              k_ref=k_ref, sponge_nu=sponge_nu, check_finite=check_finite,
+                              set_state_dealias=set_state_dealias)
+        keep = []
+        if sponge_w is not None:
+            w = np.ascontiguousarray(sponge_w, dtype=np.float64).ravel()
+            keep.append(w)
+            opt.sponge_w = w.ctypes.data_as(C.POINTER(C.c_double))
+        if stream is not None:
+            opt.cuda_stream = C.c_void_p(int(stream))
+        garr = (sbi_grid * n)(*[sbi_grid(g[0], g[1], g[2], g[3] if len(g) > 3 else 1.0)
+                                for g in self.grids])
+        harr = (C.POINTER(C.c_double) * n)()
+        if depths is not None:
+            if not isinstance(depths, (list, tuple)):
+                depths = [depths]
+            for i, d in enumerate(depths):
+                if d is None:
+                    continue
+                a = np.ascontiguousarray(d, dtype=np.float64).ravel()
+                keep.append(a)
+                harr[i] = a.ctypes.data_as(C.POINTER(C.c_double))
+        out = C.c_void_p()
+        rc = self.lib.sbi_create_batch(n, garr, gravity, harr, C.byref(opt), C.byref(out))
+        if rc != SBI_OK:
+            raise SbiError(rc, self.lib.sbi_last_error(None).decode())
+        self.ctx = out
+        self.precision = precision
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc):
+        if rc != SBI_OK:
+            raise SbiError(rc, self.lib.sbi_last_error(self.ctx).decode())
+
+    def shape(self, member=0):
+        g = self.grids[member]
+        return (g[1], g[0])
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.sbi_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI ------------------------------------------------------------------
+    def set_state(self, member, eta, phi):
+        pe, de, ke = _ptr(eta)
+        pp, dp, kp = _ptr(phi)
+        if de != dp:
+            raise ValueError("eta and phi must both be host or both be device buffers")
+        self._check(self.lib.sbi_set_state(self.ctx, member, pe, pp, de))
+
+    def get_state(self, member, eta=None, phi=None):
+        if eta is None:
+            eta = np.empty(self.shape(member))
+            phi = np.empty(self.shape(member))
+        pe, de, _ = _ptr(eta)
+        pp, dp, _ = _ptr(phi)
+        self._check(self.lib.sbi_get_state(self.ctx, member, pe, pp, de))
+        return eta, phi
+
+    def vertical_velocity(self, member=0, out=None, eulerian_w=False):
+        if out is None:
+            out = np.empty(self.shape(member))
+        po, do, _ = _ptr(out)
+        self._check(self.lib.sbi_vertical_velocity(self.ctx, member, po, do, int(eulerian_w)))
+        return out
+
+    def step(self, dt, n=1):
+        self._check(self.lib.sbi_step(self.ctx, float(dt), int(n)))
+
+    def invariants(self, member=0):
+        m, e = C.c_double(), C.c_double()
+        self._check(self.lib.sbi_invariants(self.ctx, member, C.byref(m), C.byref(e)))
+        return m.value, e.value
+
+    def orders_used(self, member=0):
+        o = C.c_int()
+        self._check(self.lib.sbi_orders_used(self.ctx, member, C.byref(o)))
+        return o.value
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.sbi_profile_enable(self.ctx, int(on)))
+
+    def profile_read(self):
+        cap = 8
+        names = (C.c_char_p * cap)()
+        launches = (C.c_longlong * cap)()
+        ms = (C.c_double * cap)()
+        cnt = C.c_int()
+        self._check(self.lib.sbi_profile_read(self.ctx, cap, names, launches, ms, C.byref(cnt)))
+        return [(names[i].decode(), launches[i], ms[i]) for i in range(cnt.value)]
+
+    def step_bytes(self, family=-1):
+        b = C.c_double()
+        self._check(self.lib.sbi_step_bytes(self.ctx, family, C.byref(b)))
+        return b.value
+
+    def step_launches(self):
+        n = C.c_int()
+        self._check(self.lib.sbi_step_launches(self.ctx, C.byref(n)))
+        return n.value

@@ -1,0 +1,165 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the FP32 path must reach 1e-5 relative L2 on V after one
+evaluation; the FP64 path 1e-11 (FFT round-off grows like eps log N and the
+order-7 terms multiply it by at most a few hundred at these amplitudes).
+Inputs are seeded band-limited fields shaped like the workloads (red spectra,
+amplitudes k|eta| up to ~0.3), projected by the oracle so both sides start
+from the same band-limited state.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbi_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-11}   # SBI_FP32, SBI_FP64
+
+
+@pytest.fixture(scope="module")
+def sbi():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2310_19840_gb300 import sbi as s
+    return s
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _case(nx, ny, Lx, Ly, h0, variable, seed, amp_eta=0.04, amp_phi=0.3, amp_delta=0.1):
+    grid = O.Grid(nx, ny, Lx, Ly if ny > 1 else 1.0)
+    delta = W.random_field(nx, ny, seed, amplitude=amp_delta * h0) if variable else None
+    pb = O.Problem(grid, 9.81, h0, delta=delta)
+    eta = O.project(pb, W.random_field(nx, ny, seed + 1, amplitude=amp_eta))
+    phi = O.project(pb, W.random_field(nx, ny, seed + 2, amplitude=amp_phi))
+    return grid, pb, eta, phi
+
+
+CASES = [
+    # nx, ny, Lx, Ly, h0, variable
+    (64, 1, 6.0, 1.0, 0.7, False),
+    (256, 1, 12.0, 1.0, 0.5, True),
+    (32, 16, 4.0, 3.0, 0.6, False),
+    (64, 32, 6.0, 4.0, 0.8, True),
+    (128, 8, 8.0, 1.5, 1.0, True),
+    (16, 64, 2.0, 5.0, 0.9, False),
+]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("case", CASES)
+def test_vertical_velocity_matches_oracle(sbi, prec, case):
+    nx, ny, Lx, Ly, h0, variable = case
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, variable, seed=100 + nx + ny)
+    depth = (h0 - pb.delta) if variable else None
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [depth], h0=h0, precision=prec)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    Vo = O.vertical_velocity(eta, phi, pb.delta, h0, grid)
+    assert rel(V, Vo) < TOL[prec]
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6])
+def test_every_order(sbi, order):
+    nx, ny, Lx, Ly, h0 = 64, 16, 5.0, 3.0, 0.6
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, True, seed=7)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=1, order=order)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    Vo = O.vertical_velocity(eta, phi, pb.delta, h0, grid, order=order)
+    assert rel(V, Vo) < TOL[1]
+
+
+def test_deep_water(sbi):
+    nx, ny, L = 64, 64, 10.0
+    grid = O.Grid(nx, ny, L, L)
+    pb = O.Problem(grid, 9.81, np.inf)
+    eta = O.project(pb, W.random_field(nx, ny, 5, amplitude=0.1))
+    phi = O.project(pb, W.random_field(nx, ny, 6, amplitude=0.5))
+    for prec in (1, 0):
+        ctx = sbi.Context([(nx, ny, L, L)], 9.81, None, h0=np.inf, precision=prec)
+        ctx.set_state(0, eta, phi)
+        assert rel(ctx.vertical_velocity(0), O.vertical_velocity(eta, phi, None, np.inf, grid)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_rk4_steps_match_oracle(sbi, prec):
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, True, seed=40)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.02, 3)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.02, 3)
+    assert rel(e, eo) < TOL[prec] and rel(p, po) < TOL[prec]
+
+
+def test_sponge_matches_oracle(sbi):
+    wl = W.bar_1d(n=512, L=40.0)
+    m = wl.members[0]
+    grid = O.Grid(m.nx, 1, m.Lx)
+    x = np.arange(m.nx) * m.Lx / m.nx
+    w = (np.sin(np.pi * x / m.Lx) ** 8).reshape(1, -1)
+    pb = O.Problem(grid, wl.gravity, m.h0, delta=m.delta, sponge_w=w, sponge_nu=wl.sponge_nu)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    for prec in (1, 0):
+        ctx = sbi.Context([(m.nx, 1, m.Lx, 1.0)], wl.gravity, [m.h0 - m.delta], h0=m.h0,
+                          precision=prec, sponge_w=w, sponge_nu=wl.sponge_nu)
+        ctx.set_state(0, eta, phi)
+        ctx.step(wl.dt, 4)
+        e, p = ctx.get_state(0)
+        eo, po = O.step(pb, eta, phi, wl.dt, 4)
+        assert rel(e, eo) < TOL[prec] and rel(p, po) < TOL[prec]
+
+
+def test_filter_matches_oracle(sbi):
+    nx, ny, L = 64, 64, 8.0
+    grid = O.Grid(nx, ny, L, L)
+    kref = 2 * np.pi / L * 3
+    pb = O.Problem(grid, 9.81, 1.0, filt_beta1=2.0, filt_beta2=8.0, k_ref=kref)
+    eta = O.project(pb, W.random_field(nx, ny, 50, amplitude=0.05))
+    phi = O.project(pb, W.random_field(nx, ny, 51, amplitude=0.3))
+    for prec in (1, 0):
+        ctx = sbi.Context([(nx, ny, L, L)], 9.81, None, h0=1.0, precision=prec,
+                          filt_beta1=2.0, filt_beta2=8.0, k_ref=kref)
+        ctx.set_state(0, eta, phi)
+        ctx.step(0.02, 2)
+        e, p = ctx.get_state(0)
+        eo, po = O.step(pb, eta, phi, 0.02, 2)
+        assert rel(e, eo) < TOL[prec] and rel(p, po) < TOL[prec]
+
+
+def test_batch_of_uneven_grids_equals_single(sbi):
+    specs = [(64, 32, 6.0, 4.0), (32, 16, 3.0, 2.0), (64, 32, 6.0, 4.0), (128, 1, 9.0, 1.0)]
+    states = []
+    for i, (nx, ny, Lx, Ly) in enumerate(specs):
+        grid, pb, eta, phi = _case(nx, ny, Lx, Ly, 0.7, False, seed=60 + 3 * i)
+        states.append((eta, phi))
+    batch = sbi.Context(specs, 9.81, None, h0=0.7, precision=0)
+    for i, (e, p) in enumerate(states):
+        batch.set_state(i, e, p)
+    batch.step(0.01, 2)
+    for i, spec in enumerate(specs):
+        single = sbi.Context([spec], 9.81, None, h0=0.7, precision=0)
+        single.set_state(0, *states[i])
+        single.step(0.01, 2)
+        eb, pb_ = batch.get_state(i)
+        es, ps = single.get_state(0)
+        assert np.array_equal(eb, es) and np.array_equal(pb_, ps)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_invariants_match_oracle(sbi, prec):
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, True, seed=70)
+    eta = eta + 0.01
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec)
+    ctx.set_state(0, eta, phi)
+    m, e = ctx.invariants(0)
+    mo, eo = O.invariants(pb, eta, phi)
+    assert abs(m - mo) <= 1e-12 * abs(mo)
+    assert abs(e - eo) <= TOL[prec] * abs(eo)
