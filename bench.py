@@ -42,11 +42,17 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--members", default=None,
+                    help="crossing_batch only: 'S,L' small (256^2) and large (512^2) members "
+                         "instead of 64,32 (for profiling runs)")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, members=None):
     import workloads as W
+    if name == "crossing_batch" and members:
+        s, l = (int(v) for v in members.split(","))
+        return W.crossing_batch(n_small=s, n_large=l)
     return getattr(W, name)()
 
 
@@ -252,7 +258,7 @@ def main():
     ge.build()
     from paper_2310_19840_gb300 import sbi
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.members)
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
     ctx = make_context(sbi, wl, prec, stream.cuda_stream)

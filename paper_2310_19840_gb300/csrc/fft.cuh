@@ -12,7 +12,9 @@
 // inverse ones exp(+2 pi i / L); neither is normalised.
 //
 // Shared-memory indices are padded by one complex per 32 (pad()) to spread
-// the power-of-two strides of the scatter over the banks.
+// the power-of-two strides of the scatter over the banks.  When a transform
+// fits in one warp (N/R <= 32 threads) its passes synchronise with __syncwarp
+// only; larger transforms use block barriers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -134,8 +136,15 @@ __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int N, int idx) {
 // threads without work still take part.  The caller must make sure nobody
 // still reads s[] from earlier work (a barrier before the call).
 // ---------------------------------------------------------------------------
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
 template <int N, int R, int Ls, int SIGN, typename V>
 struct StockhamPass {
+  static constexpr bool WARP = (N / R) <= 32;
   __device__ __forceinline__ static void run(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
     constexpr int T = N / R;
     if constexpr (N / Ls >= R) {
@@ -150,11 +159,11 @@ struct StockhamPass {
       const int base = (j - k) * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) s[pad(base + r * Ls)] = x[r];
-      __syncthreads();
+      group_sync<WARP>();
       if constexpr (Ls * R < N) {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = s[pad(j + r * T)];
-        __syncthreads();
+        group_sync<WARP>();
         StockhamPass<N, R, Ls * R, SIGN, V>::run(x, s, j, tw);
       }
     } else {
@@ -174,7 +183,7 @@ struct StockhamPass {
 #pragma unroll
         for (int m = 0; m < RP; ++m) s[pad(b + m * Ls)] = v[m];
       }
-      __syncthreads();
+      group_sync<WARP>();
     }
   }
 };
@@ -185,7 +194,7 @@ __device__ __forceinline__ void fft_block(V (&x)[R], V* s, int j, const V* __res
   static_assert(R >= 1 && R <= N && (R & (R - 1)) == 0, "R must be a power of two <= N");
   if constexpr (N == 1) {
     s[0] = x[0];
-    __syncthreads();
+    __syncwarp();
   } else {
     StockhamPass<N, R, 1, SIGN, V>::run(x, s, j, tw);
   }

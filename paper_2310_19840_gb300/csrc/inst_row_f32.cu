@@ -9,7 +9,5 @@ template <> cudaError_t launch_rk<float>(int nx, const RkParams& p, cudaStream_t
   return launch_rk_impl<float>(nx, p, st);
 }
 template <> cudaError_t prepare_row_kernels<float>(int nx) { return prepare_row_impl<float>(nx); }
-template <> size_t row_smem_bytes<float>(int nx, int nslots) {
-  return row_smem_impl<float>(nx, nslots);
-}
+template <> int row_rpc<float>(int nx, int W, int nslots) { return row_rpc_impl<float>(nx, W, nslots); }
 }  // namespace sbi

@@ -9,7 +9,5 @@ template <> cudaError_t launch_rk<double>(int nx, const RkParams& p, cudaStream_
   return launch_rk_impl<double>(nx, p, st);
 }
 template <> cudaError_t prepare_row_kernels<double>(int nx) { return prepare_row_impl<double>(nx); }
-template <> size_t row_smem_bytes<double>(int nx, int nslots) {
-  return row_smem_impl<double>(nx, nslots);
-}
+template <> int row_rpc<double>(int nx, int W, int nslots) { return row_rpc_impl<double>(nx, W, nslots); }
 }  // namespace sbi

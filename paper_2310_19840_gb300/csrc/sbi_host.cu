@@ -88,6 +88,8 @@ struct sbi_ctx {
   int nmembers = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t cap = nullptr;     // internal stream for graph capture
+  std::vector<cudaStream_t> gstreams;  // one capture branch per member group
+  std::vector<cudaEvent_t> gevents;    // fork / join events of the branches
   std::vector<Group> groups;
   std::vector<std::pair<int, int>> where;  // member -> (group, local index)
   std::vector<void*> allocs;
@@ -229,7 +231,7 @@ struct Planner {
     op.a = (uint8_t)ea;
     op.b = (uint8_t)db;
     op.c = (uint8_t)wc;
-    op.coef = (float)coef;
+    op.coef = coef;
     op.dst = (uint8_t)add_buf(r, mref(dst));
     r.bytes += mixed_bytes();
     if (room(r)) r.p.ops[r.p.nops++] = op;
@@ -239,7 +241,7 @@ struct Planner {
     op.kind = ROP_N2;
     op.slot = (uint8_t)slot0;
     op.a = g.two_d ? 2 : 1;
-    op.coef = (float)c->gravity;
+    op.coef = c->gravity;
     op.dst = (uint8_t)add_buf(r, mref(dst));
     r.bytes += mixed_bytes();
     if (room(r)) r.p.ops[r.p.nops++] = op;
@@ -252,6 +254,11 @@ struct Planner {
     op.dst = (uint8_t)add_buf(r, pref(phys_out));
     r.bytes += phys_bytes();
     if (room(r)) r.p.ops[r.p.nops++] = op;
+  }
+  int rpc_for(int nslots) {
+    const int r = c->fp64 ? row_rpc<double>(g.nx, g.W, nslots) : row_rpc<float>(g.nx, g.W, nslots);
+    if (r <= 0) oom = true;
+    return r > 0 ? r : 1;
   }
   Pass row_end(RowB& r, bool use_eta, bool use_delta, bool use_w) {
     if (use_eta) {
@@ -267,6 +274,7 @@ struct Planner {
       r.bytes += (double)g.phys_elems() * c->real_size;
     }
     r.p.nslots = r.maxslot + 1;
+    r.p.rpc = rpc_for(r.p.nslots);
     Pass ps{};
     ps.kind = PK_ROW;
     ps.nsize = g.nx;
@@ -494,6 +502,7 @@ struct Planner {
     p.rows_total = g.n * g.ny;
     p.ny = g.ny;
     p.W = g.W;
+    p.rpc = rpc_for(0);
     p.dt = dt;
     p.eta0 = dref(g.eta0);
     p.phi0 = dref(g.phi0);
@@ -567,9 +576,11 @@ int run_passes(sbi_ctx* c, const std::vector<Pass>& ps, cudaStream_t st) {
   return SBI_OK;
 }
 
-std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
-  std::vector<Pass> all;
+// Passes of one step for each member group (groups are independent).
+std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom) {
+  std::vector<std::vector<Pass>> out;
   for (auto& g : c->groups) {
+    std::vector<Pass> all;
     Planner pl{c, g};
     for (int s = 1; s <= 4; ++s) {
       pl.plan_diag(all);
@@ -578,7 +589,14 @@ std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
     }
     if (c->filter_on()) pl.plan_project(all, true);
     if (pl.oom) *oom = true;
+    out.push_back(std::move(all));
   }
+  return out;
+}
+
+std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
+  std::vector<Pass> all;
+  for (auto& v : plan_step_groups(c, dt, oom)) all.insert(all.end(), v.begin(), v.end());
   return all;
 }
 
@@ -599,39 +617,62 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
   for (auto& ge : c->graphs)
     if (ge.dt == dt && ge.prof == c->prof) { *out = &ge; return SBI_OK; }
   bool oom = false;
-  std::vector<Pass> ps = plan_step(c, dt, &oom);
+  std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, &oom);
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
   CK(cudaStreamSynchronize(c->stream), "sync before capture");
+  size_t npasses = 0;
+  for (auto& v : gps) npasses += v.size();
   if (c->prof) {
     free_graphs(c);  // a profiled graph owns the event pairs
-    for (auto e : c->ev) cudaEventDestroy(e);
-    c->ev.clear();
-    c->ev_family.clear();
-    for (size_t i = 0; i < ps.size(); ++i) {
-      cudaEvent_t a, b;
-      CK(cudaEventCreate(&a), "event");
-      CK(cudaEventCreate(&b), "event");
-      c->ev.push_back(a);
-      c->ev.push_back(b);
-      c->ev_family.push_back(family_of(ps[i]));
-    }
+    for (size_t gi = 0; gi < gps.size(); ++gi)
+      for (size_t i = 0; i < gps[gi].size(); ++i) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a), "event");
+        CK(cudaEventCreate(&b), "event");
+        c->ev.push_back(a);
+        c->ev.push_back(b);
+        c->ev_family.push_back(family_of(gps[gi][i]));
+      }
+  }
+  // one branch per group: fork from the capture stream, join back
+  while (c->gstreams.size() < gps.size()) {
+    cudaStream_t s2;
+    CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "stream");
+    c->gstreams.push_back(s2);
+  }
+  while (c->gevents.size() < gps.size() + 1) {
+    cudaEvent_t e2;
+    CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "event");
+    c->gevents.push_back(e2);
   }
   GraphEntry ge;
   ge.dt = dt;
   ge.prof = c->prof;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = SBI_OK;
-  for (size_t i = 0; i < ps.size() && rc == SBI_OK; ++i) {
-    if (c->prof) cudaEventRecord(c->ev[2 * i], c->cap);
-    rc = launch_pass(c, ps[i], c->cap);
-    if (c->prof) cudaEventRecord(c->ev[2 * i + 1], c->cap);
+  const bool branch = gps.size() > 1;
+  if (branch) cudaEventRecord(c->gevents[0], c->cap);
+  size_t evi = 0;
+  for (size_t gi = 0; gi < gps.size() && rc == SBI_OK; ++gi) {
+    cudaStream_t st = branch ? c->gstreams[gi] : c->cap;
+    if (branch) cudaStreamWaitEvent(st, c->gevents[0], 0);
+    for (size_t i = 0; i < gps[gi].size() && rc == SBI_OK; ++i, ++evi) {
+      // external event records become timing nodes of the graph
+      if (c->prof) cudaEventRecordWithFlags(c->ev[2 * evi], st, cudaEventRecordExternal);
+      rc = launch_pass(c, gps[gi][i], st);
+      if (c->prof) cudaEventRecordWithFlags(c->ev[2 * evi + 1], st, cudaEventRecordExternal);
+    }
+    if (branch) {
+      cudaEventRecord(c->gevents[gi + 1], st);
+      cudaStreamWaitEvent(c->cap, c->gevents[gi + 1], 0);
+    }
   }
   cudaError_t e = cudaStreamEndCapture(c->cap, &ge.graph);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
   CK(cudaGraphInstantiate(&ge.exec, ge.graph, 0), "graph instantiate");
-  ge.launches = (int)ps.size();
+  ge.launches = (int)npasses;
   c->graphs.push_back(ge);
   *out = &c->graphs.back();
   return SBI_OK;
@@ -1162,6 +1203,8 @@ void sbi_destroy(sbi_ctx* c) {
     else cudaFree(p);
   }
   c->allocs.clear();
+  for (auto s2 : c->gstreams) cudaStreamDestroy(s2);
+  for (auto e2 : c->gevents) cudaEventDestroy(e2);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }

@@ -4,9 +4,10 @@
 // "column" passes over each member's fields.  Between passes a field lives in
 // one of three layouts:
 //   physical  ny x nx reals (x fastest);
-//   mixed     ny x W complex: FFT along x only, keeping the W = ceil(alpha nx/2)
-//             non-negative x-modes that survive the dealias mask (the Nyquist
-//             and all higher x-modes are zero by construction), y physical;
+//   mixed     W x ny complex, stored [kx][y]: FFT along x only, keeping the
+//             W = ceil(alpha nx/2) non-negative x-modes that survive the dealias
+//             mask (the Nyquist and all higher x-modes are zero by
+//             construction), y physical, each kx column contiguous;
 //   (spectral values exist only inside a column pass).
 // A row pass turns mixed rows into physical ones (inverse real FFT along x),
 // forms pointwise products, and turns them back into mixed rows (forward real
@@ -49,7 +50,8 @@ struct RowOp {
   uint8_t c;
   uint8_t dst;
   uint16_t pad_;
-  float coef;
+  uint32_t pad2_;
+  double coef;    // PROD: scalar coefficient; N2: gravity
 };
 
 struct BufRef {
@@ -58,6 +60,7 @@ struct BufRef {
 };
 
 struct RowParams {
+  int rpc;              // rows per block (runtime, <= the kernel's maximum)
   int nops;
   int rows_total;       // members * ny
   int ny;
@@ -102,6 +105,7 @@ struct ColParams {
 enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2 };
 
 struct RkParams {
+  int rpc;              // rows per block
   const int* active;    // per-member flag (nullptr: all members)
   int mode;             // RkMode
   int stage;            // 1..4 for RK_STAGE
@@ -128,6 +132,7 @@ template <typename T> cudaError_t prepare_col_kernels(int ny);
 template <typename T> cudaError_t launch_row(int nx, const RowParams& p, cudaStream_t st);
 template <typename T> cudaError_t launch_col(int ny, const ColParams& p, cudaStream_t st);
 template <typename T> cudaError_t launch_rk(int nx, const RkParams& p, cudaStream_t st);
-template <typename T> size_t row_smem_bytes(int nx, int nslots);
+// rows per block for a row pass with nslots physical slots (0: does not fit)
+template <typename T> int row_rpc(int nx, int W, int nslots);
 
 }  // namespace sbi
