@@ -6,4 +6,7 @@ template <> cudaError_t launch_col<float>(int ny, const ColParams& p, cudaStream
   return launch_col_impl<float>(ny, p, st);
 }
 template <> cudaError_t prepare_col_kernels<float>(int ny) { return prepare_col_impl<float>(ny); }
+template <> cudaError_t launch_coef_table<float>(void* out, const TableSpec& s, cudaStream_t st) {
+  return launch_coef_table_impl<float>(out, s, st);
+}
 }  // namespace sbi

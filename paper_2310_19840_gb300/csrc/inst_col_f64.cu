@@ -6,4 +6,7 @@ template <> cudaError_t launch_col<double>(int ny, const ColParams& p, cudaStrea
   return launch_col_impl<double>(ny, p, st);
 }
 template <> cudaError_t prepare_col_kernels<double>(int ny) { return prepare_col_impl<double>(ny); }
+template <> cudaError_t launch_coef_table<double>(void* out, const TableSpec& s, cudaStream_t st) {
+  return launch_coef_table_impl<double>(out, s, st);
+}
 }  // namespace sbi

@@ -33,12 +33,12 @@ struct RowCfg {
 };
 
 // shared memory of a row block: per row the FFT scratch (which also stages
-// the incoming mixed row), the row of eta, and the physical slots
+// the incoming mixed row) and the physical slots
 template <typename T, int NX>
 __host__ __device__ constexpr size_t row_smem(int rpc, int W, int nslots) {
   using C = RowCfg<NX>;
   (void)W;
-  return sizeof(cx<T>) * (size_t)rpc * ((size_t)C::FBUF + (size_t)(1 + nslots) * C::n);
+  return sizeof(cx<T>) * (size_t)rpc * ((size_t)C::FBUF + (size_t)nslots * C::n);
 }
 
 template <int NX>
@@ -109,7 +109,9 @@ __device__ __forceinline__ void stage_mixed(cx<T>* stg_all, int fbuf, const BufR
 // Packed inverse real FFT, input side, from the staged row: Z[k] = E + i O,
 // E = X[k] + X*[n-k], O = (X[k] - X*[n-k]) e^{+2 pi i k / NX}, k = j + r TPR;
 // X[k] = 0 for k >= W, and the Nyquist mode X[n] = 0.  The unnormalised
-// inverse of Z gives NX * x packed as z[m] = x[2m] + i x[2m+1].
+// inverse of Z gives NX * x packed as z[m] = x[2m] + i x[2m+1].  The function
+// returns conj(Z): the inverse is taken as conj(F(conj Z)), so the caller runs
+// the forward FFT and conjugates what it reads back.
 template <typename T, int NX>
 __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>* stg, int W, int j,
                                           const cx<T>* __restrict__ tw) {
@@ -124,7 +126,7 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
     const V bc = cconj(b);
     const V E = cadd(a, bc);
     const V O = cmul(csub(a, bc), cconj(__ldg(tw + tw_off(NX) + k)));
-    x[r] = cadd(E, rot<1>(O));
+    x[r] = cconj(cadd(E, rot<1>(O)));
   }
 }
 
@@ -165,11 +167,9 @@ k_row(const __grid_constant__ RowParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rpc = p.rpc;
   V* fb_all = reinterpret_cast<V*>(smem_raw);      // FFT scratch, also staging
-  V* eta_all = fb_all + rpc * C::FBUF;             // rows of eta (pairs)
-  V* slot_base = eta_all + rpc * n;                // physical slots
+  V* slot_base = fb_all + rpc * C::FBUF;           // physical slots
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
   V* fb = fb_all + rloc * C::FBUF;
-  V* eta = eta_all + rloc * n;
   const int row0 = (int)blockIdx.x * rpc;
   const RowIO io(row0, rpc, p.rows_total, p.ny, p.W, p.active, p.member0);
   const int row = row0 + rloc;
@@ -179,11 +179,8 @@ k_row(const __grid_constant__ RowParams p) {
   const bool act = valid && (p.active == nullptr || p.active[p.member0 + member] != 0);
   const V* tw = reinterpret_cast<const V*>(p.tw);
 
-  if (p.eta.ptr) {
-    const V* er = act ? phys_row<T>(p.eta, member, y, NX) : nullptr;
-#pragma unroll
-    for (int r = 0; r < R; ++r) eta[j + r * TPR] = er ? er[j + r * TPR] : mk<V>(T(0), T(0));
-  }
+  // eta is read through the L1 cache by every product of the row
+  const V* eta = (act && p.eta.ptr) ? phys_row<T>(p.eta, member, y, NX) : nullptr;
 
   for (int o = 0; o < p.nops; ++o) {
     const RowOp op = p.ops[o];
@@ -194,40 +191,47 @@ k_row(const __grid_constant__ RowParams p) {
       __syncthreads();
       c2r_input<T, NX>(x, fb, p.W, j, tw);
       row_group_sync<NX>();  // the staged row is read before the FFT overwrites it
-      fft_block<n, R, +1>(x, fb, j, tw);
+      fft_block<n, R, -1>(x, fb, j, tw);
       V* slot = slot_base + (op.slot * rpc + rloc) * n;
       V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V z = fb[pad(m)];
+        const V z = cconj(fb[pad(m)]);
         slot[m] = z;
         if (out) out[m] = z;
       }
       continue;
     }
     if (op.kind == ROP_PROD) {
-      const V* slot = op.slot == kNone ? nullptr : slot_base + (op.slot * rpc + rloc) * n;
+      V* slot = op.slot == kNone ? nullptr : slot_base + (op.slot * rpc + rloc) * n;
       const T cf = T(op.coef);
+      const bool running = (op.c & 2) != 0;
       const V* drow = (act && op.b > 0 && p.delta.ptr) ? phys_row<T>(p.delta, member, y, NX) : nullptr;
-      const V* wrow = (act && op.c > 0 && p.wgt.ptr) ? phys_row<T>(p.wgt, member, y, NX) : nullptr;
+      const V* wrow = (act && (op.c & 1) && p.wgt.ptr) ? phys_row<T>(p.wgt, member, y, NX) : nullptr;
+      const V* erow = op.a > 0 ? eta : nullptr;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V v = slot ? slot[m] : mk<V>(T(1), T(1));
-        const V e = eta[m];
-        T f0 = cf * ipow(e.x, op.a), f1 = cf * ipow(e.y, op.a);
+        V v = slot ? slot[m] : mk<V>(T(1), T(1));
+        if (erow) {
+          const V e = __ldg(erow + m);
+          T e0 = e.x, e1 = e.y;
+          for (int q = 1; q < op.a; ++q) { e0 *= e.x; e1 *= e.y; }
+          v = mk<V>(v.x * e0, v.y * e1);
+        }
         if (drow) {
-          const V d = drow[m];
-          f0 *= ipow(d.x, op.b);
-          f1 *= ipow(d.y, op.b);
+          const V d = __ldg(drow + m);
+          T d0 = d.x, d1 = d.y;
+          for (int q = 1; q < op.b; ++q) { d0 *= d.x; d1 *= d.y; }
+          v = mk<V>(v.x * d0, v.y * d1);
         }
+        if (running && slot) slot[m] = v;
         if (wrow) {
-          const V w = wrow[m];
-          f0 *= w.x;
-          f1 *= w.y;
+          const V w = __ldg(wrow + m);
+          v = mk<V>(v.x * w.x, v.y * w.y);
         }
-        x[r] = mk<V>(f0 * v.x, f1 * v.y);
+        x[r] = mk<V>(cf * v.x, cf * v.y);
       }
     } else {
       // ROP_N2 / ROP_WDOT: slots V, eta_x, [eta_y,] phi_x, [phi_y]
@@ -245,7 +249,7 @@ k_row(const __grid_constant__ RowParams p) {
         const V vv = sV[m], ex = sEx[m], px = sPx[m];
         const V ey = two_d ? sEy[m] : mk<V>(T(0), T(0));
         const V py = two_d ? sPy[m] : mk<V>(T(0), T(0));
-        const V e = eta[m];
+        const V e = eta ? __ldg(eta + m) : mk<V>(T(0), T(0));
         T res[2];
         const T vc[2] = {vv.x, vv.y}, exc[2] = {ex.x, ex.y}, eyc[2] = {ey.x, ey.y};
         const T pxc[2] = {px.x, px.y}, pyc[2] = {py.x, py.y}, ec[2] = {e.x, e.y};
@@ -273,7 +277,79 @@ k_row(const __grid_constant__ RowParams p) {
 }
 
 // ===========================================================================
-// RK4 stage pass (row layout).  FP64 state and sums for every real type.
+// State arithmetic.  The FP64 path keeps the state and the RK4 sums in double.
+// The FP32 path keeps them as unevaluated sums hi + lo of two floats
+// ("double-single", about 48 significant bits) updated with the error-free
+// transformations TwoSum (Knuth) and FastTwoSum / the FMA product error
+// (Dekker): on this GPU FP64 runs at a small fraction of the FP32 rate and an
+// FP64 state update made the RK pass FP64-bound.  Both use 8 bytes per value.
+// ===========================================================================
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add_f(FF x, float f) {
+  FF s = ff_two_sum(x.hi, f);
+  s.lo += x.lo;
+  return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF s = ff_two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_mul_f(FF x, float f) {
+  const float p = x.hi * f;
+  float e = fmaf(x.hi, f, -p);
+  e = fmaf(x.lo, f, e);
+  return ff_fast_two_sum(p, e);
+}
+
+// A pair of state values (elements 2m, 2m+1) in the storage of each path.
+template <typename T> struct StatePair;
+template <> struct StatePair<double> {
+  double v[2];
+  __device__ __forceinline__ static StatePair load(const void* base, int m) {
+    const double2 d = reinterpret_cast<const double2*>(base)[m];
+    return StatePair{{d.x, d.y}};
+  }
+  __device__ __forceinline__ void store(void* base, int m) const {
+    reinterpret_cast<double2*>(base)[m] = make_double2(v[0], v[1]);
+  }
+  __device__ __forceinline__ void add(int h, double f) { v[h] += f; }
+  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, double s) { v[h] += s * a.v[h]; }
+  __device__ __forceinline__ double value(int h) const { return v[h]; }
+  __device__ __forceinline__ bool finite() const { return isfinite(v[0]) && isfinite(v[1]); }
+  __device__ __forceinline__ static StatePair zero() { return StatePair{{0.0, 0.0}}; }
+};
+template <> struct StatePair<float> {
+  FF v[2];
+  __device__ __forceinline__ static StatePair load(const void* base, int m) {
+    const float4 d = reinterpret_cast<const float4*>(base)[m];
+    return StatePair{{FF{d.x, d.y}, FF{d.z, d.w}}};
+  }
+  __device__ __forceinline__ void store(void* base, int m) const {
+    reinterpret_cast<float4*>(base)[m] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  }
+  __device__ __forceinline__ void add(int h, float f) { v[h] = ff_add_f(v[h], f); }
+  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, float s) {
+    v[h] = ff_add(v[h], ff_mul_f(a.v[h], s));
+  }
+  __device__ __forceinline__ float value(int h) const { return v[h].hi + v[h].lo; }
+  __device__ __forceinline__ bool finite() const { return isfinite(v[0].hi) && isfinite(v[1].hi); }
+  __device__ __forceinline__ static StatePair zero() { return StatePair{{FF{0.f, 0.f}, FF{0.f, 0.f}}}; }
+};
+
+// ===========================================================================
+// RK4 stage pass (row layout).  State and sums in StatePair<T> storage.
 // ===========================================================================
 template <typename T, int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::MAX_THREADS)
@@ -297,21 +373,21 @@ k_rk(const __grid_constant__ RkParams p) {
   const long long off = (long long)y * NX;
 
   // new state in the working precision (the FFT inputs of the tail)
+  using SP = StatePair<T>;
   V xe[R], xp[R];
-  const double* E0 = reinterpret_cast<const double*>(p.eta0.ptr) + member * p.eta0.stride + off;
-  const double* P0 = reinterpret_cast<const double*>(p.phi0.ptr) + member * p.phi0.stride + off;
-  double* E0w = reinterpret_cast<double*>(p.eta0.ptr) + member * p.eta0.stride + off;
-  double* P0w = reinterpret_cast<double*>(p.phi0.ptr) + member * p.phi0.stride + off;
+  const long long eoff = member * p.eta0.stride + off, poff = member * p.phi0.stride + off;
+  char* E0 = reinterpret_cast<char*>(p.eta0.ptr) + eoff * 8;   // 8 bytes per value
+  char* P0 = reinterpret_cast<char*>(p.phi0.ptr) + poff * 8;
   bool bad = false;
 
   if (p.mode == RK_ENTRY) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int m = j + r * TPR;
-      const double2 e = act ? reinterpret_cast<const double2*>(E0)[m] : make_double2(0.0, 0.0);
-      const double2 q = act ? reinterpret_cast<const double2*>(P0)[m] : make_double2(0.0, 0.0);
-      xe[r] = mk<V>(T(e.x), T(e.y));
-      xp[r] = mk<V>(T(q.x), T(q.y));
+      const SP e = act ? SP::load(E0, m) : SP::zero();
+      const SP q = act ? SP::load(P0, m) : SP::zero();
+      xe[r] = mk<V>(T(e.value(0)), T(e.value(1)));
+      xp[r] = mk<V>(T(q.value(0)), T(q.value(1)));
     }
   } else {
     V x[R];
@@ -320,75 +396,75 @@ k_rk(const __grid_constant__ RkParams p) {
     __syncthreads();
     c2r_input<T, NX>(x, fb, p.W, j, tw);
     row_group_sync<NX>();
-    fft_block<n, R, +1>(x, fb, j, tw);
+    fft_block<n, R, -1>(x, fb, j, tw);
     if (p.mode == RK_CORRECT) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = fb[pad(m)];
-        double2 e = act ? reinterpret_cast<const double2*>(E0)[m] : make_double2(0.0, 0.0);
-        e.x += double(c.x);
-        e.y += double(c.y);
-        if (act) reinterpret_cast<double2*>(E0w)[m] = e;
-        bad |= !isfinite(e.x) || !isfinite(e.y);
-        xe[r] = mk<V>(T(e.x), T(e.y));
+        const V c = cconj(fb[pad(m)]);
+        SP e = act ? SP::load(E0, m) : SP::zero();
+        e.add(0, c.x);
+        e.add(1, c.y);
+        if (act) e.store(E0, m);
+        bad |= !e.finite();
+        xe[r] = mk<V>(T(e.value(0)), T(e.value(1)));
       }
       __syncthreads();
       stage_mixed<T>(fb_all, C::FBUF, &p.corr_phi, 1, io);
       __syncthreads();
       c2r_input<T, NX>(x, fb, p.W, j, tw);
       row_group_sync<NX>();
-      fft_block<n, R, +1>(x, fb, j, tw);
+      fft_block<n, R, -1>(x, fb, j, tw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = fb[pad(m)];
-        double2 q = act ? reinterpret_cast<const double2*>(P0)[m] : make_double2(0.0, 0.0);
-        q.x += double(c.x);
-        q.y += double(c.y);
-        if (act) reinterpret_cast<double2*>(P0w)[m] = q;
-        bad |= !isfinite(q.x) || !isfinite(q.y);
-        xp[r] = mk<V>(T(q.x), T(q.y));
+        const V c = cconj(fb[pad(m)]);
+        SP q = act ? SP::load(P0, m) : SP::zero();
+        q.add(0, c.x);
+        q.add(1, c.y);
+        if (act) q.store(P0, m);
+        bad |= !q.finite();
+        xp[r] = mk<V>(T(q.value(0)), T(q.value(1)));
       }
     } else {
       // classical RK4: sums b = (1/6, 1/3, 1/3, 1/6), next-stage offsets c = (1/2, 1/2, 1)
       const V* Vr = act ? phys_row<T>(p.V, member, y, NX) : nullptr;
-      double2* AE = reinterpret_cast<double2*>(reinterpret_cast<double*>(p.acc_eta.ptr) + member * p.acc_eta.stride + off);
-      double2* AP = reinterpret_cast<double2*>(reinterpret_cast<double*>(p.acc_phi.ptr) + member * p.acc_phi.stride + off);
-      const double bw = (p.stage == 1 || p.stage == 4) ? (1.0 / 6.0) : (1.0 / 3.0);
-      const double cn = (p.stage == 3) ? 1.0 : 0.5;
-      const double dt = p.dt;
+      char* AE = reinterpret_cast<char*>(p.acc_eta.ptr) + (member * p.acc_eta.stride + off) * 8;
+      char* AP = reinterpret_cast<char*>(p.acc_phi.ptr) + (member * p.acc_phi.stride + off) * 8;
+      const T bw = T((p.stage == 1 || p.stage == 4) ? (1.0 / 6.0) : (1.0 / 3.0));
+      const T cdt = T((p.stage == 3 ? 1.0 : 0.5) * p.dt);
+      const T dt = T(p.dt);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V ft = fb[pad(m)];
-        double2 e = make_double2(0.0, 0.0), q = make_double2(0.0, 0.0);
-        if (act) {
-          const V vv = Vr[m];
-          const double2 e0 = reinterpret_cast<const double2*>(E0)[m];
-          const double2 q0 = reinterpret_cast<const double2*>(P0)[m];
-          double2 ae = make_double2(bw * double(vv.x), bw * double(vv.y));
-          double2 ap = make_double2(bw * double(ft.x), bw * double(ft.y));
-          if (p.stage > 1) {
-            const double2 a0 = AE[m], b0 = AP[m];
-            ae.x += a0.x; ae.y += a0.y;
-            ap.x += b0.x; ap.y += b0.y;
-          }
-          if (p.stage < 4) {
-            AE[m] = ae;
-            AP[m] = ap;
-            e = make_double2(e0.x + cn * dt * double(vv.x), e0.y + cn * dt * double(vv.y));
-            q = make_double2(q0.x + cn * dt * double(ft.x), q0.y + cn * dt * double(ft.y));
-          } else {
-            e = make_double2(e0.x + dt * ae.x, e0.y + dt * ae.y);
-            q = make_double2(q0.x + dt * ap.x, q0.y + dt * ap.y);
-            reinterpret_cast<double2*>(E0w)[m] = e;
-            reinterpret_cast<double2*>(P0w)[m] = q;
-            bad |= !isfinite(e.x) || !isfinite(e.y) || !isfinite(q.x) || !isfinite(q.y);
-          }
+        const V ft = cconj(fb[pad(m)]);
+        xe[r] = mk<V>(T(0), T(0));
+        xp[r] = mk<V>(T(0), T(0));
+        if (!act) continue;
+        const V vv = Vr[m];
+        SP ae = (p.stage > 1) ? SP::load(AE, m) : SP::zero();
+        SP ap = (p.stage > 1) ? SP::load(AP, m) : SP::zero();
+        ae.add(0, bw * vv.x);
+        ae.add(1, bw * vv.y);
+        ap.add(0, bw * ft.x);
+        ap.add(1, bw * ft.y);
+        SP e = SP::load(E0, m), q = SP::load(P0, m);
+        if (p.stage < 4) {
+          ae.store(AE, m);
+          ap.store(AP, m);
+          xe[r] = mk<V>(T(e.value(0) + cdt * vv.x), T(e.value(1) + cdt * vv.y));
+          xp[r] = mk<V>(T(q.value(0) + cdt * ft.x), T(q.value(1) + cdt * ft.y));
+        } else {
+          e.add_scaled(0, ae, dt);
+          e.add_scaled(1, ae, dt);
+          q.add_scaled(0, ap, dt);
+          q.add_scaled(1, ap, dt);
+          e.store(E0, m);
+          q.store(P0, m);
+          bad |= !e.finite() || !q.finite();
+          xe[r] = mk<V>(T(e.value(0)), T(e.value(1)));
+          xp[r] = mk<V>(T(q.value(0)), T(q.value(1)));
         }
-        xe[r] = mk<V>(T(e.x), T(e.y));
-        xp[r] = mk<V>(T(q.x), T(q.y));
       }
     }
   }
@@ -414,40 +490,34 @@ k_rk(const __grid_constant__ RkParams p) {
 // ===========================================================================
 // Column pass: CPB columns per block, TPC threads per column (one warp or less
 // per column up to NY = 512), each column a contiguous run of NY complex.
+// Per column the block keeps in shared memory the FFT scratch, the
+// (tanh, sech) factors of its modes and the accumulators, so the multiplier
+// loops run from shared memory and the registers hold only the FFT data.
+// Inverse transforms use F^{-1}(X) = conj(F(conj X)) so one (forward) FFT
+// instantiation serves both directions.
 // ===========================================================================
-template <int NY>
+template <typename T, int NY>
 struct ColCfg {
   static constexpr int RC = NY == 1 ? 1 : (NY <= 256 ? cmin(8, NY) : 16);
   static constexpr int TPC = NY / RC;
   static constexpr bool WARP = TPC <= 32;
-  static constexpr int CPB = NY == 1 ? 256 : cmax(1, 256 / TPC);
+  // 8-byte elements: 256 threads per block; 16-byte elements: half the columns
+  static constexpr int CPB = NY == 1 ? 256 : cmax(1, 256 / TPC / (int)(sizeof(T) / 4));
   static constexpr int THREADS = TPC * CPB;
-  static constexpr int CBUF = padded_len(NY);
+  static constexpr int SCR = NY == 1 ? 0 : padded_len(NY);
 };
 
-// per column: FFT scratch and the (tanh, sech) factors of its modes
 template <typename T, int NY>
-__host__ __device__ constexpr size_t col_smem() {
-  return sizeof(cx<T>) * (size_t)ColCfg<NY>::CPB * ((NY == 1 ? 0 : ColCfg<NY>::CBUF) + NY);
+__host__ __device__ constexpr size_t col_smem(int nacc) {
+  using C = ColCfg<T, NY>;
+  return sizeof(cx<T>) * (size_t)C::CPB * ((size_t)C::SCR + (size_t)NY * nacc);
 }
 
-// c k^p D (i kx)^gx (i ky)^gy x  (negative powers of k vanish at k = 0).  The
-// term is uniform across the block, so its fields select without divergence.
-template <typename T>
-__device__ __forceinline__ cx<T> apply_term(const ColTerm& t, cx<T> x, T k, T kxv, T kyv, T tk,
-                                            T sk, T lam) {
-  using V = cx<T>;
-  const int ap = t.kpow < 0 ? -t.kpow : t.kpow;
-  T kp = T(1);
-  for (int i = 0; i < ap; ++i) kp *= k;
-  if (t.kpow < 0) kp = (k > T(0)) ? T(1) / kp : T(0);
-  T f = T(t.c) * kp;
-  f *= (t.depth == 1) ? tk : ((t.depth == 2) ? sk : ((t.depth == 3) ? lam : T(1)));
-  f *= (t.gx ? kxv : T(1)) * (t.gx == 2 ? kxv : T(1)) * (t.gy ? kyv : T(1)) * (t.gy == 2 ? kyv : T(1));
-  const int q = (t.gx + t.gy) & 3;   // multiply by i^q
-  const T re = x.x * f, im = x.y * f;
-  T r2 = (q & 1) ? -im : re;
-  T i2 = (q & 1) ? re : im;
+template <typename V, typename S>
+__device__ __forceinline__ V cmul_ipow(V x, S f, int q) {   // x f i^q
+  const S re = x.x * f, im = x.y * f;
+  S r2 = (q & 1) ? -im : re;
+  S i2 = (q & 1) ? re : im;
   if (q & 2) {
     r2 = -r2;
     i2 = -i2;
@@ -455,122 +525,80 @@ __device__ __forceinline__ cx<T> apply_term(const ColTerm& t, cx<T> x, T k, T kx
   return mk<V>(r2, i2);
 }
 
-// tanh(k h0) and sech(k h0) = 2 e^{-k h0} / (1 + e^{-2 k h0}); deep water for h0 = inf
-template <typename T>
-__device__ __forceinline__ void depth_factors(T k, T h0, bool deep, T& tk, T& sk) {
-  if (!(k > T(0))) {
-    tk = T(0);
-    sk = T(1);
-  } else if (deep) {
-    tk = T(1);
-    sk = T(0);
-  } else {
-    const T kh = k * h0;
-    const T e = exp(-kh);
-    tk = tanh(kh);
-    sk = T(2) * e / (T(1) + e * e);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ T filter_factor(T k, T kf, T beta2) {
-  return kf > T(0) ? exp(-pow(k / kf, beta2)) : T(1);
-}
-
-template <typename T, int NY, int NACC>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+template <typename T, int NY>
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS)
 k_col(const __grid_constant__ ColParams p) {
   using V = cx<T>;
-  using C = ColCfg<NY>;
-  constexpr int RC = C::RC, TPC = C::TPC, CPB = C::CPB;
+  using C = ColCfg<T, NY>;
+  constexpr int RC = C::RC, TPC = C::TPC, CPB = C::CPB, SCR = C::SCR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x / TPC, j = threadIdx.x % TPC;
-  constexpr int SCR = NY == 1 ? 0 : C::CBUF;
-  V* sc = reinterpret_cast<V*>(smem_raw) + c * SCR;
-  V* dts = reinterpret_cast<V*>(smem_raw) + CPB * SCR + c * NY;   // (tanh, sech) per mode
+  V* base = reinterpret_cast<V*>(smem_raw);
+  V* sc = base + c * SCR;                                   // FFT scratch
+  V* acc0 = base + CPB * SCR + c * NY * p.nacc;             // accumulators
+  V* acc1 = acc0 + (p.nacc > 1 ? NY : 0);
   const int gc = blockIdx.x * CPB + c;
   const bool valid = gc < p.cols_total;
   const int member = valid ? gc / p.W : 0;
   const int kx = valid ? gc % p.W : 0;
   const bool act = valid && (p.active == nullptr || p.active[p.member0 + member] != 0);
   const V* tw = reinterpret_cast<const V*>(p.tw);
-  const bool deep = isinf(p.h0);
-  const T h0 = deep ? T(0) : T(p.h0);
-  const T kxv = T(kx) * T(p.two_pi_over_Lx);
-  const T ky1 = T(p.two_pi_over_Ly);
   const long long col_off = (long long)kx * NY;
 
-  // depth factors of the thread's modes n = j + r TPC (read back only by this thread)
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
-    const int ni = j + r * TPC;
-    const int ns = (NY == 1) ? 0 : (ni < NY / 2 ? ni : ni - NY);
-    const T kyv = T(ns) * ky1;
-    T tk, sk;
-    depth_factors<T>(sqrt(kxv * kxv + kyv * kyv), h0, deep, tk, sk);
-    dts[ni] = mk<V>(tk, sk);
+    acc0[j + r * TPC] = mk<V>(T(0), T(0));
+    acc1[j + r * TPC] = mk<V>(T(0), T(0));
   }
 
-  V acc[NACC][RC];
-#pragma unroll
-  for (int a = 0; a < NACC; ++a)
-#pragma unroll
-    for (int r = 0; r < RC; ++r) acc[a][r] = mk<V>(T(0), T(0));
   for (int i = 0; i < p.nin; ++i) {
-    V x[RC];
     const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
+    V x[RC];
 #pragma unroll
     for (int r = 0; r < RC; ++r) x[r] = act ? src[j + r * TPC] : mk<V>(T(0), T(0));
     if constexpr (NY > 1) {
       group_sync<C::WARP>();  // scratch free
       fft_block<NY, RC, -1>(x, sc, j, tw);
-#pragma unroll
-      for (int r = 0; r < RC; ++r) x[r] = sc[pad(j + r * TPC)];
     }
     for (int q = p.term_begin[i]; q < p.term_begin[i + 1]; ++q) {
       const ColTerm t = p.terms[q];
+      const T* tab = reinterpret_cast<const T*>(t.tab) + col_off;
+      const int ph = (t.gx + t.gy) & 3;
+      V* acc = (t.acc == 0) ? acc0 : acc1;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
         const int ni = j + r * TPC;
-        const int ns = (NY == 1) ? 0 : (ni < NY / 2 ? ni : ni - NY);
-        const T kyv = T(ns) * ky1;
-        const T kk = sqrt(kxv * kxv + kyv * kyv);
-        const V ts = dts[ni];
-        const V v = apply_term<T>(t, x[r], kk, kxv, kyv, ts.x, ts.y, T(1));
-        if (NACC == 1 || t.acc == 0) acc[0][r] = cadd(acc[0][r], v);
-        else acc[NACC - 1][r] = cadd(acc[NACC - 1][r], v);
+        const V v = (NY > 1) ? sc[pad(ni)] : x[0];
+        acc[ni] = cadd(acc[ni], cmul_ipow(v, __ldg(tab + ni), ph));
       }
     }
   }
   for (int o = 0; o < p.nouts; ++o) {
     const ColTerm t = p.outs[o];
+    const T* tab = reinterpret_cast<const T*>(t.tab) + col_off;
+    const int ph = (t.gx + t.gy) & 3;
+    const V* acc = (t.acc == 0) ? acc0 : acc1;
     V x[RC];
+    // conjugated input: the forward FFT of conj(X) is the conjugate of F^{-1}(X)
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
       const int ni = j + r * TPC;
-      const int ns = (NY == 1) ? 0 : (ni < NY / 2 ? ni : ni - NY);
-      const T kyv = T(ns) * ky1;
-      const T kk = sqrt(kxv * kxv + kyv * kyv);
-      const bool keep = kx < p.kx_keep && (ns < 0 ? -ns : ns) < p.ky_keep;
-      const T lam = (t.depth == 3) ? filter_factor<T>(kk, T(p.filt_kf), T(p.filt_beta2)) : T(1);
-      const V a = (NACC == 1 || t.acc == 0) ? acc[0][r] : acc[NACC - 1][r];
-      if (t.mask == 2) {
-        // (M D - 1) a: projection correction, D = Lambda (depth 3) or 1
-        ColTerm u = t;
-        u.depth = 0;
-        const T mfac = (keep ? lam : T(0)) - T(1);
-        x[r] = cscale(apply_term<T>(u, a, kk, kxv, kyv, T(0), T(0), lam), mfac);
-      } else {
-        const V ts = dts[ni];
-        x[r] = apply_term<T>(t, a, kk, kxv, kyv, ts.x, ts.y, lam);
-        if (t.mask == 1 && !keep) x[r] = mk<V>(T(0), T(0));
-      }
+      x[r] = cconj(cmul_ipow(acc[ni], __ldg(tab + ni), ph));
     }
     if constexpr (NY > 1) {
       group_sync<C::WARP>();
-      fft_block<NY, RC, +1>(x, sc, j, tw);
+      fft_block<NY, RC, -1>(x, sc, j, tw);
 #pragma unroll
-      for (int r = 0; r < RC; ++r) x[r] = sc[pad(j + r * TPC)];
+      for (int r = 0; r < RC; ++r) x[r] = cconj(sc[pad(j + r * TPC)]);
+    } else {
+      x[0] = cconj(x[0]);
+    }
+    if (o == 0 && p.npass > 0 && act) {
+      for (int q = 0; q < p.npass; ++q) {
+        const V* ps = reinterpret_cast<const V*>(p.pass[q].ptr) + member * p.pass[q].stride + col_off;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[j + r * TPC]);
+      }
     }
     if (act) {
       V* dst = reinterpret_cast<V*>(p.buf[t.in].ptr) + member * p.buf[t.in].stride + col_off;
@@ -578,6 +606,83 @@ k_col(const __grid_constant__ ColParams p) {
       for (int r = 0; r < RC; ++r) dst[j + r * TPC] = x[r];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Multiplier tables: the real factor of a ColTerm for every stored mode
+// (kx < W, all ny), evaluated in FP64 and rounded to the working precision.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)s.W * s.ny) return;
+  const int kx = (int)(idx / s.ny), n = (int)(idx % s.ny);
+  const int ns = (s.ny == 1) ? 0 : (n < s.ny / 2 ? n : n - s.ny);
+  const double kxv = kx * s.two_pi_over_Lx, kyv = ns * s.two_pi_over_Ly;
+  const double k = sqrt(kxv * kxv + kyv * kyv);
+  double tk = 0.0, sk = 1.0;
+  if (k > 0.0) {
+    if (isinf(s.h0)) {
+      tk = 1.0;
+      sk = 0.0;
+    } else {
+      const double e = exp(-k * s.h0);
+      tk = tanh(k * s.h0);
+      sk = 2.0 * e / (1.0 + e * e);
+    }
+  }
+  const double lam = s.filt_kf > 0.0 ? exp(-pow(k / s.filt_kf, s.filt_beta2)) : 1.0;
+  double kp = 1.0;
+  const int ap = s.kpow < 0 ? -s.kpow : s.kpow;
+  for (int i = 0; i < ap; ++i) kp *= k;
+  if (s.kpow < 0) kp = k > 0.0 ? 1.0 / kp : 0.0;
+  double f = s.c * kp;
+  const double d = s.depth == 1 ? tk : (s.depth == 2 ? sk : (s.depth == 3 ? lam : 1.0));
+  for (int i = 0; i < s.gx; ++i) f *= kxv;
+  for (int i = 0; i < s.gy; ++i) f *= kyv;
+  const bool keep = kx < s.kx_keep && (ns < 0 ? -ns : ns) < s.ky_keep;
+  if (s.mask == 2) f *= (keep ? d : 0.0) - 1.0;
+  else f *= d * ((s.mask == 1 && !keep) ? 0.0 : 1.0);
+  out[idx] = T(f);
+}
+
+template <typename T>
+cudaError_t launch_coef_table_impl(void* out, const TableSpec& s, cudaStream_t st) {
+  const long long n = (long long)s.W * s.ny;
+  k_coef_table<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<T*>(out), s);
+  return cudaGetLastError();
+}
+
+// Host-visible doubles <-> state storage of the working precision.
+template <typename T>
+__global__ void k_state_from_double(const double* __restrict__ src, void* __restrict__ dst, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if constexpr (sizeof(T) == 8) {
+    reinterpret_cast<double*>(dst)[i] = src[i];
+  } else {
+    const float hi = float(src[i]);
+    const float lo = float(src[i] - double(hi));
+    reinterpret_cast<float2*>(dst)[i] = make_float2(hi, lo);
+  }
+}
+template <typename T>
+__global__ void k_state_to_double(const void* __restrict__ src, double* __restrict__ dst, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if constexpr (sizeof(T) == 8) {
+    dst[i] = reinterpret_cast<const double*>(src)[i];
+  } else {
+    const float2 v = reinterpret_cast<const float2*>(src)[i];
+    dst[i] = double(v.x) + double(v.y);
+  }
+}
+template <typename T>
+cudaError_t state_convert_impl(const void* src, void* dst, long long n, bool to_double, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (to_double) k_state_to_double<T><<<blocks, 256, 0, st>>>(src, reinterpret_cast<double*>(dst), n);
+  else k_state_from_double<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const double*>(src), dst, n);
+  return cudaGetLastError();
 }
 
 // ===========================================================================
@@ -593,11 +698,8 @@ cudaError_t prepare_nx() {
 
 template <typename T, int NY>
 cudaError_t prepare_ny() {
-  cudaError_t e = cudaFuncSetAttribute(k_col<T, NY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)col_smem<T, NY>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_col<T, NY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem<T, NY>());
+  return cudaFuncSetAttribute(k_col<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)col_smem<T, NY>(kMaxColAcc));
 }
 
 template <typename T, int NX>
@@ -620,12 +722,10 @@ cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
 
 template <typename T, int NY>
 cudaError_t launch_col_n(const ColParams& p, cudaStream_t st) {
-  using C = ColCfg<NY>;
+  using C = ColCfg<T, NY>;
+  if (p.nacc < 1 || p.nacc > kMaxColAcc) return cudaErrorInvalidValue;
   const int blocks = (p.cols_total + C::CPB - 1) / C::CPB;
-  if (p.nacc > 1)
-    k_col<T, NY, 2><<<blocks, C::THREADS, col_smem<T, NY>(), st>>>(p);
-  else
-    k_col<T, NY, 1><<<blocks, C::THREADS, col_smem<T, NY>(), st>>>(p);
+  k_col<T, NY><<<blocks, C::THREADS, col_smem<T, NY>(p.nacc), st>>>(p);
   return cudaGetLastError();
 }
 

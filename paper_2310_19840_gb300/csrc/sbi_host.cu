@@ -65,6 +65,7 @@ struct Group {
   double* out64 = nullptr;   // conversion buffer for one member's field
   int* d_active = nullptr;   // per-member flags for single-member passes
   std::map<std::string, void*> mixed;
+  std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
   size_t mixed_elems() const { return (size_t)ny * W; }
 };
@@ -299,8 +300,41 @@ struct Planner {
     t.mask = (uint8_t)mask;
     return t;
   }
+  // Device table of a multiplier (created once per group and key).
+  const void* table(const ColTerm& t) {
+    char key[160];
+    snprintf(key, sizeof(key), "%.17g|%d|%d|%d|%d|%d", t.c, t.kpow, t.depth, t.gx, t.gy, t.mask);
+    auto it = g.tables.find(key);
+    if (it != g.tables.end()) return it->second;
+    void* p = dalloc(c, (size_t)g.W * g.ny * c->real_size);
+    if (!p) {
+      oom = true;
+      return nullptr;
+    }
+    TableSpec s{};
+    s.W = g.W;
+    s.ny = g.ny;
+    s.kx_keep = g.kx_keep;
+    s.ky_keep = g.ky_keep;
+    s.two_pi_over_Lx = 2.0 * M_PI / g.Lx;
+    s.two_pi_over_Ly = g.two_d ? 2.0 * M_PI / g.Ly : 0.0;
+    s.h0 = g.deep ? INFINITY : g.h0;
+    s.filt_kf = c->filter_on() ? c->opt.filt_beta1 * c->opt.k_ref : 0.0;
+    s.filt_beta2 = c->opt.filt_beta2;
+    s.c = t.c;
+    s.kpow = t.kpow;
+    s.depth = t.depth;
+    s.gx = t.gx;
+    s.gy = t.gy;
+    s.mask = t.mask;
+    cudaError_t e = c->fp64 ? launch_coef_table<double>(p, s, c->cap) : launch_coef_table<float>(p, s, c->cap);
+    if (e != cudaSuccess) oom = true;
+    g.tables[key] = p;
+    return p;
+  }
+
   Pass col(const std::vector<ColIn>& ins, const std::vector<std::pair<std::string, ColTerm>>& outs,
-           int nacc) {
+           int nacc, const std::vector<std::string>& passthrough = {}) {
     ColParams p;
     std::memset(&p, 0, sizeof(p));
     p.W = g.W;
@@ -333,6 +367,7 @@ struct Planner {
       for (auto t : ins[i].terms) {
         t.in = (uint8_t)i;
         t.c *= scale;
+        t.tab = table(t);
         p.terms[nt++] = t;
       }
     }
@@ -342,15 +377,22 @@ struct Planner {
     for (size_t o = 0; o < outs.size(); ++o) {
       ColTerm t = outs[o].second;
       t.in = (uint8_t)(p.nin + o);
+      t.tab = table(t);
       p.buf[p.nin + o] = mref(outs[o].first);
       p.outs[o] = t;
     }
     p.nouts = (int)outs.size();
+    if (passthrough.size() > 8) {
+      oom = true;
+    } else {
+      for (size_t q = 0; q < passthrough.size(); ++q) p.pass[q] = mref(passthrough[q]);
+      p.npass = (int)passthrough.size();
+    }
     Pass ps{};
     ps.kind = PK_COL;
     ps.nsize = g.ny;
     ps.col = p;
-    ps.bytes = mixed_bytes() * (ins.size() + outs.size());
+    ps.bytes = mixed_bytes() * (ins.size() + outs.size() + passthrough.size());
     return ps;
   }
 
@@ -376,16 +418,17 @@ struct Planner {
     return col(ins, outs, 2);
   }
 
-  // Row l: eager products of order l-1 (see file header).
+  // Row l: eager products of order l-1 (see file header), formed as running
+  // products (the slot is multiplied by eta or delta once per product).
   Pass plan_row_level(int l) {
     const int M = c->opt.order;
     RowB r = row_begin();
     c2r(r, 0, {S("V%d", l - 1)});
-    for (int j = 1; j <= M - (l - 1); ++j) prod(r, 0, j, 0, 0, 1.0, S2("P%d_%d", j, l - 1));
+    for (int j = 1; j <= M - (l - 1); ++j) prod(r, 0, 1, 0, 2, 1.0, S2("P%d_%d", j, l - 1));
     if (l == 2) {
       for (char d : dims()) {
         c2r(r, 0, {std::string("dphi") + d});
-        for (int j = 1; j <= M - 1; ++j) prod(r, 0, j, 0, 0, 1.0, S("Q%d", j) + d);
+        for (int j = 1; j <= M - 1; ++j) prod(r, 0, 1, 0, 2, 1.0, S("Q%d", j) + d);
       }
     }
     bool use_delta = false;
@@ -393,10 +436,12 @@ struct Planner {
       const int m = l - 1;
       for (char d : dims()) {
         c2r(r, 0, {S("db%d", m) + d});
+        int jprev = 0;
         for (int j = 1; j <= M - m; ++j) {
           const int ll = j + m;
           if (ll <= M - 1 || (j % 2 == 1)) {
-            prod(r, 0, 0, j, 0, 1.0, S2("R%d_%d", j, m) + d);
+            prod(r, 0, 0, j - jprev, 2, 1.0, S2("R%d_%d", j, m) + d);
+            jprev = j;
             use_delta = true;
           }
         }
@@ -447,18 +492,23 @@ struct Planner {
       }
     }
     std::vector<std::pair<std::string, ColTerm>> outs;
-    outs.push_back({S("V%d", l), term(0, 1.0, 0, 0, 0, 0, 1)});
+    // the last order is written as the sum V^_1 + ... + V^_M (mixed), the only
+    // form in which it is used
+    const bool last = l == M;
+    outs.push_back({last ? std::string("Vsum") : S("V%d", l), term(0, 1.0, 0, 0, 0, 0, 1)});
     if (phi_out) {
       for (char d : dims())
         outs.push_back({S("db%d", l) + d, term(1, 1.0, 0, 0, d == 'x', d == 'y', 1)});
     }
-    return col(ins, outs, phi_out ? 2 : 1);
+    std::vector<std::string> pass;
+    if (last)
+      for (int q = 1; q < M; ++q) pass.push_back(S("V%d", q));
+    return col(ins, outs, phi_out ? 2 : 1, pass);
   }
 
+  // mixed buffers whose sum is F_x{V}
   std::vector<std::string> v_names() const {
-    std::vector<std::string> v;
-    for (int l = 1; l <= c->opt.order; ++l) v.push_back(S("V%d", l));
-    return v;
+    return {c->opt.order == 1 ? std::string("V1") : std::string("Vsum")};
   }
 
   void plan_diag(std::vector<Pass>& out) {
@@ -700,8 +750,19 @@ __global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst,
 
 // Partial sums of eta and 1/2 (phi V + g eta^2) over fixed chunks of one
 // member, each chunk reduced by one block in a fixed tree order.
+// one state value as a double (hi + lo float pairs in the FP32 path)
 template <typename T>
-__global__ void k_invariant_partials(const double* __restrict__ eta, const double* __restrict__ phi,
+__device__ __forceinline__ double state_value(const void* base, long long i) {
+  if constexpr (sizeof(T) == 8) {
+    return reinterpret_cast<const double*>(base)[i];
+  } else {
+    const float2 v = reinterpret_cast<const float2*>(base)[i];
+    return double(v.x) + double(v.y);
+  }
+}
+
+template <typename T>
+__global__ void k_invariant_partials(const void* __restrict__ eta, const void* __restrict__ phi,
                                      const T* __restrict__ V, long long n, double g, int chunk,
                                      double* __restrict__ out) {
   __shared__ double sm[2][256];
@@ -710,9 +771,9 @@ __global__ void k_invariant_partials(const double* __restrict__ eta, const doubl
   for (int i = threadIdx.x; i < chunk; i += blockDim.x) {
     const long long q = base + i;
     if (q < n) {
-      const double h = eta[q];
+      const double h = state_value<T>(eta, q);
       m += h;
-      e += 0.5 * (phi[q] * double(V[q]) + g * h * h);
+      e += 0.5 * (state_value<T>(phi, q) * double(V[q]) + g * h * h);
     }
   }
   sm[0][threadIdx.x] = m;
@@ -1010,11 +1071,20 @@ int sbi_set_state(sbi_ctx* c, int member, const double* eta, const double* phi, 
   if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
   Group& g = c->groups[c->where[member].first];
   const size_t off = (size_t)c->where[member].second * g.phys_elems();
-  const size_t bytes = g.phys_elems() * 8;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const long long np = (long long)g.phys_elems();
   CK(cudaStreamSynchronize(c->stream), "sync");
-  CK(cudaMemcpyAsync(g.eta0 + off, eta, bytes, kind, c->cap), "copy eta");
-  CK(cudaMemcpyAsync(g.phi0 + off, phi, bytes, kind, c->cap), "copy phi");
+  const double* srcs[2] = {eta, phi};
+  double* dsts[2] = {g.eta0 + off, g.phi0 + off};
+  for (int q = 0; q < 2; ++q) {
+    const double* src = srcs[q];
+    if (!on_device) {
+      CK(cudaMemcpyAsync(g.out64, srcs[q], np * 8, cudaMemcpyHostToDevice, c->cap), "copy state");
+      src = g.out64;
+    }
+    cudaError_t e = c->fp64 ? state_convert<double>(src, dsts[q], np, false, c->cap)
+                            : state_convert<float>(src, dsts[q], np, false, c->cap);
+    CK(e, "state conversion");
+  }
   // dealias the stored state of this member only: (M - 1) correction; then
   // refresh this member's working copies
   std::vector<int> act(g.n, 0);
@@ -1042,10 +1112,17 @@ int sbi_get_state(sbi_ctx* c, int member, double* eta, double* phi, int on_devic
   if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
   Group& g = c->groups[c->where[member].first];
   const size_t off = (size_t)c->where[member].second * g.phys_elems();
-  const size_t bytes = g.phys_elems() * 8;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  CK(cudaMemcpyAsync(eta, g.eta0 + off, bytes, kind, c->stream), "copy eta");
-  CK(cudaMemcpyAsync(phi, g.phi0 + off, bytes, kind, c->stream), "copy phi");
+  const long long np = (long long)g.phys_elems();
+  const double* srcs[2] = {g.eta0 + off, g.phi0 + off};
+  double* dsts[2] = {eta, phi};
+  for (int q = 0; q < 2; ++q) {
+    double* dst = on_device ? dsts[q] : g.out64;
+    cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], dst, np, true, c->stream)
+                            : state_convert<float>(srcs[q], dst, np, true, c->stream);
+    CK(e, "state conversion");
+    if (!on_device)
+      CK(cudaMemcpyAsync(dsts[q], g.out64, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy state");
+  }
   CK(cudaStreamSynchronize(c->stream), "get_state");
   return SBI_OK;
 }

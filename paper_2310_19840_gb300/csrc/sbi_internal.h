@@ -34,7 +34,8 @@ constexpr uint8_t kNone = 255;
 
 enum RowOpKind : uint8_t {
   ROP_C2R = 0,   // slot <- c2r(sum of mixed bufs [a, a+b)); optional physical copy to dst
-  ROP_PROD = 1,  // mixed dst <- r2c(coef * eta^a * delta^b * w^c * slot)   (slot kNone: 1)
+  ROP_PROD = 1,  // mixed dst <- r2c(coef * eta^a * delta^b * w^(c&1) * slot)  (slot kNone: 1);
+                 // c & 2: running product, the slot itself becomes eta^a delta^b slot
   ROP_N2 = 2,    // mixed dst <- r2c(dynamic-condition right-hand side) from slots
                  // slot..slot+4 = V, eta_x, eta_y, phi_x, phi_y (2-D) or
                  // V, eta_x, phi_x (1-D); coef = gravity
@@ -74,13 +75,18 @@ struct RowParams {
   const void* tw;
 };
 
+// One multiplier of a column pass: c k^p D(k) (i kx)^gx (i ky)^gy, times the
+// dealias mask M (mask = 1) or (M D - 1) without D elsewhere (mask = 2).  The
+// real factor is tabulated per mode once per context (tab, layout [kx][ny]);
+// the kernels apply tab and the phase i^(gx+gy).
 struct ColTerm {
+  const void* tab; // per-mode real factor in the working precision
   uint8_t in;     // input buffer (local index); for outputs: destination buffer
   uint8_t acc;    // accumulator index
   uint8_t gx, gy; // powers of (i kx), (i ky)
   int8_t kpow;    // power of |k| (negative powers vanish at k = 0)
   uint8_t depth;  // 0: 1, 1: tanh(k h0), 2: sech(k h0), 3: Lambda(k) = exp(-(k/kf)^beta2)
-  uint8_t mask;   // outputs: 1 multiplies by the dealias mask, 2 by (mask - 1) (projection correction)
+  uint8_t mask;   // 0: none, 1: dealias mask, 2: (mask * D - 1) projection correction
   uint8_t pad_;
   double c;
 };
@@ -95,11 +101,20 @@ struct ColParams {
   int kx_keep, ky_keep;     // keep m < kx_keep and |n| < ky_keep
   double filt_kf, filt_beta2;
   double* norm_out;         // optional per-member FP64 partial norms of accumulator 0 (nullptr: off)
+  int npass;                // mixed buffers added unchanged to output 0 after its inverse FFT
+  BufRef pass[8];
   int term_begin[kMaxColBufs + 1];   // terms sorted by input
   ColTerm terms[kMaxColTerms];
   ColTerm outs[kMaxColOuts];
   BufRef buf[kMaxColBufs];
   const void* tw;
+};
+
+// Parameters of one multiplier table (see ColTerm).
+struct TableSpec {
+  int W, ny, kx_keep, ky_keep;
+  double two_pi_over_Lx, two_pi_over_Ly, h0, filt_kf, filt_beta2, c;
+  int kpow, depth, gx, gy, mask;
 };
 
 enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2 };
@@ -129,9 +144,15 @@ struct RkParams {
 // first launch.  Unsupported sizes return cudaErrorInvalidValue.
 template <typename T> cudaError_t prepare_row_kernels(int nx);
 template <typename T> cudaError_t prepare_col_kernels(int ny);
+struct TableSpec;
+template <typename T> cudaError_t launch_coef_table(void* out, const TableSpec& s, cudaStream_t st);
 template <typename T> cudaError_t launch_row(int nx, const RowParams& p, cudaStream_t st);
 template <typename T> cudaError_t launch_col(int ny, const ColParams& p, cudaStream_t st);
 template <typename T> cudaError_t launch_rk(int nx, const RkParams& p, cudaStream_t st);
+// Convert n state values between host-visible doubles and the state storage
+// of the working precision (double, or hi/lo float pairs for FP32).
+template <typename T> cudaError_t state_convert(const void* src, void* dst, long long n, bool to_double,
+                                                cudaStream_t st);
 // rows per block for a row pass with nslots physical slots (0: does not fit)
 template <typename T> int row_rpc(int nx, int W, int nslots);
 

@@ -163,3 +163,27 @@ def test_invariants_match_oracle(sbi, prec):
     mo, eo = O.invariants(pb, eta, phi)
     assert abs(m - mo) <= 1e-12 * abs(mo)
     assert abs(e - eo) <= TOL[prec] * abs(eo)
+
+
+@pytest.mark.parametrize("nx,ny", [(4096, 1), (16, 2048), (4096, 8), (1024, 1024), (512, 512),
+                                   (256, 256), (2048, 16), (4096, 2048)])
+def test_every_kernel_size_fp32_matches_fp64(sbi, nx, ny):
+    # Largest and extreme grids: each size instantiation launches in both
+    # precisions and the FP32 path agrees with the FP64 path (variable depth).
+    # The grid spacing is fixed (0.05 m) so k|delta| stays below ~1 at every
+    # size: FP32 round-off is amplified by (k delta)^j / j! in the delta terms.
+    # The spectra are spread over the band (as in the wave workloads): with all
+    # the energy in the box-scale mode V would be ~k_max/k_1 times smaller
+    # than the FP32 round-off of the short modes.
+    Lx, Ly, h0 = 0.05 * nx, (0.05 * ny if ny > 1 else 1.0), 0.6
+    delta = W.random_field(nx, ny, 3, amplitude=0.06, band=0.2, slope=0.5)
+    eta = W.random_field(nx, ny, 4, amplitude=0.03, band=0.2, slope=0.5)
+    phi = W.random_field(nx, ny, 5, amplitude=0.2, band=0.2, slope=0.5)
+    out = {}
+    for prec in (1, 0):
+        ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec)
+        ctx.set_state(0, eta, phi)
+        out[prec] = ctx.vertical_velocity(0)
+        ctx.close()
+    assert np.all(np.isfinite(out[1]))
+    assert rel(out[0], out[1]) < TOL[0]
