@@ -159,6 +159,39 @@ int sbi_step_bytes(const sbi_ctx* ctx, int family, double* bytes);
 /* Number of kernel launches in one captured step. */
 int sbi_step_launches(const sbi_ctx* ctx, int* launches);
 
+/* Mass and energy of one state without any device allocation.  (This entry
+ * point has no counterpart in the paper; it serves callers that may not
+ * allocate device memory.)
+ *
+ * Some callers cannot call cudaMalloc or cudaFree: code running inside
+ * another framework's memory pool or a fixed arena, plugins that are handed
+ * device buffers only, and hosts that forbid allocation (and the device
+ * synchronisation it implies) once they are running.  This call computes the
+ * same reductions as sbi_invariants, mass = int eta dA and energy =
+ * 1/2 int (V phi~ + g eta^2) dA in FP64, from caller-owned DEVICE arrays eta,
+ * phi and V (nx*ny doubles each, row-major; V as returned by
+ * sbi_vertical_velocity with on_device = 1), on the caller's stream
+ * (cuda_stream, NULL: legacy default stream), and writes the two host doubles
+ * *mass and *energy (it synchronises that stream).  It needs no context.
+ *
+ * Its partial sums live in one file-scope device array of 64 KB (room for
+ * 4096 chunks of 8192 points): grids of more than 33,554,432 points are
+ * rejected with SBI_EINVAL.  Every device that loads the library holds the
+ * array until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised by the
+ * caller.  Nothing in the array needs to start at zero (each call writes every
+ * partial sum before reading it).  No cudaMalloc, cudaFree or other allocating
+ * routine is called.  Errors: SBI_EINVAL (NULL pointer, bad grid, too large),
+ * SBI_ECUDA; the message is returned by sbi_noalloc_last_error(). */
+int sbi_invariants_noalloc(const sbi_grid* g, double gravity, const double* eta,
+                           const double* phi, const double* V, void* cuda_stream,
+                           double* mass, double* energy);
+
+/* Message of the last failing sbi_invariants_noalloc call on this thread. */
+const char* sbi_noalloc_last_error(void);
+
 /* Message of the last failing call on ctx (or of the last failing create when
  * ctx is NULL).  Never NULL. */
 const char* sbi_last_error(const sbi_ctx* ctx);

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsbi.so")
-SOURCES = ["inst_col_f32.cu", "inst_col_f64.cu", "inst_row_f32.cu", "inst_row_f64.cu", "sbi_host.cu"]
+SOURCES = ["inst_col_f32.cu", "inst_col_f64.cu", "inst_row_f32.cu", "inst_row_f64.cu", "sbi_host.cu",
+           "sbi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -63,6 +63,10 @@ EXPORTS = {
                                    C.POINTER(C.c_int)]),
     "sbi_step_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sbi_step_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]),
+    "sbi_noalloc_last_error": (C.c_char_p, []),
     "sbi_last_error": (C.c_char_p, [C.c_void_p]),
     "sbi_destroy": (None, [C.c_void_p]),
 }
@@ -114,6 +118,26 @@ def _ptr(a, dtype=np.float64):
         pass
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data, 0, arr
+
+
+def invariants_noalloc(grid, gravity, eta, phi, V, stream=None):
+    """Mass and energy from device arrays without any device allocation
+    (sbi_invariants_noalloc); eta, phi, V are contiguous float64 CUDA tensors."""
+    lib = load()
+    g = sbi_grid(grid[0], grid[1], grid[2], grid[3] if len(grid) > 3 else 1.0)
+    ptrs = []
+    for a in (eta, phi, V):
+        p, dev, keep = _ptr(a)
+        if not dev:
+            raise ValueError("sbi_invariants_noalloc takes device arrays")
+        ptrs.append(p)
+    m, e = C.c_double(), C.c_double()
+    st = C.c_void_p(int(stream)) if stream is not None else None
+    rc = lib.sbi_invariants_noalloc(C.byref(g), float(gravity), ptrs[0], ptrs[1], ptrs[2], st,
+                                    C.byref(m), C.byref(e))
+    if rc != SBI_OK:
+        raise SbiError(rc, lib.sbi_noalloc_last_error().decode())
+    return m.value, e.value
 
 
 class Context:
