@@ -48,12 +48,28 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, members=None):
+def make_workload(name, members=None, rank=0):
+    """The workload of one rank.  Ranks are independent replicas (weak
+    scaling): on the batched crossing seas rank r advances its own set of
+    realisations (random phases seeded from 1000 + 96 r), no data is exchanged."""
     import workloads as W
-    if name == "crossing_batch" and members:
-        s, l = (int(v) for v in members.split(","))
-        return W.crossing_batch(n_small=s, n_large=l)
+    if name == "crossing_batch":
+        s, l = (64, 32)
+        if members:
+            s, l = (int(v) for v in members.split(","))
+        return W.crossing_batch(n_small=s, n_large=l, seed0=1000 + (s + l) * rank)
     return getattr(W, name)()
+
+
+def reduce_max(value, world, device=None):
+    """Max of a per-rank float over all ranks (the timed region's wall time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload_config(wl):
@@ -247,6 +263,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if os.environ.get("MASTER_ADDR") is None and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
     import numpy as np
     import torch
     rank, world, local = dist_env()
@@ -258,7 +276,7 @@ def main():
     ge.build()
     from paper_2310_19840_gb300 import sbi
 
-    wl = make_workload(args.workload, args.members)
+    wl = make_workload(args.workload, args.members, rank)
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
     ctx = make_context(sbi, wl, prec, stream.cuda_stream)
@@ -278,10 +296,7 @@ def main():
     clocks.start()
     secs = time_steps(ctx, torch, stream, wl.dt, args.steps, args.warmup)
     clk = clocks.stop()
-    t = torch.tensor([secs], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    secs = float(t.item())
+    secs = reduce_max(secs, world, device="cuda")
     pts = wl.points
     value = pts * args.steps * world / secs
 

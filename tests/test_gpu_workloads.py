@@ -1,0 +1,216 @@
+"""GPU checks on the workloads at their full sizes, in the launch configuration
+the benchmark uses, plus failure detection and checkpoint/restart.
+
+Full-size outputs are compared with the oracle where it runs in seconds
+(1-D grids, 256^2 and 512^2 members); for the 4096 x 2048 variable-depth grid
+the checks are properties that hold at any size: agreement of the FP32 and FP64
+paths, equivariance under a shift by one grid cell, linearity of V in phi~,
+and exact mass conservation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbi_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sbi():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2310_19840_gb300 import sbi as s
+    return s
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def problem_of(wl, m):
+    g = O.Grid(m.nx, m.ny, m.Lx, m.Ly if m.ny > 1 else 1.0)
+    return O.Problem(g, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
+                     sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
+                     filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+
+
+def context_of(sbi, wl, members, prec, **kw):
+    ms = [wl.members[i] for i in members]
+    grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in ms]
+    depths = [(m.h0 - m.delta) if m.delta is not None else None for m in ms]
+    return sbi.Context(grids, wl.gravity, depths, h0=ms[0].h0, order=wl.order,
+                       alias_frac=wl.alpha, precision=prec, filt_beta1=wl.filt_beta1,
+                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref, sponge_w=wl.sponge_w,
+                       sponge_nu=wl.sponge_nu, **kw)
+
+
+def test_solitary_wave_run_energy_and_speed(sbi):
+    # The 1-D solitary wave (N=256, h=1, a/h=0.3), FP64 GPU path over 400 steps:
+    # energy conserved to 1e-4 (Sec. 3.1 reports ~1e-5), crest speed within 3% of
+    # sqrt(g(h+a)), and the state equal to the oracle's to 1e-9.
+    wl = W.solitary_1d()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    ctx = context_of(sbi, wl, [0], 1)
+    ctx.set_state(0, eta, phi)
+    _, E0 = ctx.invariants(0)
+    ctx.step(wl.dt, 400)
+    e, p = ctx.get_state(0)
+    _, E1 = ctx.invariants(0)
+    assert abs(E1 - E0) / E0 < 1e-4
+    eo, po = O.step(pb, eta, phi, wl.dt, 400)
+    assert rel(e, eo) < 1e-9 and rel(p, po) < 1e-9
+
+    def crest(f):
+        f = f[0]
+        i = int(np.argmax(f))
+        fm, f0, fp = f[i - 1], f[i], f[(i + 1) % f.size]
+        return (i + 0.5 * (fm - fp) / (fm - 2 * f0 + fp)) * m.Lx / m.nx
+    speed = (crest(e) - crest(eta)) / (400 * wl.dt)
+    assert abs(speed - wl.notes["c"]) / wl.notes["c"] < 0.03
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_submerged_bar_full_size_steps(sbi, prec, tol):
+    # N=4096 bar with sponge layers: a few RK4 steps against the oracle.
+    wl = W.bar_1d()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    ctx = context_of(sbi, wl, [0], prec)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    assert rel(V, O.vertical_velocity(eta, phi, m.delta, m.h0, pb.grid)) < tol
+    ctx.step(wl.dt, 3)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, wl.dt, 3)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-11), (0, 1e-5)])
+def test_stokes_full_size_diagnostic(sbi, prec, tol):
+    wl = W.stokes_2d()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    ctx = context_of(sbi, wl, [0], prec)
+    ctx.set_state(0, eta, phi)
+    assert rel(ctx.vertical_velocity(0), O.vertical_velocity(eta, phi, None, m.h0, pb.grid)) < tol
+
+
+def test_crossing_members_in_the_bench_batch(sbi):
+    # The benchmark's 96-member batch (FP32): the first 256^2 and the first
+    # 512^2 member after one RK4 step against the oracle.
+    wl = W.crossing_batch()
+    ctx = context_of(sbi, wl, list(range(len(wl.members))), 0, check_finite=1)
+    start = {}
+    for i, m in enumerate(wl.members):
+        if i in (0, 64):
+            # both sides start from the same projected (dealiased, filtered) state
+            pb = problem_of(wl, m)
+            start[i] = (pb, O.project(pb, m.eta), O.project(pb, m.phi))
+            ctx.set_state(i, start[i][1], start[i][2])
+        else:
+            ctx.set_state(i, m.eta, m.phi)
+    ctx.step(wl.dt, 1)
+    for i in (0, 64):
+        pb, e0, p0 = start[i]
+        eo, po = O.step(pb, e0, p0, wl.dt, 1)
+        e, p = ctx.get_state(i)
+        assert rel(e, eo) < 1e-5 and rel(p, po) < 1e-5
+
+
+def test_large_variable_depth_properties(sbi):
+    # 4096 x 2048 variable-depth crossing sea: FP32 vs FP64 paths, shift
+    # equivariance, linearity in phi~ and exact mass conservation.
+    wl = W.large_variable()
+    m = wl.members[0]
+    grid = (m.nx, m.ny, m.Lx, m.Ly)
+    out = {}
+    dA = (m.Lx / m.nx) * (m.Ly / m.ny)
+    for prec in (1, 0):
+        ctx = context_of(sbi, wl, [0], prec)
+        ctx.set_state(0, m.eta, m.phi)
+        out[prec] = ctx.vertical_velocity(0)
+        # mass: F{V}(0) = 0, so the change over a step is the round-off of the
+        # increment dt sum(V) in the path's precision
+        mass0, _ = ctx.invariants(0)
+        ctx.step(wl.dt, 1)
+        mass1, _ = ctx.invariants(0)
+        eps = 2.0 ** -52 if prec == 1 else 2.0 ** -23
+        bound = 20.0 * eps * wl.dt * np.sum(np.abs(out[prec])) * dA
+        assert abs(mass1 - mass0) <= bound, (prec, mass1 - mass0, bound)
+        ctx.close()
+    err = rel(out[0], out[1])
+    print(f"large_variable FP32 vs FP64 V rel L2 = {err:.3e}")
+    assert err < 1e-5
+    # shift by one cell in x (delta, eta and phi~ together): V shifts with them
+    ctx = sbi.Context([grid], wl.gravity, [np.roll(m.h0 - m.delta, 1, axis=1)], h0=m.h0,
+                      precision=1, filt_beta1=wl.filt_beta1, filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+    ctx.set_state(0, np.roll(m.eta, 1, axis=1), np.roll(m.phi, 1, axis=1))
+    Vs = ctx.vertical_velocity(0)
+    assert rel(Vs, np.roll(out[1], 1, axis=1)) < 1e-11
+    # linearity in phi~ at fixed eta, delta (same shifted configuration)
+    ctx.set_state(0, np.roll(m.eta, 1, axis=1), 2.5 * np.roll(m.phi, 1, axis=1))
+    assert rel(ctx.vertical_velocity(0), 2.5 * Vs) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_checkpoint_restart_is_bit_exact(sbi, prec):
+    # step(n) equals step(k) + get_state / set_state + step(n - k) bit for bit.
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid = O.Grid(nx, ny, Lx, Ly)
+    delta = W.random_field(nx, ny, 41, amplitude=0.05)
+    pb = O.Problem(grid, 9.81, h0, delta=delta)
+    eta = O.project(pb, W.random_field(nx, ny, 42, amplitude=0.03))
+    phi = O.project(pb, W.random_field(nx, ny, 43, amplitude=0.2))
+    a = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec,
+                    set_state_dealias=0)
+    a.set_state(0, eta, phi)
+    a.step(0.02, 5)
+    ea, pa = a.get_state(0)
+    b = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec,
+                    set_state_dealias=0)
+    b.set_state(0, eta, phi)
+    b.step(0.02, 2)
+    e2, p2 = b.get_state(0)
+    c = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec,
+                    set_state_dealias=0)
+    c.set_state(0, e2, p2)
+    c.step(0.02, 3)
+    ec, pc = c.get_state(0)
+    assert np.array_equal(ea, ec) and np.array_equal(pa, pc)
+
+
+def test_nonfinite_state_is_reported(sbi):
+    # A NaN in the state is detected on the device after the step and reported
+    # as SBI_ENONFINITE (a flag the kernel sets; nothing traps).
+    nx, ny = 32, 16
+    eta = W.random_field(nx, ny, 51, amplitude=0.02)
+    phi = W.random_field(nx, ny, 52, amplitude=0.1)
+    eta[3, 5] = np.nan
+    ctx = sbi.Context([(nx, ny, 3.0, 2.0)], 9.81, None, h0=1.0, precision=0, set_state_dealias=0)
+    ctx.set_state(0, eta, phi)
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.step(0.01, 1)
+    assert ei.value.code == sbi.SBI_ENONFINITE
+    # the context stays usable
+    ctx.set_state(0, np.zeros((ny, nx)), np.zeros((ny, nx)))
+
+
+def test_bad_calls_fail_cleanly(sbi):
+    ctx = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0)
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.set_state(3, np.zeros(32), np.zeros(32))
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.step(-1.0, 1)
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.step(math.nan, 1)
+    assert ei.value.code == sbi.SBI_EINVAL

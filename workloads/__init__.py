@@ -333,7 +333,7 @@ def crossing_sea(nx: int, ny: int, Lx: float, Ly: float, h: float, seed: int,
 
 
 def crossing_batch(n_small: int = 64, n_large: int = 32, kp: float = KP_CROSSING,
-                   g: float = G) -> Workload:
+                   g: float = G, seed0: int = 1000) -> Workload:
     lam = 2.0 * np.pi / kp
     h = 5.0 / kp
     members = []
@@ -341,7 +341,7 @@ def crossing_batch(n_small: int = 64, n_large: int = 32, kp: float = KP_CROSSING
     for n, nl, cnt in ((256, 10, n_small), (512, 20, n_large)):
         for _ in range(cnt):
             L = nl * lam
-            eta, phi = crossing_sea(n, n, L, L, h, 1000 + idx, kp=kp, g=g)
+            eta, phi = crossing_sea(n, n, L, L, h, seed0 + idx, kp=kp, g=g)
             members.append(Member(n, n, L, L, h, eta, phi))
             idx += 1
     omega_p = math.sqrt(g * kp * math.tanh(kp * h))
