@@ -291,11 +291,12 @@ class Problem:
     filt_beta1: float = 0.0
     filt_beta2: float = 0.0
     k_ref: float = 1.0
+    adapt_tol: float = 0.0      # R9: 0 = fixed order
 
 
 def surface_rhs(pb: Problem, eta, phi):
     """(eta_t, phi~_t) of Eq. (prognostic) in physical space."""
-    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha)
+    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
     phi_t = dynamic_rhs(eta, phi, V, pb.gravity, pb.grid, pb.alpha)
     if pb.sponge_w is not None and pb.sponge_nu != 0.0:
         phi_t = phi_t - damping_pressure(phi, pb.sponge_w, pb.sponge_nu, pb.grid, pb.alpha)
@@ -337,7 +338,7 @@ def invariants(pb: Problem, eta, phi):
     """Mass int eta dA and energy 1/2 int (V phi~ + g eta^2) dA (Eq. energy)."""
     eta = np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
     phi = np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
-    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha)
+    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
     mass = float(np.sum(eta) * pb.grid.dA)
     energy = float(0.5 * np.sum(V * phi + pb.gravity * eta * eta) * pb.grid.dA)
     return mass, energy

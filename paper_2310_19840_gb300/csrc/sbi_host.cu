@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "../../include/sbi.h"
+#include "fft.cuh"
 #include "sbi_internal.h"
 
 using namespace sbi;
@@ -40,10 +41,29 @@ namespace {
 
 std::string g_create_error = "no error";
 
-enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2 };
-enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_COUNT = 3 };
+enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2, PK_CONV = 3 };
+
+// Device-side convergence test of the adaptive order (opt.adapt_tol > 0):
+// after order l, per member, inc = ||F{V_l}||^2 and tot = ||F{V_1 + .. + V_l}||^2
+// (Parseval on the mixed layout, FP64).  A member still iterating whose
+// inc <= tol^2 tot stops: its mixed sum is written to Vsum and its flag cleared,
+// so the passes of the higher orders skip it.
+constexpr int kConvBlocks = 64;   // partial sums per member
+struct ConvParams {
+  int phase;            // 0: reset flags, 1: partial norms, 2: write sums, 3: update flags
+  int nlev;             // l: buffers V_1..V_l
+  const void* V[7];
+  void* vsum;
+  long long stride;     // complex elements per member
+  int W, ny, n, level, last;
+  double tol2;
+  int *conv, *orders, *notconv;
+  double* red;          // [n][kConvBlocks][2]
+};
+enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_CONV = 3, FAM_COUNT = 4 };
 const char* kFamilyNames[FAM_COUNT] = {"k_col (column FFT + spectral combine)",
-                                       "k_row (row FFT + products)", "k_rk (RK4 stage)"};
+                                       "k_row (row FFT + products)", "k_rk (RK4 stage)",
+                                       "k_conv (adaptive-order test)"};
 
 struct Pass {
   PassKind kind;
@@ -51,6 +71,7 @@ struct Pass {
   RowParams row;
   ColParams col;
   RkParams rk;
+  ConvParams conv;
   double bytes;  // algorithmic device-memory traffic of the launch
 };
 
@@ -64,6 +85,10 @@ struct Group {
   void *eta_w = nullptr, *Vphys = nullptr, *delta = nullptr, *wout = nullptr;
   double* out64 = nullptr;   // conversion buffer for one member's field
   int* d_active = nullptr;   // per-member flags for single-member passes
+  int* d_conv = nullptr;     // adaptive order: 1 while a member still iterates
+  int* d_orders = nullptr;   // adaptive order: orders used by the last diagnostic
+  int* d_notconv = nullptr;  // adaptive order: tolerance not met at the highest order
+  double* d_red = nullptr;   // adaptive order: partial norms
   std::map<std::string, void*> mixed;
   std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
@@ -511,11 +536,52 @@ struct Planner {
     return {c->opt.order == 1 ? std::string("V1") : std::string("Vsum")};
   }
 
+  Pass plan_conv(int phase, int l) {
+    Pass ps{};
+    ps.kind = PK_CONV;
+    ConvParams& q = ps.conv;
+    q.phase = phase;
+    // the highest order exists only inside the sum Vsum: there the increment is
+    // Vsum - (V_1 + .. + V_{M-1}), read from the M - 1 lower-order buffers
+    q.nlev = (l == c->opt.order) ? l - 1 : l;
+    for (int m = 1; m <= q.nlev && m <= 7; ++m) q.V[m - 1] = mixed(S("V%d", m));
+    q.vsum = mixed("Vsum");
+    q.stride = (long long)g.mixed_elems();
+    q.W = g.W;
+    q.ny = g.ny;
+    q.n = g.n;
+    q.level = l;
+    q.last = l == c->opt.order;
+    q.tol2 = c->opt.adapt_tol * c->opt.adapt_tol;
+    q.conv = g.d_conv;
+    q.orders = g.d_orders;
+    q.notconv = g.d_notconv;
+    q.red = g.d_red;
+    ps.bytes = phase == 1 ? mixed_bytes() * l : (phase == 2 ? mixed_bytes() * (l + 1) : 0.0);
+    return ps;
+  }
+
   void plan_diag(std::vector<Pass>& out) {
+    const bool adapt = c->opt.adapt_tol > 0.0 && c->opt.order > 1;
+    if (adapt) out.push_back(plan_conv(0, 1));
     out.push_back(plan_col_a());
     for (int l = 2; l <= c->opt.order; ++l) {
-      out.push_back(plan_row_level(l));
-      out.push_back(plan_col_level(l));
+      Pass r = plan_row_level(l), q = plan_col_level(l);
+      if (adapt) {
+        r.row.active = g.d_conv;
+        q.col.active = g.d_conv;
+      }
+      out.push_back(r);
+      out.push_back(q);
+      if (adapt) {
+        if (l < c->opt.order) {
+          out.push_back(plan_conv(1, l));
+          out.push_back(plan_conv(2, l));
+        } else {
+          out.push_back(plan_conv(1, l));
+        }
+        out.push_back(plan_conv(3, l));
+      }
     }
   }
 
@@ -606,11 +672,126 @@ struct Planner {
   }
 };
 
+
+// ---------------------------------------------------------------------------
+// Adaptive-order convergence test (phases of ConvParams)
+// ---------------------------------------------------------------------------
+__global__ void k_conv_reset(ConvParams q, int order) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= q.n) return;
+  q.conv[m] = 1;
+  q.orders[m] = order;
+  q.notconv[m] = 0;
+}
+
+// Parseval weights on the mixed layout: kx = 0 once, kx > 0 twice (the
+// conjugate modes); the common factor ny cancels in the ratio.
+template <typename T>
+__global__ void k_conv_norms(ConvParams q) {
+  using V = cx<T>;
+  __shared__ double sm[2][256];
+  const int m = blockIdx.y;
+  double inc = 0.0, tot = 0.0;
+  if (q.conv[m]) {
+    const long long ne = (long long)q.W * q.ny;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+         e += (long long)gridDim.x * blockDim.x) {
+      const double w = (e / q.ny) == 0 ? 1.0 : 2.0;
+      double sr = 0.0, si = 0.0, lr = 0.0, li = 0.0;
+      for (int l = 0; l < q.nlev; ++l) {
+        const V v = reinterpret_cast<const V*>(q.V[l])[m * q.stride + e];
+        sr += double(v.x);
+        si += double(v.y);
+        if (l == q.nlev - 1) { lr = double(v.x); li = double(v.y); }
+      }
+      if (q.last) {   // V_M = Vsum - (V_1 + .. + V_{M-1})
+        const V t = reinterpret_cast<const V*>(q.vsum)[m * q.stride + e];
+        lr = double(t.x) - sr;
+        li = double(t.y) - si;
+        sr = double(t.x);
+        si = double(t.y);
+      }
+      inc += w * (lr * lr + li * li);
+      tot += w * (sr * sr + si * si);
+    }
+  }
+  sm[0][threadIdx.x] = inc;
+  sm[1][threadIdx.x] = tot;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + st];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    q.red[(m * kConvBlocks + blockIdx.x) * 2] = sm[0][0];
+    q.red[(m * kConvBlocks + blockIdx.x) * 2 + 1] = sm[1][0];
+  }
+}
+
+__device__ __forceinline__ bool conv_meets(const ConvParams& q, int m) {
+  double inc = 0.0, tot = 0.0;
+  for (int b = 0; b < kConvBlocks; ++b) {   // fixed order
+    inc += q.red[(m * kConvBlocks + b) * 2];
+    tot += q.red[(m * kConvBlocks + b) * 2 + 1];
+  }
+  return inc <= q.tol2 * tot;
+}
+
+template <typename T>
+__global__ void k_conv_write(ConvParams q) {
+  using V = cx<T>;
+  __shared__ int go;
+  const int m = blockIdx.y;
+  if (threadIdx.x == 0) go = q.conv[m] && conv_meets(q, m);
+  __syncthreads();
+  if (!go) return;
+  const long long ne = (long long)q.W * q.ny;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * blockDim.x) {
+    V s = mk<V>(T(0), T(0));
+    for (int l = 0; l < q.nlev; ++l) s = cadd(s, reinterpret_cast<const V*>(q.V[l])[m * q.stride + e]);
+    reinterpret_cast<V*>(q.vsum)[m * q.stride + e] = s;
+  }
+}
+
+__global__ void k_conv_update(ConvParams q) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= q.n || !q.conv[m]) return;
+  if (conv_meets(q, m)) {
+    q.conv[m] = 0;
+    q.orders[m] = q.level;
+  } else if (q.last) {
+    q.notconv[m] = 1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Execution
 // ---------------------------------------------------------------------------
 int launch_pass(sbi_ctx* c, const Pass& p, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
+  if (p.kind == PK_CONV) {
+    const ConvParams& q = p.conv;
+    const dim3 grid(kConvBlocks, q.n);
+    switch (q.phase) {
+      case 0: k_conv_reset<<<(q.n + 255) / 256, 256, 0, st>>>(q, c->opt.order); break;
+      case 1:
+        if (c->fp64) k_conv_norms<double><<<grid, 256, 0, st>>>(q);
+        else k_conv_norms<float><<<grid, 256, 0, st>>>(q);
+        break;
+      case 2:
+        if (c->fp64) k_conv_write<double><<<grid, 256, 0, st>>>(q);
+        else k_conv_write<float><<<grid, 256, 0, st>>>(q);
+        break;
+      default: k_conv_update<<<(q.n + 255) / 256, 256, 0, st>>>(q); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return SBI_OK;
+  }
   if (p.kind == PK_ROW) e = c->fp64 ? launch_row<double>(p.nsize, p.row, st) : launch_row<float>(p.nsize, p.row, st);
   else if (p.kind == PK_COL) e = c->fp64 ? launch_col<double>(p.nsize, p.col, st) : launch_col<float>(p.nsize, p.col, st);
   else e = c->fp64 ? launch_rk<double>(p.nsize, p.rk, st) : launch_rk<float>(p.nsize, p.rk, st);
@@ -650,7 +831,9 @@ std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
   return all;
 }
 
-int family_of(const Pass& p) { return p.kind == PK_COL ? FAM_COL : (p.kind == PK_ROW ? FAM_ROW : FAM_RK); }
+int family_of(const Pass& p) {
+  return p.kind == PK_COL ? FAM_COL : (p.kind == PK_ROW ? FAM_ROW : (p.kind == PK_RK ? FAM_RK : FAM_CONV));
+}
 
 void free_graphs(sbi_ctx* c) {
   for (auto& ge : c->graphs) {
@@ -813,6 +996,14 @@ int init_group(sbi_ctx* c, Group& g) {
   g.wout = dalloc(c, np * c->real_size);
   g.out64 = (double*)dalloc(c, g.phys_elems() * 8);
   g.d_active = (int*)dalloc(c, (size_t)g.n * sizeof(int));
+  if (c->opt.adapt_tol > 0.0) {
+    g.d_conv = (int*)dalloc(c, (size_t)g.n * sizeof(int));
+    g.d_orders = (int*)dalloc(c, (size_t)g.n * sizeof(int));
+    g.d_notconv = (int*)dalloc(c, (size_t)g.n * sizeof(int));
+    g.d_red = (double*)dalloc(c, (size_t)g.n * kConvBlocks * 2 * sizeof(double));
+    if (!g.d_conv || !g.d_orders || !g.d_notconv || !g.d_red)
+      return fail(c, SBI_ENOMEM, "device allocation failed");
+  }
   if (!g.eta0 || !g.phi0 || !g.acc_eta || !g.acc_phi || !g.eta_w || !g.Vphys || !g.wout ||
       !g.out64 || !g.d_active)
     return fail(c, SBI_ENOMEM, "device allocation failed");
@@ -1146,7 +1337,14 @@ int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, 
   CK(cudaGetLastError(), "convert");
   if (!on_device)
     CK(cudaMemcpyAsync(V_out, g.out64, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy V");
+  int notconv = 0;
+  if (g.d_notconv)
+    CK(cudaMemcpyAsync(&notconv, g.d_notconv + c->where[member].second, sizeof(int),
+                       cudaMemcpyDeviceToHost, c->stream), "flag");
   CK(cudaStreamSynchronize(c->stream), "vertical_velocity");
+  if (notconv)
+    return fail(c, SBI_ENOTCONVERGED, "adaptive order reached %d without meeting adapt_tol "
+                "(V is the order-%d sum)", c->opt.order, c->opt.order);
   return SBI_OK;
 }
 
@@ -1218,7 +1416,14 @@ int sbi_orders_used(sbi_ctx* c, int member, int* orders) {
   int rc = check_member(c, member);
   if (rc) return rc;
   if (!orders) return fail(c, SBI_EINVAL, "orders is NULL");
-  *orders = c->orders_used[member];
+  Group& g = c->groups[c->where[member].first];
+  if (g.d_orders) {
+    CK(cudaMemcpyAsync(orders, g.d_orders + c->where[member].second, sizeof(int),
+                       cudaMemcpyDeviceToHost, c->stream), "orders");
+    CK(cudaStreamSynchronize(c->stream), "orders");
+  } else {
+    *orders = c->opt.order;
+  }
   return SBI_OK;
 }
 

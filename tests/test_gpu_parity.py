@@ -7,6 +7,8 @@ Inputs are seeded band-limited fields shaped like the workloads (red spectra,
 amplitudes k|eta| up to ~0.3), projected by the oracle so both sides start
 from the same band-limited state.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -187,3 +189,52 @@ def test_every_kernel_size_fp32_matches_fp64(sbi, nx, ny):
         ctx.close()
     assert np.all(np.isfinite(out[1]))
     assert rel(out[0], out[1]) < TOL[0]
+
+
+def _ratios(eta, phi, delta, h0, grid):
+    """||F{V_l}|| / ||F{V_1 + .. + V_l}|| per order l >= 2 (oracle)."""
+    _, terms = O.vertical_velocity(eta, phi, delta, h0, grid, return_terms=True)
+    out, tot = [], np.zeros_like(np.fft.fft2(terms["V"][0]))
+    for l, Vl in enumerate(terms["V"], start=1):
+        Vh = np.fft.fft2(Vl)
+        tot = tot + Vh
+        if l >= 2:
+            out.append(np.sqrt(np.sum(np.abs(Vh) ** 2) / np.sum(np.abs(tot) ** 2)))
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_adaptive_order_matches_oracle(sbi, prec):
+    # Reading R9: stop at the first l with ||F{V_l}|| <= tol ||sum F{V_m}||.  The
+    # tolerance sits midway (geometrically) between two consecutive ratios so
+    # that round-off cannot flip the decision.
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, True, seed=90, amp_eta=0.06)
+    r = _ratios(eta, phi, pb.delta, h0, grid)
+    L = 4                                   # stop at order 4
+    tol = math.sqrt(r[L - 2] * r[L - 3])    # r[i] belongs to order i + 2
+    assert r[L - 2] < tol < r[L - 3]
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec,
+                      adapt_tol=tol)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    assert ctx.orders_used(0) == L
+    Vo = O.vertical_velocity(eta, phi, pb.delta, h0, grid, tol=tol)
+    assert rel(V, Vo) < TOL[prec]
+    # the RK4 step uses the adaptive order in every stage
+    pb.adapt_tol = tol
+    ctx.step(0.02, 1)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.02, 1)
+    assert rel(e, eo) < TOL[prec] and rel(p, po) < TOL[prec]
+
+
+def test_adaptive_order_not_met_is_reported(sbi):
+    nx, ny, Lx, Ly, h0 = 32, 16, 4.0, 3.0, 0.6
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, False, seed=95, amp_eta=0.08)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, None, h0=h0, precision=1, adapt_tol=1e-30)
+    ctx.set_state(0, eta, phi)
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.vertical_velocity(0)
+    assert ei.value.code == sbi.SBI_ENOTCONVERGED
+    assert ctx.orders_used(0) == 7
