@@ -162,17 +162,29 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(family):
-    """Per-launch DRAM bytes of a kernel family from the committed ncu summary,
-    valid only while the kernel sources are unchanged."""
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_crossing_batch.txt")
+
+
+def ncu_traffic(family, workload):
+    """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a
+    kernel family, scaled to a launch of the full workload, from the committed
+    ncu summary; None unless the summary was taken on this workload with the
+    current CUDA sources."""
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    except Exception:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
         return None
-    if d.get("source_sha") != source_sha():
+    kv = {}
+    for ln in lines:
+        ln = ln.split("#", 1)[0].split()
+        if len(ln) == 2:
+            kv[ln[0]] = ln[1]
+    if kv.get("source_sha") != source_sha() or kv.get("workload") != workload:
         return None
-    ent = d.get("families", {}).get(family)
-    return ent
+    try:
+        return float(kv[family])
+    except (KeyError, ValueError):
+        return None
 
 
 def make_context(sbi, wl, precision, stream, **extra):
@@ -315,9 +327,9 @@ def main():
     achieved = bytes_per_launch / avg_s / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    tr = ncu_traffic(name.split()[0])
+    tr = ncu_traffic(name.split()[0], args.workload) if args.members is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": (tr or {}).get("bytes_per_launch"),
+                "frac": achieved / peak, "traffic": tr,
                 "kernel": name, "launches_per_step": launches_per_step,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_s * 1e3,

@@ -144,7 +144,9 @@ int sbi_orders_used(sbi_ctx* ctx, int member, int* orders);
 
 /* Per-kernel-family timing of the step (for measurement).  sbi_profile_enable
  * turns on CUDA-event pairs around every pass of the captured step (the graph
- * is re-captured).  sbi_profile_read returns, for family i < *count (at most
+ * is re-captured).  While it is on, the member groups of a batch run one after
+ * the other instead of concurrently, so that each pair times one launch that
+ * has the GPU to itself.  sbi_profile_read returns, for family i < *count (at most
  * cap entries), its name, the number of timed launches and their total device
  * milliseconds since the last enable, and synchronizes the stream. */
 int sbi_profile_enable(sbi_ctx* ctx, int on);

@@ -884,7 +884,9 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
   ge.prof = c->prof;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = SBI_OK;
-  const bool branch = gps.size() > 1;
+  // the groups run as concurrent branches; a profiled replay runs them one
+  // after the other, so that each launch's event pair times that launch alone
+  const bool branch = gps.size() > 1 && !c->prof;
   if (branch) cudaEventRecord(c->gevents[0], c->cap);
   size_t evi = 0;
   for (size_t gi = 0; gi < gps.size() && rc == SBI_OK; ++gi) {

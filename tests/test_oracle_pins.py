@@ -300,3 +300,51 @@ def test_translating_stokes_wave():
         h3.append(F[3])
     assert res[0] / res[1] > 6.5, res
     assert h1[0] / h1[1] > 20.0 and h3[0] / h3[1] > 20.0, (h1, h3)
+
+
+def test_adaptive_order_stops_at_first_small_taylor_increment():
+    # R9 (Sec. 2.4: the series is truncated once further orders stop changing
+    # V).  With constant eta = a over a flat bottom, a single mode of phi~ has
+    # order-l increments equal to the degree-(l-1) Taylor coefficients of
+    # k tanh(k(h+a)) (sympy), so the order at which the test first holds and
+    # the truncated sum are known independently of the oracle's recursion.
+    vfun, _ = _taylor_tables()
+    g = O.Grid(32, 1, 2 * np.pi)
+    a, h0, mode = 0.06, 0.8, 3
+    kk = 2 * np.pi * mode / g.Lx
+    c = [vfun[d](a, 0.0, kk, h0) for d in range(7)]          # increments V_1..V_7
+    part = np.cumsum(c)
+    ratio = [abs(c[l]) / abs(part[l]) for l in range(7)]
+    for L in (3, 4, 5):
+        tol = math.sqrt(ratio[L - 1] * ratio[L - 2])          # between orders L-1 and L
+        assert all(ratio[l] > tol for l in range(1, L - 1)) and ratio[L - 1] <= tol
+        x = np.arange(g.nx) * g.Lx / g.nx
+        carrier = np.cos(kk * x)[None, :]
+        V, terms = O.vertical_velocity(np.full((1, g.nx), a), carrier, None, h0, g, alpha=1.0,
+                                       tol=tol, return_terms=True)
+        assert terms["used"] == L
+        amp = np.sum(V * carrier) / np.sum(carrier * carrier)
+        assert abs(amp - part[L - 1]) < 1e-12 * kk
+    # tol = 0 keeps every order
+    _, terms = O.vertical_velocity(np.full((1, g.nx), a), np.cos(kk * np.arange(g.nx) * g.Lx / g.nx)[None, :],
+                                   None, h0, g, alpha=1.0, return_terms=True)
+    assert terms["used"] == 7
+
+
+def test_low_pass_filter_special_values():
+    # R8 (Eq. filter): Lambda = exp(-|k/(beta1 k_ref)|^beta2) is 1/e at the
+    # cut-off k = beta1 k_ref for every beta2, about 1 well below it and about 0
+    # well above it for a steep beta2 (the paper's 30).
+    g = O.Grid(128, 1, 2 * np.pi)
+    x = np.arange(g.nx) * g.Lx / g.nx
+    k_ref, b1, b2 = 2.0, 8.0, 30.0                  # cut-off at wavenumber 16
+    pb = O.Problem(g, 9.81, 1.0, alpha=1.0, filt_beta1=b1, filt_beta2=b2, k_ref=k_ref)
+    modes = {4: 1.0, 8: 1.0, 16: math.exp(-1.0), 24: 0.0, 40: 0.0}
+    f = sum(np.cos(m * x) for m in modes)[None, :]
+    out = O.project(pb, f)
+    for m, lam in modes.items():
+        amp = 2.0 * np.mean(out[0] * np.cos(m * x))
+        assert abs(amp - lam) < 1e-8, (m, amp, lam)
+    pb2 = O.Problem(g, 9.81, 1.0, alpha=1.0, filt_beta1=b1, filt_beta2=4.0, k_ref=k_ref)
+    out2 = O.project(pb2, np.cos(16 * x)[None, :])
+    assert abs(2.0 * np.mean(out2[0] * np.cos(16 * x)) - math.exp(-1.0)) < 1e-12
