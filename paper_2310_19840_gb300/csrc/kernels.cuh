@@ -32,13 +32,17 @@ struct RowCfg {
   static constexpr int FBUF = padded_len(n);
 };
 
-// shared memory of a row block: per row the FFT scratch (which also stages
-// the incoming mixed row) and the physical slots
+// Row stride of the staging buffer: odd, so that the rows of a block fall on
+// different shared-memory banks when the copies land.
+__host__ __device__ constexpr int stage_stride(int W) { return W | 1; }
+
+// shared memory of a row block: per row the FFT scratch, the physical slots
+// and the staging row that receives the incoming mixed row
 template <typename T, int NX>
 __host__ __device__ constexpr size_t row_smem(int rpc, int W, int nslots) {
   using C = RowCfg<NX>;
-  (void)W;
-  return sizeof(cx<T>) * (size_t)rpc * ((size_t)C::FBUF + (size_t)nslots * C::n);
+  return sizeof(cx<T>) * (size_t)rpc *
+         ((size_t)C::FBUF + (size_t)nslots * C::n + (size_t)stage_stride(W));
 }
 
 template <int NX>
@@ -106,6 +110,46 @@ __device__ __forceinline__ void stage_mixed(cx<T>* stg_all, int fbuf, const BufR
   }
 }
 
+// Asynchronous copies global -> shared (cp.async, 8 or 16 bytes each): the
+// copies of a whole staging pass are in flight together and land while the
+// block computes; cp_async_wait_all + a block barrier make them visible.
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst_smem, const V* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(V) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Block-cooperative asynchronous load of one mixed buffer's rows into the
+// staging rows stg[rl * sw + k], k < W; rows that are absent or inactive are
+// zero-filled with plain stores.
+template <typename T>
+__device__ __forceinline__ void stage_async(cx<T>* stg_all, int sw, const BufRef& b, const RowIO& io) {
+  using V = cx<T>;
+  V* stg = stg_all + io.rl * sw;
+  const V* src = reinterpret_cast<const V*>(b.ptr);
+  for (int k = io.k0; k < io.W; k += io.kstep) {
+    if (io.ok) cp_async_elem(stg + k, src + io.at(b, k));
+    else stg[k] = mk<V>(T(0), T(0));
+  }
+  cp_async_commit();
+}
+
+// index of the first C2R op at or after o if it reads a single buffer (such
+// inputs are staged asynchronously, ahead of time), else -1.  A C2R that sums
+// several buffers is staged synchronously, so nothing may be in flight into
+// the staging rows before it.
+__device__ __forceinline__ int next_async_c2r(const RowParams& p, int o) {
+  for (; o < p.nops; ++o)
+    if (p.ops[o].kind == ROP_C2R) return p.ops[o].b == 1 ? o : -1;
+  return -1;
+}
+
 // Packed inverse real FFT, input side, from the staged row: Z[k] = E + i O,
 // E = X[k] + X*[n-k], O = (X[k] - X*[n-k]) e^{+2 pi i k / NX}, k = j + r TPR;
 // X[k] = 0 for k >= W, and the Nyquist mode X[n] = 0.  The unnormalised
@@ -166,8 +210,10 @@ k_row(const __grid_constant__ RowParams p) {
   constexpr int n = C::n, R = C::R, TPR = C::TPR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rpc = p.rpc;
-  V* fb_all = reinterpret_cast<V*>(smem_raw);      // FFT scratch, also staging
+  const int sw = stage_stride(p.W);
+  V* fb_all = reinterpret_cast<V*>(smem_raw);      // FFT scratch
   V* slot_base = fb_all + rpc * C::FBUF;           // physical slots
+  V* stg_all = slot_base + p.nslots * rpc * n;     // staging rows
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
   V* fb = fb_all + rloc * C::FBUF;
   const int row0 = (int)blockIdx.x * rpc;
@@ -182,15 +228,27 @@ k_row(const __grid_constant__ RowParams p) {
   // eta is read through the L1 cache by every product of the row
   const V* eta = (act && p.eta.ptr) ? phys_row<T>(p.eta, member, y, NX) : nullptr;
 
+  // the first single-buffer input is in flight from the start
+  int pending = next_async_c2r(p, 0);
+  if (pending >= 0) stage_async<T>(stg_all, sw, p.buf[p.ops[pending].a], io);
+
   for (int o = 0; o < p.nops; ++o) {
     const RowOp op = p.ops[o];
     V x[R];
     if (op.kind == ROP_C2R) {
-      __syncthreads();  // scratch free (previous cooperative store done)
-      stage_mixed<T>(fb_all, C::FBUF, p.buf + op.a, op.b, io);
-      __syncthreads();
-      c2r_input<T, NX>(x, fb, p.W, j, tw);
-      row_group_sync<NX>();  // the staged row is read before the FFT overwrites it
+      if (o == pending) {
+        cp_async_wait_all();
+        __syncthreads();  // every copy landed; scratch free (previous store done)
+      } else {
+        __syncthreads();  // staging and scratch free
+        stage_mixed<T>(stg_all, sw, p.buf + op.a, op.b, io);
+        __syncthreads();
+      }
+      c2r_input<T, NX>(x, stg_all + rloc * sw, p.W, j, tw);
+      __syncthreads();  // every row has read its staging row
+      // the next single-buffer input lands while this one is transformed
+      pending = next_async_c2r(p, o + 1);
+      if (pending >= 0) stage_async<T>(stg_all, sw, p.buf[p.ops[pending].a], io);
       fft_block<n, R, -1>(x, fb, j, tw);
       V* slot = slot_base + (op.slot * rpc + rloc) * n;
       V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
@@ -786,7 +844,7 @@ cudaError_t launch_col_impl(int ny, const ColParams& p, cudaStream_t st) {
 // memory stays within 200 KB; 0 if even one row does not fit.
 template <typename T>
 int row_rpc_impl(int nx, int W, int nslots) {
-  const size_t budget = 200 * 1024;
+  const size_t budget = 227 * 1024;
   int maxr = 0;
   size_t per = 0;
   switch (nx) {
