@@ -21,15 +21,23 @@ namespace sbi {
 // ===========================================================================
 // Row passes
 // ===========================================================================
+// Row-pass geometry.  Up to n = 256 a row is transformed by one warp or less
+// with 8 elements per thread (radix-8 Stockham passes, warp-synchronous), and
+// a block holds up to 512 threads; in FP32 such blocks are compiled for two
+// resident blocks per SM (64 registers per thread), which doubles the warps
+// per SM over 16 elements per thread.  Longer rows use 16 elements per thread
+// and block-wide barriers.
 template <int NX>
 struct RowCfg {
-  static constexpr int n = NX / 2;                       // packed complex length
-  static constexpr int R = (n >= 128) ? 16 : cmin(8, n); // elements per thread
-  static constexpr int TPR = n / R;                      // threads per row
+  static constexpr int n = NX / 2;                         // packed complex length
+  static constexpr int R = (n >= 512) ? 16 : cmin(8, n);   // elements per thread
+  static constexpr int TPR = n / R;                        // threads per row
   static constexpr bool WARP = TPR <= 32;
-  static constexpr int RPC_MAX = cmin(256, WARP ? cmax(16, 256 / TPR) : cmax(1, 512 / TPR));
+  static constexpr int RPC_MAX = cmin(256, WARP ? cmax(16, 512 / TPR) : cmax(1, 512 / TPR));
   static constexpr int MAX_THREADS = TPR * RPC_MAX;
   static constexpr int FBUF = padded_len(n);
+  template <typename T>
+  static constexpr int min_blocks() { return (WARP && R <= 8 && sizeof(T) == 4) ? 2 : 1; }
 };
 
 // Row stride of the staging buffer: odd, so that the rows of a block fall on
@@ -203,7 +211,7 @@ __device__ __forceinline__ T ipow(T v, int p) {
 }
 
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::MAX_THREADS)
+__global__ void __launch_bounds__(RowCfg<NX>::MAX_THREADS, RowCfg<NX>::template min_blocks<T>())
 k_row(const __grid_constant__ RowParams p) {
   using V = cx<T>;
   using C = RowCfg<NX>;
@@ -245,23 +253,11 @@ k_row(const __grid_constant__ RowParams p) {
         __syncthreads();
       }
       c2r_input<T, NX>(x, stg_all + rloc * sw, p.W, j, tw);
-      __syncthreads();  // every row has read its staging row
+      __syncthreads();  // every row has read its staging row; scratch free
       // the next single-buffer input lands while this one is transformed
       pending = next_async_c2r(p, o + 1);
       if (pending >= 0) stage_async<T>(stg_all, sw, p.buf[p.ops[pending].a], io);
-      fft_block<n, R, -1>(x, fb, j, tw);
-      V* slot = slot_base + (op.slot * rpc + rloc) * n;
-      V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int m = j + r * TPR;
-        const V z = cconj(fb[pad(m)]);
-        slot[m] = z;
-        if (out) out[m] = z;
-      }
-      continue;
-    }
-    if (op.kind == ROP_PROD) {
+    } else if (op.kind == ROP_PROD) {
       V* slot = op.slot == kNone ? nullptr : slot_base + (op.slot * rpc + rloc) * n;
       const T cf = T(op.coef);
       const bool running = (op.c & 2) != 0;
@@ -327,8 +323,23 @@ k_row(const __grid_constant__ RowParams p) {
       }
       if (op.kind == ROP_WDOT) continue;
     }
-    __syncthreads();  // scratch free (previous cooperative store done)
+    // one transform call site for every op keeps the kernel's code small
+    const bool c2r = op.kind == ROP_C2R;
+    if (!c2r) __syncthreads();  // scratch free (previous cooperative store done)
     fft_block<n, R, -1>(x, fb, j, tw);
+    if (c2r) {
+      // inverse transform: the row in physical space, packed as complex pairs
+      V* slot = slot_base + (op.slot * rpc + rloc) * n;
+      V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int m = j + r * TPR;
+        const V z = cconj(fb[pad(m)]);
+        slot[m] = z;
+        if (out) out[m] = z;
+      }
+      continue;
+    }
     __syncthreads();  // every row's spectrum ready
     r2c_store<T, NX>(fb_all, p.buf[op.dst], io, tw);
   }
@@ -844,11 +855,18 @@ cudaError_t launch_col_impl(int ny, const ColParams& p, cudaStream_t st) {
 // memory stays within 200 KB; 0 if even one row does not fit.
 template <typename T>
 int row_rpc_impl(int nx, int W, int nslots) {
-  const size_t budget = 227 * 1024;
+  // one block may take the whole 227 KB; blocks compiled for two per SM get
+  // half of the SM's 228 KB less the 1 KB each block reserves
+  size_t budget = 227 * 1024;
   int maxr = 0;
   size_t per = 0;
   switch (nx) {
-#define SBI_CASE(N) case N: maxr = RowCfg<N>::RPC_MAX; per = row_smem<T, N>(1, W, nslots); break;
+#define SBI_CASE(N)                                                         \
+  case N:                                                                   \
+    maxr = RowCfg<N>::RPC_MAX;                                              \
+    per = row_smem<T, N>(1, W, nslots);                                     \
+    if (RowCfg<N>::template min_blocks<T>() == 2) budget = 113 * 1024;      \
+    break;
     SBI_FOR_NX(SBI_CASE)
 #undef SBI_CASE
     default: return 0;
