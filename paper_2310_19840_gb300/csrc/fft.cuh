@@ -11,8 +11,11 @@
 // order in shared memory.  Forward transforms use w = exp(-2 pi i / L),
 // inverse ones exp(+2 pi i / L); neither is normalised.
 //
-// Shared-memory indices are padded by one complex per 32 (pad()) to spread
-// the power-of-two strides of the scatter over the banks.  When a transform
+// Shared-memory indices are padded by one complex per 16 (pad()) to spread
+// the power-of-two strides of the scatter over the banks: for the radix-8 and
+// radix-16 passes used here this keeps every store and load of a warp at the
+// minimum of two 128-byte wavefronts for lengths of 128 and up (one per 32
+// left the radix-8 stores of lengths 128 and 256 at 3.3 and 2.7).  When a transform
 // fits in one warp (N/R <= 32 threads) its passes synchronise with __syncwarp
 // only; larger transforms use block barriers.
 #pragma once
@@ -38,8 +41,8 @@ template <int SIGN, typename V> __device__ __forceinline__ V rot(V a) {
   return SIGN > 0 ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
 }
 
-__host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 5) + 1; }
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 

@@ -264,6 +264,18 @@ k_row(const __grid_constant__ RowParams p) {
       const V* drow = (act && op.b > 0 && p.delta.ptr) ? phys_row<T>(p.delta, member, y, NX) : nullptr;
       const V* wrow = (act && (op.c & 1) && p.wgt.ptr) ? phys_row<T>(p.wgt, member, y, NX) : nullptr;
       const V* erow = op.a > 0 ? eta : nullptr;
+      if (slot && erow && op.a == 1 && !drow && !wrow && running) {
+        // the common running product slot <- eta * slot, straight-line
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int m = j + r * TPR;
+          const V e = __ldg(erow + m);
+          V v = slot[m];
+          v = mk<V>(v.x * e.x, v.y * e.y);
+          slot[m] = v;
+          x[r] = mk<V>(cf * v.x, cf * v.y);
+        }
+      } else {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
@@ -286,6 +298,7 @@ k_row(const __grid_constant__ RowParams p) {
           v = mk<V>(v.x * w.x, v.y * w.y);
         }
         x[r] = mk<V>(cf * v.x, cf * v.y);
+      }
       }
     } else {
       // ROP_N2 / ROP_WDOT: slots V, eta_x, [eta_y,] phi_x, [phi_y]
