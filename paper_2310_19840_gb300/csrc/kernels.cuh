@@ -37,7 +37,8 @@ struct RowCfg {
   static constexpr int MAX_THREADS = TPR * RPC_MAX;
   static constexpr int FBUF = padded_len(n);
   template <typename T>
-  static constexpr int min_blocks() { return (WARP && R <= 8 && sizeof(T) == 4) ? 2 : 1; }
+  // 0: no minimum, the register count is left to the compiler
+  static constexpr int min_blocks() { return (WARP && R <= 8 && sizeof(T) == 4) ? 2 : 0; }
 };
 
 // Row stride of the staging buffer: odd, so that the rows of a block fall on
@@ -578,15 +579,19 @@ k_rk(const __grid_constant__ RkParams p) {
 // Inverse transforms use F^{-1}(X) = conj(F(conj X)) so one (forward) FFT
 // instantiation serves both directions.
 // ===========================================================================
+// Column-pass geometry: 8 elements per thread up to NY = 512 (one warp per
+// column at 256, two at 512), 16 beyond.  In FP32 the radix-8 columns of at
+// least a warp are compiled for four resident blocks per SM (64 registers).
 template <typename T, int NY>
 struct ColCfg {
-  static constexpr int RC = NY == 1 ? 1 : (NY <= 256 ? cmin(8, NY) : 16);
+  static constexpr int RC = NY == 1 ? 1 : (NY <= 512 ? cmin(8, NY) : 16);
   static constexpr int TPC = NY / RC;
   static constexpr bool WARP = TPC <= 32;
   // 8-byte elements: 256 threads per block; 16-byte elements: half the columns
   static constexpr int CPB = NY == 1 ? 256 : cmax(1, 256 / TPC / (int)(sizeof(T) / 4));
   static constexpr int THREADS = TPC * CPB;
   static constexpr int SCR = NY == 1 ? 0 : padded_len(NY);
+  static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && RC == 8 && TPC >= 32) ? 4 : 0;  // 0: no minimum
 };
 
 template <typename T, int NY>
@@ -608,7 +613,7 @@ __device__ __forceinline__ V cmul_ipow(V x, S f, int q) {   // x f i^q
 }
 
 template <typename T, int NY>
-__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS)
+__global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, ColCfg<T, NY>::MIN_BLOCKS)
 k_col(const __grid_constant__ ColParams p) {
   using V = cx<T>;
   using C = ColCfg<T, NY>;
