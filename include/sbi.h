@@ -83,6 +83,12 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* user);  /* optional device allocator (NULL: cudaMalloc) */
     void  (*dev_free)(void* ptr, void* user);      /* matching free (NULL: cudaFree) */
     void*  alloc_user;   /* passed to dev_alloc / dev_free */
+    int    autotune;     /* 1 (default): before a step graph is captured (and on the first
+                            diagnostic), time each row and column pass at a few block shapes
+                            (rows per block, columns per block) and keep the fastest.  The
+                            shapes change only how the work is split into blocks, never the
+                            arithmetic, so results are identical with any choice.  0: use
+                            the largest shape that fits (no timing runs). */
 } sbi_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -160,6 +166,16 @@ int sbi_step_bytes(const sbi_ctx* ctx, int family, double* bytes);
 
 /* Number of kernel launches in one captured step. */
 int sbi_step_launches(const sbi_ctx* ctx, int* launches);
+
+/* Choices of the autotuner (opt.autotune), one line per distinct pass shape:
+ *   "<pass shape>: rpc|cpb <chosen>/<default> <ms per launch> ms", e.g.
+ *   "row nx=512 rows=16384 slots=1 ops=21 CPPPPPPCPPPPPPCPPPPPP: rpc 8/16 0.0910 ms"
+ * (ms is -1 for a shape that was not timed: one candidate only, or a pass
+ * that is not re-run because its outputs alias its inputs).
+ * Writes at most cap bytes (NUL-terminated) into buf and the full length
+ * (without the NUL) into *needed; buf may be NULL when cap is 0.  The paper
+ * has no counterpart. */
+int sbi_autotune_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 /* Mass and energy of one state without any device allocation.  (This entry
  * point has no counterpart in the paper; it serves callers that may not

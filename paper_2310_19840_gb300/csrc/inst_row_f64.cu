@@ -10,6 +10,7 @@ template <> cudaError_t launch_rk<double>(int nx, const RkParams& p, cudaStream_
 }
 template <> cudaError_t prepare_row_kernels<double>(int nx) { return prepare_row_impl<double>(nx); }
 template <> int row_rpc<double>(int nx, int W, int nslots) { return row_rpc_impl<double>(nx, W, nslots); }
+template <> int row_tpr<double>(int nx) { return row_tpr_impl<double>(nx); }
 template <> cudaError_t state_convert<double>(const void* src, void* dst, long long n, bool to_double,
                                           cudaStream_t st) {
   return state_convert_impl<double>(src, dst, n, to_double, st);

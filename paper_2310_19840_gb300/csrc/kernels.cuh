@@ -571,11 +571,11 @@ k_rk(const __grid_constant__ RkParams p) {
 }
 
 // ===========================================================================
-// Column pass: CPB columns per block, TPC threads per column (one warp or less
-// per column up to NY = 512), each column a contiguous run of NY complex.
-// Per column the block keeps in shared memory the FFT scratch, the
-// (tanh, sech) factors of its modes and the accumulators, so the multiplier
-// loops run from shared memory and the registers hold only the FFT data.
+// Column pass: cpb columns per block (the size's CPB unless the launch asks
+// for fewer), TPC threads per column, each column a contiguous run of NY
+// complex.  Per column the block keeps the FFT scratch and the accumulators
+// in shared memory; the per-mode multipliers come from tables in global
+// memory (one real per stored mode and term).
 // Inverse transforms use F^{-1}(X) = conj(F(conj X)) so one (forward) FFT
 // instantiation serves both directions.
 // ===========================================================================
@@ -595,9 +595,22 @@ struct ColCfg {
 };
 
 template <typename T, int NY>
-__host__ __device__ constexpr size_t col_smem(int nacc) {
+__host__ __device__ constexpr size_t col_smem(int nacc, int cpb) {
   using C = ColCfg<T, NY>;
-  return sizeof(cx<T>) * (size_t)C::CPB * ((size_t)C::SCR + (size_t)NY * nacc);
+  return sizeof(cx<T>) * (size_t)cpb * ((size_t)C::SCR + (size_t)NY * nacc);
+}
+
+// columns per block of a launch: the size's default CPB, or a smaller count
+// that still makes whole warps (the column FFTs synchronise whole warps)
+template <typename T, int NY>
+__host__ __device__ constexpr int col_cpb(int requested) {
+  using C = ColCfg<T, NY>;
+  return requested > 0 ? requested : C::CPB;
+}
+template <typename T, int NY>
+__host__ __device__ constexpr bool col_cpb_ok(int cpb) {
+  using C = ColCfg<T, NY>;
+  return cpb >= 1 && cpb <= C::CPB && (cpb * C::TPC) % 32 == 0;
 }
 
 template <typename V, typename S>
@@ -617,14 +630,15 @@ __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, ColCfg<T, NY>::MIN_BLO
 k_col(const __grid_constant__ ColParams p) {
   using V = cx<T>;
   using C = ColCfg<T, NY>;
-  constexpr int RC = C::RC, TPC = C::TPC, CPB = C::CPB, SCR = C::SCR;
+  constexpr int RC = C::RC, TPC = C::TPC, SCR = C::SCR;
+  const int cpb = col_cpb<T, NY>(p.cpb);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x / TPC, j = threadIdx.x % TPC;
   V* base = reinterpret_cast<V*>(smem_raw);
   V* sc = base + c * SCR;                                   // FFT scratch
-  V* acc0 = base + CPB * SCR + c * NY * p.nacc;             // accumulators
+  V* acc0 = base + cpb * SCR + c * NY * p.nacc;             // accumulators
   V* acc1 = acc0 + (p.nacc > 1 ? NY : 0);
-  const int gc = blockIdx.x * CPB + c;
+  const int gc = blockIdx.x * cpb + c;
   const bool valid = gc < p.cols_total;
   const int member = valid ? gc / p.W : 0;
   const int kx = valid ? gc % p.W : 0;
@@ -786,7 +800,7 @@ cudaError_t prepare_nx() {
 template <typename T, int NY>
 cudaError_t prepare_ny() {
   return cudaFuncSetAttribute(k_col<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem<T, NY>(kMaxColAcc));
+                              (int)col_smem<T, NY>(kMaxColAcc, ColCfg<T, NY>::CPB));
 }
 
 template <typename T, int NX>
@@ -811,8 +825,10 @@ template <typename T, int NY>
 cudaError_t launch_col_n(const ColParams& p, cudaStream_t st) {
   using C = ColCfg<T, NY>;
   if (p.nacc < 1 || p.nacc > kMaxColAcc) return cudaErrorInvalidValue;
-  const int blocks = (p.cols_total + C::CPB - 1) / C::CPB;
-  k_col<T, NY><<<blocks, C::THREADS, col_smem<T, NY>(p.nacc), st>>>(p);
+  const int cpb = col_cpb<T, NY>(p.cpb);
+  if (!col_cpb_ok<T, NY>(cpb)) return cudaErrorInvalidValue;
+  const int blocks = (p.cols_total + cpb - 1) / cpb;
+  k_col<T, NY><<<blocks, C::TPC * cpb, col_smem<T, NY>(p.nacc, cpb), st>>>(p);
   return cudaGetLastError();
 }
 
@@ -901,6 +917,26 @@ int row_rpc_impl(int nx, int W, int nslots) {
   // a block must cover whole warps (the row FFTs synchronise whole warps)
   if (per * (size_t)r > budget || (r * tpr) % 32 != 0) return 0;
   return r;
+}
+
+template <typename T>
+int row_tpr_impl(int nx) {
+  switch (nx) {
+#define SBI_CASE(N) case N: return RowCfg<N>::TPR;
+    SBI_FOR_NX(SBI_CASE)
+#undef SBI_CASE
+    default: return 0;
+  }
+}
+
+template <typename T>
+int col_geometry_impl(int ny, int* tpc) {
+  switch (ny) {
+#define SBI_CASE(N) case N: *tpc = ColCfg<T, N>::TPC; return ColCfg<T, N>::CPB;
+    SBI_FOR_NY(SBI_CASE)
+#undef SBI_CASE
+    default: *tpc = 0; return 0;
+  }
 }
 
 }  // namespace sbi

@@ -132,6 +132,14 @@ struct sbi_ctx {
   std::vector<double> prof_ms;
   std::vector<long long> prof_launches;
   std::vector<int> orders_used;
+  // autotuner: block shape per pass signature (rows or columns per block)
+  struct Tuned {
+    int choice, deflt;
+    double ms;
+  };
+  std::map<std::string, Tuned> tuned;
+  std::vector<std::string> tune_order;  // signatures in the order they were tuned
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   bool filter_on() const { return opt.filt_beta1 > 0.0; }
 };
 
@@ -807,6 +815,128 @@ int run_passes(sbi_ctx* c, const std::vector<Pass>& ps, cudaStream_t st) {
   return SBI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner.  A row pass may run with any power-of-two number of rows per
+// block up to the planner's choice, a column pass with any number of columns
+// per block up to the size's default, as long as a block is made of whole
+// warps.  Neither changes the arithmetic of a row or a column, so the results
+// are the same bits for every choice; only the split into blocks (occupancy,
+// tail of the last wave) changes.  Each distinct pass shape is timed once on
+// the real buffers (one warm-up and three timed launches per candidate) and
+// the fastest is kept; the planner's default stays unless another candidate
+// is at least 3 % faster.  Passes whose outputs alias their inputs (not
+// idempotent, e.g. an in-place filter) are never re-run and keep the default.
+// ---------------------------------------------------------------------------
+bool pass_idempotent(const Pass& p) {
+  std::vector<const void*> in, out;
+  if (p.kind == PK_ROW) {
+    const RowParams& r = p.row;
+    for (int o = 0; o < r.nops; ++o) {
+      const RowOp& op = r.ops[o];
+      if (op.kind == ROP_C2R) {
+        for (int q = 0; q < op.b; ++q) in.push_back(r.buf[op.a + q].ptr);
+        if (op.dst != kNone) out.push_back(r.buf[op.dst].ptr);
+      } else {
+        out.push_back(r.buf[op.dst].ptr);
+      }
+    }
+    in.push_back(r.eta.ptr);
+    in.push_back(r.delta.ptr);
+    in.push_back(r.wgt.ptr);
+  } else if (p.kind == PK_COL) {
+    const ColParams& q = p.col;
+    for (int i = 0; i < q.nin; ++i) in.push_back(q.buf[i].ptr);
+    for (int i = 0; i < q.npass; ++i) in.push_back(q.pass[i].ptr);
+    for (int o = 0; o < q.nouts; ++o) out.push_back(q.buf[q.nin + o].ptr);
+    if (q.norm_out) return false;
+  } else {
+    return false;
+  }
+  for (const void* a : out)
+    for (const void* b : in)
+      if (a && a == b) return false;
+  return true;
+}
+
+std::string pass_signature(const Pass& p) {
+  char b[160];
+  if (p.kind == PK_ROW) {
+    std::string ops;
+    for (int o = 0; o < p.row.nops; ++o) ops += "CPNW"[p.row.ops[o].kind & 3];
+    snprintf(b, sizeof(b), "row nx=%d rows=%d slots=%d ops=%d ", p.nsize, p.row.rows_total, p.row.nslots,
+             p.row.nops);
+    return b + ops;
+  }
+  snprintf(b, sizeof(b), "col ny=%d cols=%d in=%d terms=%d out=%d acc=%d pass=%d", p.nsize,
+           p.col.cols_total, p.col.nin, p.col.nterms, p.col.nouts, p.col.nacc, p.col.npass);
+  return b;
+}
+
+int tune_pass(sbi_ctx* c, Pass& p, cudaStream_t st) {
+  if (!c->opt.autotune || (p.kind != PK_ROW && p.kind != PK_COL)) return SBI_OK;
+  auto apply = [&](Pass& q, int v) {
+    if (q.kind == PK_ROW) q.row.rpc = v;
+    else q.col.cpb = v;
+  };
+  const std::string key = pass_signature(p);
+  auto it = c->tuned.find(key);
+  if (it != c->tuned.end()) {
+    apply(p, it->second.choice);
+    return SBI_OK;
+  }
+  std::vector<int> cand;
+  int deflt = 0;
+  if (p.kind == PK_ROW) {
+    const int tpr = c->fp64 ? row_tpr<double>(p.nsize) : row_tpr<float>(p.nsize);
+    deflt = p.row.rpc;
+    for (int r = deflt; r >= 1 && cand.size() < 4; r /= 2)
+      if (tpr > 0 && (r * tpr) % 32 == 0) cand.push_back(r);
+  } else {
+    int tpc = 0;
+    const int cpb = c->fp64 ? col_geometry<double>(p.nsize, &tpc) : col_geometry<float>(p.nsize, &tpc);
+    deflt = p.col.cpb > 0 ? p.col.cpb : cpb;
+    for (int v = deflt; v >= 1 && cand.size() < 4; v /= 2)
+      if (tpc > 0 && (v * tpc) % 32 == 0) cand.push_back(v);
+  }
+  int best = deflt;
+  double best_ms = -1.0, deflt_ms = -1.0;
+  if (cand.size() > 1 && pass_idempotent(p)) {
+    if (!c->tune_ev[0]) {
+      CK(cudaEventCreate(&c->tune_ev[0]), "event");
+      CK(cudaEventCreate(&c->tune_ev[1]), "event");
+    }
+    for (int v : cand) {
+      Pass q = p;
+      apply(q, v);
+      int rc = launch_pass(c, q, st);  // warm-up
+      if (rc) return rc;
+      CK(cudaEventRecord(c->tune_ev[0], st), "event");
+      for (int k = 0; k < 3; ++k) {
+        rc = launch_pass(c, q, st);
+        if (rc) return rc;
+      }
+      CK(cudaEventRecord(c->tune_ev[1], st), "event");
+      CK(cudaEventSynchronize(c->tune_ev[1]), "tuning sync");
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]), "event time");
+      const double t = ms / 3.0;
+      if (v == deflt) deflt_ms = t;
+      if (best_ms < 0.0 || t < best_ms) {
+        best_ms = t;
+        best = v;
+      }
+    }
+    if (best != deflt && !(best_ms < 0.97 * deflt_ms)) {
+      best = deflt;
+      best_ms = deflt_ms;
+    }
+  }
+  c->tuned[key] = sbi_ctx::Tuned{best, deflt, best_ms};
+  c->tune_order.push_back(key);
+  apply(p, best);
+  return SBI_OK;
+}
+
 // Passes of one step for each member group (groups are independent).
 std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom) {
   std::vector<std::vector<Pass>> out;
@@ -854,6 +984,12 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
   CK(cudaStreamSynchronize(c->stream), "sync before capture");
+  // block shapes are tuned (or taken from earlier tuning) before capture
+  for (auto& v : gps)
+    for (auto& p : v) {
+      const int rc = tune_pass(c, p, c->cap);
+      if (rc) return rc;
+    }
   size_t npasses = 0;
   for (auto& v : gps) npasses += v.size();
   if (c->prof) {
@@ -984,7 +1120,12 @@ int run_diag(sbi_ctx* c, int gi, bool eulerian) {
   pl.plan_sum_v(ps, eulerian);
   if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
   CK(cudaStreamSynchronize(c->cap), "sync");
-  return run_passes(c, ps, c->stream);
+  for (auto& p : ps) {
+    int rc = tune_pass(c, p, c->stream);
+    if (!rc) rc = launch_pass(c, p, c->stream);
+    if (rc) return rc;
+  }
+  return SBI_OK;
 }
 
 int init_group(sbi_ctx* c, Group& g) {
@@ -1242,6 +1383,7 @@ void sbi_default_options(sbi_options* opt) {
   opt->cuda_stream = nullptr;
   opt->check_finite = 1;
   opt->set_state_dealias = 1;
+  opt->autotune = 1;
 }
 
 int sbi_create(const sbi_grid* g, double gravity, const double* h, const sbi_options* opt,
@@ -1475,6 +1617,25 @@ int sbi_step_launches(const sbi_ctx* cc, int* launches) {
   return SBI_OK;
 }
 
+int sbi_autotune_report(const sbi_ctx* cc, char* buf, size_t cap, size_t* needed) {
+  if (!cc || !needed || (cap > 0 && !buf)) return SBI_EINVAL;
+  std::string out;
+  for (const auto& key : cc->tune_order) {
+    const auto& t = cc->tuned.at(key);
+    char line[96];
+    snprintf(line, sizeof(line), ": %s %d/%d %.4f ms\n", key.rfind("row", 0) == 0 ? "rpc" : "cpb",
+             t.choice, t.deflt, t.ms);
+    out += key + line;
+  }
+  *needed = out.size();
+  if (cap > 0) {
+    const size_t n = out.size() < cap - 1 ? out.size() : cap - 1;
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return SBI_OK;
+}
+
 const char* sbi_last_error(const sbi_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 void sbi_destroy(sbi_ctx* c) {
@@ -1489,6 +1650,8 @@ void sbi_destroy(sbi_ctx* c) {
   c->allocs.clear();
   for (auto s2 : c->gstreams) cudaStreamDestroy(s2);
   for (auto e2 : c->gevents) cudaEventDestroy(e2);
+  for (auto e2 : c->tune_ev)
+    if (e2) cudaEventDestroy(e2);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }

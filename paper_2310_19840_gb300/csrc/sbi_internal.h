@@ -93,6 +93,7 @@ struct ColTerm {
 
 struct ColParams {
   int nin, nterms, nouts, nacc;
+  int cpb;                  // columns per block (0: the size's default; see col_cpb_ok)
   int W, ny, nx;
   int cols_total;           // members * W
   int member0;
@@ -155,5 +156,9 @@ template <typename T> cudaError_t state_convert(const void* src, void* dst, long
                                                 cudaStream_t st);
 // rows per block for a row pass with nslots physical slots (0: does not fit)
 template <typename T> int row_rpc(int nx, int W, int nslots);
+// launch geometry of a size: threads per row of a row pass; default columns
+// per block and threads per column of a column pass (0 for an unknown size)
+template <typename T> int row_tpr(int nx);
+template <typename T> int col_geometry(int ny, int* tpc);
 
 }  // namespace sbi

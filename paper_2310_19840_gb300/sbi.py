@@ -40,7 +40,8 @@ class sbi_options(C.Structure):
                 ("sponge_w", C.POINTER(C.c_double)), ("sponge_nu", C.c_double),
                 ("cuda_stream", C.c_void_p), ("check_finite", C.c_int),
                 ("set_state_dealias", C.c_int),
-                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("autotune", C.c_int)]
 
 
 EXPORTS = {
@@ -63,6 +64,7 @@ EXPORTS = {
                                    C.POINTER(C.c_int)]),
     "sbi_step_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sbi_step_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sbi_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
@@ -145,7 +147,8 @@ class Context:
 
     def __init__(self, grids, gravity, depths=None, *, h0=math.nan, order=7, alias_frac=0.5,
                  precision=SBI_FP32, adapt_tol=0.0, filt_beta1=0.0, filt_beta2=0.0, k_ref=1.0,
-                 sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1):
+                 sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1,
+                 autotune=1):
         self.lib = load()
         if isinstance(grids, tuple):
             grids = [grids]
@@ -154,7 +157,7 @@ class Context:
         opt = default_options(order=order, alias_frac=alias_frac, h0=h0, precision=precision,
                               adapt_tol=adapt_tol, filt_beta1=filt_beta1, filt_beta2=filt_beta2,
                               k_ref=k_ref, sponge_nu=sponge_nu, check_finite=check_finite,
-                              set_state_dealias=set_state_dealias)
+                              set_state_dealias=set_state_dealias, autotune=autotune)
         keep = []
         if sponge_w is not None:
             w = np.ascontiguousarray(sponge_w, dtype=np.float64).ravel()
@@ -254,6 +257,13 @@ class Context:
         b = C.c_double()
         self._check(self.lib.sbi_step_bytes(self.ctx, family, C.byref(b)))
         return b.value
+
+    def autotune_report(self):
+        need = C.c_size_t()
+        self._check(self.lib.sbi_autotune_report(self.ctx, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value + 1)
+        self._check(self.lib.sbi_autotune_report(self.ctx, buf, len(buf), C.byref(need)))
+        return buf.value.decode()
 
     def step_launches(self):
         n = C.c_int()

@@ -135,6 +135,35 @@ def test_filter_matches_oracle(sbi):
         assert rel(e, eo) < TOL[prec] and rel(p, po) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_block_shapes_give_identical_results(sbi, prec):
+    # The autotuner only changes rows / columns per block: a context with it
+    # and one without produce the same bits after diagnostics and steps, and
+    # it reports one choice per distinct pass shape.
+    specs = [(256, 128, 12.0, 8.0), (512, 64, 20.0, 4.0)]
+    depth = [0.6 - W.random_field(256, 128, 71, amplitude=0.05), None]
+    out = {}
+    for tune in (0, 1):
+        ctx = sbi.Context(specs, 9.81, depth, h0=0.6, precision=prec, autotune=tune,
+                          filt_beta1=8.0, filt_beta2=30.0, k_ref=1.0)
+        for i, (nx, ny, Lx, Ly) in enumerate(specs):
+            ctx.set_state(i, W.random_field(nx, ny, 72 + i, amplitude=0.03),
+                          W.random_field(nx, ny, 74 + i, amplitude=0.2))
+        V = ctx.vertical_velocity(0)
+        ctx.step(0.01, 3)
+        out[tune] = (V, ctx.get_state(0), ctx.get_state(1))
+        if tune:
+            rep = ctx.autotune_report().strip().splitlines()
+            assert any(": rpc " in ln for ln in rep) and any(": cpb " in ln for ln in rep)
+            assert len(set(ln.split(":")[0] for ln in rep)) == len(rep)
+        else:
+            assert ctx.autotune_report() == ""
+    assert np.array_equal(out[0][0], out[1][0])
+    for m in (1, 2):
+        for f in (0, 1):
+            assert np.array_equal(out[0][m][f], out[1][m][f])
+
+
 def test_batch_of_uneven_grids_equals_single(sbi):
     specs = [(64, 32, 6.0, 4.0), (32, 16, 3.0, 2.0), (64, 32, 6.0, 4.0), (128, 1, 9.0, 1.0)]
     states = []

@@ -49,6 +49,36 @@ def test_default_options(lib):
     o = sbi.default_options()
     assert o.order == 7 and o.alias_frac == 0.5 and math.isnan(o.h0)
     assert o.precision == sbi.SBI_FP32 and o.check_finite == 1 and o.set_state_dealias == 1
+    assert o.autotune == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # The ctypes mirrors of sbi_grid and sbi_options must have the C layout:
+    # a C program compiled against include/sbi.h prints sizeof and offsetof.
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2310_19840_gb300 import sbi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sbi_grid": sbi.sbi_grid, "sbi_options": sbi.sbi_options}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sbi.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                    check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
 
 
 @pytest.mark.parametrize("grid,kw,msg", [
