@@ -187,6 +187,23 @@ def ncu_traffic(family, workload):
         return None
 
 
+def autotune_summary(report):
+    """Block shapes the autotuner chose, counted per pass kind, e.g.
+    {"row": {"rpc 16": 5, "rpc 8": 2}, "col": {"cpb 8": 9}, "non_default": 2}."""
+    out, changed = {}, 0
+    for ln in report.splitlines():
+        if ": " not in ln:
+            continue
+        shape, choice = ln.rsplit(": ", 1)
+        knob, vals = choice.split()[:2]
+        chosen, deflt = vals.split("/")
+        kind = out.setdefault(shape.split()[0], {})
+        kind[f"{knob} {chosen}"] = kind.get(f"{knob} {chosen}", 0) + 1
+        changed += chosen != deflt
+    out["non_default"] = changed
+    return out
+
+
 def make_context(sbi, wl, precision, stream, **extra):
     grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in wl.members]
     depths = [(m.h0 - m.delta) if m.delta is not None else None for m in wl.members]
@@ -319,26 +336,39 @@ def main():
     fams = ctx.profile_read()
     ctx.profile_enable(False)
     fam_bytes = [ctx.step_bytes(i) for i in range(len(fams))]
+    # transform-pass model: every 1-D transform pass over a field streams it
+    # once in and once out, 2 x (bytes of a real) per point (8 B in FP32)
+    per_unit = 2 * (8 if prec == sbi.SBI_FP64 else 4)
+    fam_model = [ctx.step_transforms(i) * per_unit for i in range(len(fams))]
     dom = max(range(len(fams)), key=lambda i: fams[i][2])
     name, nlaunch, ms = fams[dom]
     launches_per_step = nlaunch / max(1, args.steps)
-    bytes_per_launch = fam_bytes[dom] / max(1e-9, launches_per_step)
+    model_per_launch = fam_model[dom] / max(1e-9, launches_per_step)
+    fused_per_launch = fam_bytes[dom] / max(1e-9, launches_per_step)
     avg_s = (ms / 1000.0) / max(1, nlaunch)
-    achieved = bytes_per_launch / avg_s / 1e9
+    achieved = model_per_launch / avg_s / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     tr = ncu_traffic(name.split()[0], args.workload) if args.members is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr,
                 "kernel": name, "launches_per_step": launches_per_step,
-                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "basis": f"transform-pass model: {per_unit} B per point per 1-D transform pass "
+                         "over a field (one read, one write)",
+                "algorithmic_bytes_per_launch": model_per_launch,
+                "fused_bytes_per_launch": fused_per_launch,
+                "fused_GBps": fused_per_launch / avg_s / 1e9,
+                "fused_frac": fused_per_launch / avg_s / 1e9 / peak,
                 "avg_launch_ms": avg_s * 1e3,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
                 "share_of_step": ms / sum(f[2] for f in fams),
                 "families": [{"kernel": f[0], "launches": f[1], "ms": f[2],
-                              "algorithmic_GBps": (fam_bytes[i] * args.steps / (f[2] / 1e3) / 1e9)
+                              "model_GBps": (fam_model[i] * args.steps / (f[2] / 1e3) / 1e9)
+                              if f[2] > 0 else None,
+                              "fused_GBps": (fam_bytes[i] * args.steps / (f[2] / 1e3) / 1e9)
                               if f[2] > 0 else None} for i, f in enumerate(fams)]}
     step_gbps = bytes_step * args.steps / secs / 1e9
+    step_model_gbps = ctx.step_transforms(-1) * per_unit * args.steps / secs / 1e9
 
     # ---- error at this configuration: FP32 path vs FP64 path, member 0 ----
     err = None
@@ -396,12 +426,13 @@ def main():
 
     cfg = workload_config(wl)
     cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
+    cfg["autotune"] = autotune_summary(ctx.autotune_report())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == sbi.SBI_FP64 else "f32", "data": "synthetic",
             "config": cfg, "clocks": clk, "gpu_launches": launches * args.steps,
-            "algorithmic_step_GBps": step_gbps, "roofline": roofline,
+            "model_step_GBps": step_model_gbps, "fused_step_GBps": step_gbps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_arm, "error": err}
     if rank == 0:
         print(json.dumps(line), flush=True)

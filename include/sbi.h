@@ -164,6 +164,15 @@ int sbi_profile_read(sbi_ctx* ctx, int cap, const char** names, long long* launc
  * writing its outputs once.  family < 0 gives the whole step. */
 int sbi_step_bytes(const sbi_ctx* ctx, int family, double* bytes);
 
+/* Transform work of one step: the number of one-dimensional transform
+ * passes over a whole field (along x or along y) times the field's points,
+ * summed over the kernels of a family (family < 0: the whole step).  A 2-D
+ * FFT of a field counts twice.  Column passes count the whole field although
+ * they transform only the kept x-modes.  This is the unit of the
+ * bandwidth model in which every transform pass streams its field once in
+ * and once out. */
+int sbi_step_transforms(const sbi_ctx* ctx, int family, double* point_transforms);
+
 /* Number of kernel launches in one captured step. */
 int sbi_step_launches(const sbi_ctx* ctx, int* launches);
 

@@ -72,7 +72,8 @@ struct Pass {
   ColParams col;
   RkParams rk;
   ConvParams conv;
-  double bytes;  // algorithmic device-memory traffic of the launch
+  double bytes;   // algorithmic device-memory traffic of the launch
+  double xforms;  // 1-D transform passes over a whole field, times the field's points
 };
 
 struct Group {
@@ -314,6 +315,9 @@ struct Planner {
     ps.nsize = g.nx;
     ps.row = r.p;
     ps.bytes = r.bytes;
+    int nx_fields = 0;  // every op but WDOT transforms one field along x
+    for (int o = 0; o < r.p.nops; ++o) nx_fields += r.p.ops[o].kind != ROP_WDOT;
+    ps.xforms = (double)nx_fields * g.phys_elems() * g.n;
     return ps;
   }
 
@@ -426,6 +430,8 @@ struct Planner {
     ps.nsize = g.ny;
     ps.col = p;
     ps.bytes = mixed_bytes() * (ins.size() + outs.size() + passthrough.size());
+    // every input and output is one field transformed along y
+    ps.xforms = g.ny > 1 ? (double)(ins.size() + outs.size()) * g.phys_elems() * g.n : 0.0;
     return ps;
   }
 
@@ -640,6 +646,10 @@ struct Planner {
     p.phi_hat = mref("phi_m");
     p.nonfinite = c->d_flags;
     p.tw = c->tw;
+    // transforms along x: the stage's phi~_t (STAGE) or the two corrections
+    // (CORRECT) back to physical space, and the working copies forward (tail)
+    const int nxf = (mode == RK_STAGE ? 1 : (mode == RK_CORRECT ? 2 : 0)) + (tail ? 2 : 0);
+    const double xforms = (double)nxf * g.phys_elems() * g.n;
     double b = phys64_bytes() * 2;  // read master
     if (mode == RK_STAGE) {
       b += mixed_bytes() + phys_bytes();                      // phi~_t, V
@@ -654,6 +664,7 @@ struct Planner {
     ps.nsize = g.nx;
     ps.rk = p;
     ps.bytes = b;
+    ps.xforms = xforms;
     return ps;
   }
 
@@ -1604,6 +1615,19 @@ int sbi_step_bytes(const sbi_ctx* cc, int family, double* bytes) {
   for (auto& p : ps)
     if (family < 0 || family_of(p) == family) b += p.bytes;
   *bytes = b;
+  return SBI_OK;
+}
+
+int sbi_step_transforms(const sbi_ctx* cc, int family, double* point_transforms) {
+  sbi_ctx* c = const_cast<sbi_ctx*>(cc);
+  if (!c || !point_transforms) return SBI_EINVAL;
+  bool oom = false;
+  std::vector<Pass> ps = plan_step(c, 1.0, &oom);
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  double x = 0.0;
+  for (auto& p : ps)
+    if (family < 0 || family_of(p) == family) x += p.xforms;
+  *point_transforms = x;
   return SBI_OK;
 }
 

@@ -63,6 +63,7 @@ EXPORTS = {
                                    C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int)]),
     "sbi_step_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "sbi_step_transforms": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sbi_step_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "sbi_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
@@ -264,6 +265,11 @@ class Context:
         buf = C.create_string_buffer(need.value + 1)
         self._check(self.lib.sbi_autotune_report(self.ctx, buf, len(buf), C.byref(need)))
         return buf.value.decode()
+
+    def step_transforms(self, family=-1):
+        x = C.c_double()
+        self._check(self.lib.sbi_step_transforms(self.ctx, family, C.byref(x)))
+        return x.value
 
     def step_launches(self):
         n = C.c_int()
