@@ -21,16 +21,17 @@ namespace sbi {
 // ===========================================================================
 // Row passes
 // ===========================================================================
-// Row-pass geometry.  Up to n = 256 a row is transformed by one warp or less
-// with 8 elements per thread (radix-8 Stockham passes, warp-synchronous), and
-// a block holds up to 512 threads; in FP32 such blocks are compiled for two
-// resident blocks per SM (64 registers per thread), which doubles the warps
-// per SM over 16 elements per thread.  Longer rows use 16 elements per thread
-// and block-wide barriers.
+// Row-pass geometry: 8 elements per thread (radix-8 Stockham passes).  Up to
+// n = 256 a row is transformed by one warp or less (warp-synchronous), longer
+// rows by several warps with block barriers; a block holds up to 512
+// threads.  In FP32 the blocks are compiled for two resident blocks per SM
+// (64 registers per thread, no spills): measured against 16 elements per
+// thread this doubles the warps per SM and runs the row passes faster at
+// every size.
 template <int NX>
 struct RowCfg {
   static constexpr int n = NX / 2;                         // packed complex length
-  static constexpr int R = (n >= 512) ? 16 : cmin(8, n);   // elements per thread
+  static constexpr int R = cmin(8, n);   // elements per thread
   static constexpr int TPR = n / R;                        // threads per row
   static constexpr bool WARP = TPR <= 32;
   static constexpr int RPC_MAX = cmin(256, WARP ? cmax(16, 512 / TPR) : cmax(1, 512 / TPR));
@@ -38,7 +39,7 @@ struct RowCfg {
   static constexpr int FBUF = padded_len(n);
   template <typename T>
   // 0: no minimum, the register count is left to the compiler
-  static constexpr int min_blocks() { return (WARP && R <= 8 && sizeof(T) == 4) ? 2 : 0; }
+  static constexpr int min_blocks() { return sizeof(T) == 4 ? 2 : 0; }
 };
 
 // Row stride of the staging buffer: odd, so that the rows of a block fall on
@@ -579,12 +580,12 @@ k_rk(const __grid_constant__ RkParams p) {
 // Inverse transforms use F^{-1}(X) = conj(F(conj X)) so one (forward) FFT
 // instantiation serves both directions.
 // ===========================================================================
-// Column-pass geometry: 8 elements per thread up to NY = 512 (one warp per
-// column at 256, two at 512), 16 beyond.  In FP32 the radix-8 columns of at
-// least a warp are compiled for four resident blocks per SM (64 registers).
+// Column-pass geometry: 8 elements per thread (one warp per column at 256,
+// two at 512, ...).  In FP32 columns of at least a warp are compiled for four
+// resident blocks per SM (64 registers).
 template <typename T, int NY>
 struct ColCfg {
-  static constexpr int RC = NY == 1 ? 1 : (NY <= 512 ? cmin(8, NY) : 16);
+  static constexpr int RC = NY == 1 ? 1 : cmin(8, NY);
   static constexpr int TPC = NY / RC;
   static constexpr bool WARP = TPC <= 32;
   // 8-byte elements: 256 threads per block; 16-byte elements: half the columns
