@@ -395,16 +395,16 @@ def main():
     e2e = None
     if not args.no_e2e:
         ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0)
-        host = [(torch.from_numpy(np.ascontiguousarray(m.eta)).pin_memory(),
-                 torch.from_numpy(np.ascontiguousarray(m.phi)).pin_memory()) for m in wl.members]
-        outs = [(torch.empty_like(e).pin_memory(), torch.empty_like(p).pin_memory())
-                for e, p in host]
+        # every member's eta and phi~, concatenated in member order, in pinned memory
+        eta_h = torch.from_numpy(np.concatenate([np.ravel(m.eta) for m in wl.members])).pin_memory()
+        phi_h = torch.from_numpy(np.concatenate([np.ravel(m.phi) for m in wl.members])).pin_memory()
+        eta_o = torch.empty_like(eta_h).pin_memory()
+        phi_o = torch.empty_like(phi_h).pin_memory()
+
         def e2e_step():
-            for i, (e, p) in enumerate(host):
-                ctx_e.set_state(i, e, p)
+            ctx_e.set_state_all(eta_h, phi_h)
             ctx_e.step(wl.dt, 1)
-            for i, (e, p) in enumerate(outs):
-                ctx_e.get_state(i, e, p)
+            ctx_e.get_state_all(eta_o, phi_o)
         for _ in range(max(1, args.warmup)):
             e2e_step()
         torch.cuda.synchronize()
@@ -414,10 +414,10 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        nbytes = sum(2 * e.numel() * 8 for e, _ in host)
+        nbytes = 2 * eta_h.numel() * 8
         e2e = {"value": pts * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ke,
-               "api": "sbi_set_state(host) + sbi_step(dt, 1) + sbi_get_state(host) per member"}
+               "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + sbi_get_state_all(pinned host)"}
         ctx_e.close()
 
     cpu = None

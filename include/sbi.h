@@ -128,6 +128,18 @@ int sbi_set_state(sbi_ctx* ctx, int member, const double* eta, const double* phi
 /* Copy the state of one member out (nx*ny doubles each).  Synchronizes the stream. */
 int sbi_get_state(sbi_ctx* ctx, int member, double* eta, double* phi, int on_device);
 
+/* Set / copy out the state of every member at once.  eta and phi each hold
+ * sum over members of nx*ny doubles: member 0's field (row-major), then
+ * member 1's, and so on, in member order.  The result is the same as one
+ * sbi_set_state / sbi_get_state per member; the work is batched per member
+ * group (one staging buffer of the group's size, allocated on first use and
+ * kept, one conversion and one dealias pass per group) and the stream is
+ * synchronized once.  Host buffers in pinned memory make the copies
+ * asynchronous DMA.  The paper has no counterpart (the calls batch its
+ * per-problem initial condition and output). */
+int sbi_set_state_all(sbi_ctx* ctx, const double* eta, const double* phi, int on_device);
+int sbi_get_state_all(sbi_ctx* ctx, double* eta, double* phi, int on_device);
+
 /* Surface vertical velocity V = sqrt(1+|grad eta|^2) dphi/dn at the current
  * state (Sec. 2.2-2.4), nx*ny doubles.  With eulerian_w = 1 the Eulerian
  * vertical velocity at the surface, w = (V + grad eta . grad phi~)/(1+|grad eta|^2),

@@ -85,6 +85,7 @@ struct Group {
   double *eta0 = nullptr, *phi0 = nullptr, *acc_eta = nullptr, *acc_phi = nullptr;
   void *eta_w = nullptr, *Vphys = nullptr, *delta = nullptr, *wout = nullptr;
   double* out64 = nullptr;   // conversion buffer for one member's field
+  double* stage64 = nullptr; // conversion buffer for every member's field (batch calls; lazy)
   int* d_active = nullptr;   // per-member flags for single-member passes
   int* d_conv = nullptr;     // adaptive order: 1 while a member still iterates
   int* d_orders = nullptr;   // adaptive order: orders used by the last diagnostic
@@ -1449,6 +1450,85 @@ int sbi_set_state(sbi_ctx* c, int member, const double* eta, const double* phi, 
   rc = run_passes(c, ps, c->cap);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->cap), "set_state");
+  return SBI_OK;
+}
+
+// offset (in doubles) of each member's field in a concatenated buffer
+std::vector<size_t> member_offsets(const sbi_ctx* c) {
+  std::vector<size_t> off(c->nmembers + 1, 0);
+  for (int m = 0; m < c->nmembers; ++m) {
+    const Group& g = c->groups[c->where[m].first];
+    off[m + 1] = off[m] + g.phys_elems();
+  }
+  return off;
+}
+
+int ensure_stage(sbi_ctx* c, Group& g) {
+  if (!g.stage64) g.stage64 = (double*)dalloc(c, g.phys_elems() * g.n * 8);
+  return g.stage64 ? SBI_OK : fail(c, SBI_ENOMEM, "device allocation failed");
+}
+
+int sbi_set_state_all(sbi_ctx* c, const double* eta, const double* phi, int on_device) {
+  if (!c) return SBI_EINVAL;
+  if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
+  const std::vector<size_t> off = member_offsets(c);
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    Group& g = c->groups[gi];
+    int rc = ensure_stage(c, g);
+    if (rc) return rc;
+    const size_t np = g.phys_elems();
+    const double* srcs[2] = {eta, phi};
+    double* dsts[2] = {g.eta0, g.phi0};
+    for (int q = 0; q < 2; ++q) {
+      // gather the group's members into the staging buffer, then convert
+      for (int li = 0; li < g.n; ++li) {
+        const int m = g.members[li];
+        CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[m], np * 8, kind, c->cap),
+           "copy state");
+      }
+      cudaError_t e = c->fp64 ? state_convert<double>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap)
+                              : state_convert<float>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap);
+      CK(e, "state conversion");
+    }
+    // dealias (or only refresh the working copies of) every member of the group
+    Planner pl{c, g};
+    std::vector<Pass> ps;
+    if (c->opt.set_state_dealias) pl.plan_project(ps, false);
+    else ps.push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
+    if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+    rc = run_passes(c, ps, c->cap);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->cap), "set_state_all");
+  return SBI_OK;
+}
+
+int sbi_get_state_all(sbi_ctx* c, double* eta, double* phi, int on_device) {
+  if (!c) return SBI_EINVAL;
+  if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
+  const std::vector<size_t> off = member_offsets(c);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    Group& g = c->groups[gi];
+    int rc = ensure_stage(c, g);
+    if (rc) return rc;
+    const size_t np = g.phys_elems();
+    const double* srcs[2] = {g.eta0, g.phi0};
+    double* dsts[2] = {eta, phi};
+    for (int q = 0; q < 2; ++q) {
+      cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream)
+                              : state_convert<float>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream);
+      CK(e, "state conversion");
+      for (int li = 0; li < g.n; ++li) {
+        const int m = g.members[li];
+        CK(cudaMemcpyAsync(dsts[q] + off[m], g.stage64 + (size_t)li * np, np * 8, kind, c->stream),
+           "copy state");
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream), "get_state_all");
   return SBI_OK;
 }
 

@@ -54,6 +54,8 @@ EXPORTS = {
     "sbi_num_members": (C.c_int, [C.c_void_p]),
     "sbi_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "sbi_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "sbi_set_state_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "sbi_get_state_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sbi_vertical_velocity": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -220,6 +222,44 @@ class Context:
         pe, de, _ = _ptr(eta)
         pp, dp, _ = _ptr(phi)
         self._check(self.lib.sbi_get_state(self.ctx, member, pe, pp, de))
+        return eta, phi
+
+    def total_points(self):
+        return sum(g[0] * g[1] for g in self.grids)
+
+    def split(self, flat):
+        """Per-member (ny, nx) views of a concatenated field (member order)."""
+        out, o = [], 0
+        for g in self.grids:
+            n = g[0] * g[1]
+            out.append(flat[o:o + n].reshape(g[1], g[0]))
+            o += n
+        return out
+
+    def set_state_all(self, eta, phi):
+        """sbi_set_state_all: eta, phi hold every member's field concatenated
+        in member order (numpy arrays or contiguous float64 torch tensors)."""
+        pe, de, ke = _ptr(eta)
+        pp, dp, kp = _ptr(phi)
+        if de != dp:
+            raise ValueError("eta and phi must both be host or both be device buffers")
+        for a in (ke, kp):
+            if int(np.prod(a.shape)) != self.total_points():
+                raise ValueError("eta and phi must hold every member's points")
+        self._check(self.lib.sbi_set_state_all(self.ctx, pe, pp, de))
+
+    def get_state_all(self, eta=None, phi=None):
+        if eta is None:
+            eta = np.empty(self.total_points())
+            phi = np.empty(self.total_points())
+        pe, de, ke = _ptr(eta)
+        pp, dp, kp = _ptr(phi)
+        if de != dp:
+            raise ValueError("eta and phi must both be host or both be device buffers")
+        for a in (ke, kp):
+            if int(np.prod(a.shape)) != self.total_points():
+                raise ValueError("eta and phi must hold every member's points")
+        self._check(self.lib.sbi_get_state_all(self.ctx, pe, pp, de))
         return eta, phi
 
     def vertical_velocity(self, member=0, out=None, eulerian_w=False):

@@ -164,6 +164,28 @@ def test_autotuned_block_shapes_give_identical_results(sbi, prec):
             assert np.array_equal(out[0][m][f], out[1][m][f])
 
 
+@pytest.mark.parametrize("dealias", [0, 1])
+def test_batch_state_calls_equal_per_member_calls(sbi, dealias):
+    # sbi_set_state_all / sbi_get_state_all on members of interleaved sizes
+    # give the same bits as one sbi_set_state / sbi_get_state per member.
+    specs = [(64, 32, 6.0, 4.0), (32, 16, 3.0, 2.0), (64, 32, 6.0, 4.0), (128, 1, 9.0, 1.0)]
+    eta = [W.random_field(nx, ny, 80 + i, amplitude=0.03).ravel() for i, (nx, ny, _, _) in enumerate(specs)]
+    phi = [W.random_field(nx, ny, 90 + i, amplitude=0.2).ravel() for i, (nx, ny, _, _) in enumerate(specs)]
+    a = sbi.Context(specs, 9.81, None, h0=0.7, precision=0, set_state_dealias=dealias)
+    b = sbi.Context(specs, 9.81, None, h0=0.7, precision=0, set_state_dealias=dealias)
+    for i in range(len(specs)):
+        a.set_state(i, eta[i], phi[i])
+    b.set_state_all(np.concatenate(eta), np.concatenate(phi))
+    for ctx in (a, b):
+        ctx.step(0.01, 2)
+    ea, pa = a.get_state_all()
+    for i in range(len(specs)):
+        e1, p1 = a.get_state(i)
+        e2, p2 = b.get_state(i)
+        assert np.array_equal(e1, e2) and np.array_equal(p1, p2)
+        assert np.array_equal(a.split(ea)[i], e1) and np.array_equal(a.split(pa)[i], p1)
+
+
 def test_batch_of_uneven_grids_equals_single(sbi):
     specs = [(64, 32, 6.0, 4.0), (32, 16, 3.0, 2.0), (64, 32, 6.0, 4.0), (128, 1, 9.0, 1.0)]
     states = []
