@@ -56,6 +56,16 @@ R8  Low-pass filter (Eq. filter): Lambda = exp(-|k/(beta1 k_ref)|^beta2), applie
 R9  Order truncation: the scheme is explicit with a fixed maximum order M <= 7.
     An optional tolerance stops at the first l whose increment satisfies
     ||F{V_l}||_2 <= tol ||sum_{m<=l} F{V_m}||_2.
+R10 Pneumatic wavemaker (Eq. for p_g, submerged-bar section): the printed
+    pressure is nondimensional (g = 1); dimensionally
+    p_g / rho = g sum_j a_j sqrt(e/2pi) [1 + 2 k_j h0 / sinh(2 k_j h0)]
+                  exp(-(k_j d)^2 / 2) sin(omega_j t + theta_j),
+    with omega_j^2 = g k_j tanh(k_j h0), d the periodic distance in x from the
+    centre x0 (the bell "split in halves at both ends" is the bell centred at
+    x0 = 0 of the periodic box) and, in 2-D, no dependence on y (a line
+    source).  It enters the dynamic condition like p_d: phi~_t gets -p_g/rho,
+    inside the dealiasing of that right-hand side.  With this scaling linear
+    theory gives radiated waves of amplitude a_j on each side.
 
 Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
 has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
@@ -261,10 +271,10 @@ def damping_pressure(phi, weight, nu, grid: Grid, alpha: float = 0.5):
     return nu * ifft(mask * inv * ik_dot(prod, KX, KY))
 
 
-def dynamic_rhs(eta, phi, V, gravity, grid: Grid, alpha: float = 0.5):
+def dynamic_rhs(eta, phi, V, gravity, grid: Grid, alpha: float = 0.5, pressure=None):
     """phi~_t without the damping pressure: the second line of Eq. (prognostic)
     written in physical space, -g eta + 1/2[(V + grad eta.grad phi~)^2/(1+|grad eta|^2)
-    - |grad phi~|^2], dealiased (R5)."""
+    - |grad phi~|^2] (minus a surface pressure / rho when given), dealiased (R5)."""
     KX, KY, K = wavenumbers(grid)
     mask = dealias_mask(grid, alpha)
     eta = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
@@ -275,7 +285,48 @@ def dynamic_rhs(eta, phi, V, gravity, grid: Grid, alpha: float = 0.5):
     ge2 = sum(a * a for a in ge)
     gp2 = sum(a * a for a in gp)
     n2 = -gravity * eta + 0.5 * ((V + dot) ** 2 / (1.0 + ge2) - gp2)
+    if pressure is not None:
+        n2 = n2 - pressure
     return ifft(mask * fft(n2))
+
+
+@dataclass
+class Wavemaker:
+    """Components of the pneumatic wavemaker (R10): amplitudes a_j [m], angular
+    frequencies omega_j [rad/s], phases theta_j, and the centre x0 [m]."""
+    amp: np.ndarray
+    omega: np.ndarray
+    phase: np.ndarray
+    x0: float = 0.0
+
+
+def dispersion_wavenumber(omega: float, h0: float, gravity: float) -> float:
+    """k with omega^2 = g k tanh(k h0) (Newton from the deep-water value)."""
+    k = omega * omega / gravity
+    if math.isinf(h0):
+        return k
+    for _ in range(100):
+        t = math.tanh(k * h0)
+        f = gravity * k * t - omega * omega
+        df = gravity * (t + k * h0 * (1.0 - t * t))
+        dk = f / df
+        k -= dk
+        if abs(dk) <= 1e-15 * k:
+            break
+    return k
+
+
+def wavemaker_pressure(wm: Wavemaker, grid: Grid, h0: float, gravity: float, t: float):
+    """p_g / rho of R10 at time t on the grid, shape (ny, nx)."""
+    x = np.arange(grid.nx) * (grid.Lx / grid.nx)
+    d = np.mod(x - wm.x0 + 0.5 * grid.Lx, grid.Lx) - 0.5 * grid.Lx
+    p = np.zeros(grid.nx)
+    for a, w, th in zip(np.atleast_1d(wm.amp), np.atleast_1d(wm.omega), np.atleast_1d(wm.phase)):
+        k = dispersion_wavenumber(float(w), h0, gravity)
+        shoal = 1.0 if math.isinf(h0) else 1.0 + 2.0 * k * h0 / math.sinh(2.0 * k * h0)
+        p += (gravity * a * math.sqrt(math.e / (2.0 * math.pi)) * shoal
+              * np.exp(-0.5 * (k * d) ** 2) * math.sin(w * t + th))
+    return np.broadcast_to(p, (grid.ny, grid.nx)).copy()
 
 
 @dataclass
@@ -292,12 +343,16 @@ class Problem:
     filt_beta2: float = 0.0
     k_ref: float = 1.0
     adapt_tol: float = 0.0      # R9: 0 = fixed order
+    wavemaker: "Wavemaker | None" = None   # R10
 
 
-def surface_rhs(pb: Problem, eta, phi):
-    """(eta_t, phi~_t) of Eq. (prognostic) in physical space."""
+def surface_rhs(pb: Problem, eta, phi, t: float = 0.0):
+    """(eta_t, phi~_t) of Eq. (prognostic) in physical space at time t."""
     V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
-    phi_t = dynamic_rhs(eta, phi, V, pb.gravity, pb.grid, pb.alpha)
+    pg = None
+    if pb.wavemaker is not None:
+        pg = wavemaker_pressure(pb.wavemaker, pb.grid, pb.h0, pb.gravity, t)
+    phi_t = dynamic_rhs(eta, phi, V, pb.gravity, pb.grid, pb.alpha, pressure=pg)
     if pb.sponge_w is not None and pb.sponge_nu != 0.0:
         phi_t = phi_t - damping_pressure(phi, pb.sponge_w, pb.sponge_nu, pb.grid, pb.alpha)
     return V, phi_t
@@ -312,24 +367,25 @@ def project(pb: Problem, f):
     return ifft(m * fft(np.asarray(f, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)))
 
 
-def rk4_step(f, y, dt):
-    """Classical RK4 for y' = f(y); y is a tuple of arrays."""
+def rk4_step(f, y, dt, t=0.0):
+    """Classical RK4 for y' = f(t, y) from time t; y is a tuple of arrays."""
     def axpy(a, x, b):
         return tuple(xi + a * bi for xi, bi in zip(x, b))
-    k1 = f(y)
-    k2 = f(axpy(0.5 * dt, y, k1))
-    k3 = f(axpy(0.5 * dt, y, k2))
-    k4 = f(axpy(dt, y, k3))
+    k1 = f(t, y)
+    k2 = f(t + 0.5 * dt, axpy(0.5 * dt, y, k1))
+    k3 = f(t + 0.5 * dt, axpy(0.5 * dt, y, k2))
+    k4 = f(t + dt, axpy(dt, y, k3))
     return tuple(yi + dt / 6.0 * (a + 2.0 * b + 2.0 * c + d)
                  for yi, a, b, c, d in zip(y, k1, k2, k3, k4))
 
 
-def step(pb: Problem, eta, phi, dt: float, n: int = 1):
-    """n RK4 steps of (eta, phi~), each followed by the projection of R5/R8."""
+def step(pb: Problem, eta, phi, dt: float, n: int = 1, t0: float = 0.0):
+    """n RK4 steps of (eta, phi~) from time t0, each followed by the
+    projection of R5/R8."""
     y = (np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx),
          np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx))
-    for _ in range(n):
-        y = rk4_step(lambda s: surface_rhs(pb, s[0], s[1]), y, dt)
+    for i in range(n):
+        y = rk4_step(lambda t, s: surface_rhs(pb, s[0], s[1], t), y, dt, t0 + i * dt)
         y = (project(pb, y[0]), project(pb, y[1]))
     return y
 

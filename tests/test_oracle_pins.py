@@ -348,3 +348,67 @@ def test_low_pass_filter_special_values():
     pb2 = O.Problem(g, 9.81, 1.0, alpha=1.0, filt_beta1=b1, filt_beta2=4.0, k_ref=k_ref)
     out2 = O.project(pb2, np.cos(16 * x)[None, :])
     assert abs(2.0 * np.mean(out2[0] * np.cos(16 * x)) - math.exp(-1.0)) < 1e-12
+
+
+@pytest.mark.parametrize("h0,T,L,xs", [(0.5, 1.2, 60.0, (10.0, 50.0)), (0.5, 3.0, 120.0, (20.0, 100.0))])
+def test_wavemaker_radiates_waves_of_amplitude_a(h0, T, L, xs):
+    # R10: with the pressure of the submerged-bar section (scaled by g), linear
+    # theory gives a radiated wave of amplitude a_j on each side: the Fourier
+    # transform of the bell at k_j cancels sqrt(e/2pi) and the shoaling factor
+    # [1 + 2kh/sinh 2kh] cancels the group velocity.  A small-amplitude run
+    # (order 1) with the paper's Gaussian damping zone (centred at L/2, width
+    # 4 pi / k) is fitted at two gauges after the front has passed.  Cases
+    # kh = 1.53 (factor 1.29) and kh = 0.5 (factor 1.85).
+    g, nx, a = 9.81, 512, 1e-4
+    w = 2 * math.pi / T
+    k = O.dispersion_wavenumber(w, h0, g)
+    grid = O.Grid(nx, 1, L)
+    x = np.arange(nx) * L / nx
+    damp = np.exp(-(k * (x - L / 2) / (4 * math.pi)) ** 2)[None, :]
+    wm = O.Wavemaker(np.array([a]), np.array([w]), np.array([0.0]), 0.0)
+    pb = O.Problem(grid, g, h0, order=1, sponge_w=damp, sponge_nu=w, wavemaker=wm)
+    dt = T / 40
+    idx = [int(round(xi / (L / nx))) for xi in xs]
+    eta, phi = np.zeros((1, nx)), np.zeros((1, nx))
+    t_end = 10.0 * T if T > 2 else 20.0 * T
+    n = int(round(t_end / dt))
+    rec = []
+    for i in range(n):
+        eta, phi = O.step(pb, eta, phi, dt, 1, t0=i * dt)
+        rec.append(eta[0, idx])
+    rec = np.array(rec)
+    t = (np.arange(n) + 1) * dt
+    sel = t >= t_end - 4 * T
+    basis = np.stack([np.cos(w * t[sel]), np.sin(w * t[sel]), np.ones(sel.sum())], 1)
+    for c in range(len(idx)):
+        coef, *_ = np.linalg.lstsq(basis, rec[sel, c], rcond=None)
+        amp = math.hypot(coef[0], coef[1])
+        assert abs(amp / a - 1.0) < 0.02, (h0, T, xs[c], amp / a)
+
+
+def test_wavemaker_pressure_shape():
+    # R10: the bell is centred at x0 on the periodic box, symmetric, of
+    # e-folding half-width sqrt(2)/k, and proportional to sin(omega t + theta).
+    g, h0 = 9.81, 0.4
+    grid = O.Grid(256, 1, 20.0)
+    wm = O.Wavemaker(np.array([0.01]), np.array([4.0]), np.array([0.3]), 5.0)
+    k = O.dispersion_wavenumber(4.0, h0, g)
+    t = 0.7
+    p = O.wavemaker_pressure(wm, grid, h0, g, t)[0]
+    x = np.arange(256) * 20.0 / 256
+    i0 = int(round(5.0 / (20.0 / 256)))
+    peak = g * 0.01 * math.sqrt(math.e / (2 * math.pi)) * (1 + 2 * k * h0 / math.sinh(2 * k * h0)) * math.sin(4.0 * t + 0.3)
+    assert abs(p[i0] - peak) < 1e-12 * abs(peak)
+    for m in (1, 5, 17):
+        assert abs(p[i0 + m] - p[i0 - m]) < 1e-14
+        d = m * 20.0 / 256
+        assert abs(p[i0 + m] - peak * math.exp(-0.5 * (k * d) ** 2)) < 1e-12
+    # periodic: the bell wraps around the ends
+    wm2 = O.Wavemaker(np.array([0.01]), np.array([4.0]), np.array([0.3]), 0.0)
+    p2 = O.wavemaker_pressure(wm2, grid, h0, g, t)[0]
+    assert abs(p2[1] - p2[-1]) < 1e-14
+    # deep water: the shoaling factor is 1
+    p3 = O.wavemaker_pressure(wm, grid, math.inf, g, t)[0]
+    k3 = 16.0 / g
+    assert abs(p3[i0] - g * 0.01 * math.sqrt(math.e / (2 * math.pi)) * math.sin(4.0 * t + 0.3)) < 1e-12
+    assert abs(p3[i0 + 3] / p3[i0] - math.exp(-0.5 * (k3 * 3 * 20.0 / 256) ** 2)) < 1e-12
