@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="crossing_batch",
-                    choices=["crossing_batch", "large_variable", "bar_1d", "stokes_2d"])
+                    choices=["crossing_batch", "large_variable", "bar_1d", "stokes_2d",
+                             "bar_wavemaker_1d", "solitary_1d"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,7 +82,10 @@ def workload_config(wl):
            "alias_frac": wl.alpha, "dt": wl.dt,
            "filter": bool(wl.filt_beta1 > 0), "sponge": wl.sponge_w is not None,
            "variable_depth": any(m.delta is not None for m in wl.members),
-           "l2": "inputs larger than L2 (no flush needed)"}
+           "l2": ("inputs larger than L2 (no flush needed)" if wl.points * 150 > 129e6 else
+                  "working set fits in L2 (about 150 B per point, not flushed): small-workload timing")}
+    if wl.wavemaker:
+        cfg["wavemaker"] = {"components": len(wl.wavemaker["amp"]), "x0": wl.wavemaker["x0"]}
     return cfg
 
 
@@ -208,10 +212,14 @@ def make_context(sbi, wl, precision, stream, **extra):
     grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in wl.members]
     depths = [(m.h0 - m.delta) if m.delta is not None else None for m in wl.members]
     h0 = wl.members[0].h0
-    return sbi.Context(grids, wl.gravity, depths, h0=h0, order=wl.order, alias_frac=wl.alpha,
-                       precision=precision, filt_beta1=wl.filt_beta1, filt_beta2=wl.filt_beta2,
-                       k_ref=wl.k_ref, sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu,
-                       stream=stream, check_finite=0, **extra)
+    ctx = sbi.Context(grids, wl.gravity, depths, h0=h0, order=wl.order, alias_frac=wl.alpha,
+                      precision=precision, filt_beta1=wl.filt_beta1, filt_beta2=wl.filt_beta2,
+                      k_ref=wl.k_ref, sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu,
+                      stream=stream, check_finite=0, **extra)
+    if wl.wavemaker:
+        ctx.set_wavemaker(wl.wavemaker["amp"], wl.wavemaker["omega"], wl.wavemaker["phase"],
+                          wl.wavemaker["x0"])
+    return ctx
 
 
 def time_steps(ctx, torch, stream, dt, steps, warmup):
@@ -248,7 +256,10 @@ def cpu_oracle_sample(wl, target_s=10.0):
         g = O.Grid(m.nx, m.ny, m.Lx, m.Ly)
         pb = O.Problem(g, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
                        sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
-                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref,
+                       wavemaker=None if not wl.wavemaker else O.Wavemaker(
+                           np.array(wl.wavemaker["amp"]), np.array(wl.wavemaker["omega"]),
+                           np.array(wl.wavemaker["phase"]), wl.wavemaker["x0"]))
         t0 = time.perf_counter()
         O.step(pb, m.eta, m.phi, wl.dt, 1)
         t_tot += time.perf_counter() - t0

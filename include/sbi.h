@@ -157,6 +157,29 @@ int sbi_step(sbi_ctx* ctx, double dt, int n);
  * Synchronizes the stream. */
 int sbi_invariants(sbi_ctx* ctx, int member, double* mass, double* energy);
 
+/* Simulation time t [s] of the context: 0 after creation, advanced by dt for
+ * every step of sbi_step.  It sets the phase of the wavemaker pressure. */
+int sbi_set_time(sbi_ctx* ctx, double t);
+int sbi_get_time(const sbi_ctx* ctx, double* t);
+
+/* Pneumatic wavemaker of the submerged-bar section (Sec. 3, its Eq. for p_g):
+ * a surface pressure subtracted in the dynamic condition, as the damping
+ * pressure of Eq. (pd) is,
+ *   p_g / rho = g sum_j a_j sqrt(e/2pi) [1 + 2 k_j h0 / sinh(2 k_j h0)]
+ *                 exp(-(k_j d)^2 / 2) sin(omega_j t + theta_j),
+ * with omega_j^2 = g k_j tanh(k_j h0) (h0 of each member group; deep water:
+ * the bracket is 1), d the periodic distance in x from x0 and no dependence on
+ * y (a line source in 2-D).  In linear theory it radiates waves of amplitude
+ * a_j on both sides.  The printed pressure is nondimensional (g = 1); the
+ * factor g is this library's dimensional reading.
+ *   ncomp  number of components J, 0..256 (0 removes the wavemaker)
+ *   amp, omega, phase   J host doubles each: a_j [m], omega_j [rad/s] > 0, theta_j
+ *   x0     centre of the bell [m] (0: split in halves at both ends of the box)
+ * The pressure of each RK4 stage is evaluated at the stage's time.  The step
+ * graph is re-captured.  SBI_EINVAL for bad arguments. */
+int sbi_set_wavemaker(sbi_ctx* ctx, int ncomp, const double* amp, const double* omega,
+                      const double* phase, double x0);
+
 /* Orders used by the last diagnostic of a member (M unless adapt_tol > 0). */
 int sbi_orders_used(sbi_ctx* ctx, int member, int* orders);
 

@@ -312,6 +312,7 @@ k_row(const __grid_constant__ RowParams p) {
       const V* sPy = two_d ? slot_base + ((op.slot + 4) * rpc + rloc) * n : nullptr;
       const T g = T(op.coef);
       V* wout = (op.kind == ROP_WDOT && act) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
+      const V* pgr = (op.kind == ROP_N2 && p.pg) ? reinterpret_cast<const V*>(p.pg) : nullptr;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
@@ -319,9 +320,11 @@ k_row(const __grid_constant__ RowParams p) {
         const V ey = two_d ? sEy[m] : mk<V>(T(0), T(0));
         const V py = two_d ? sPy[m] : mk<V>(T(0), T(0));
         const V e = eta ? __ldg(eta + m) : mk<V>(T(0), T(0));
+        const V pw = pgr ? __ldg(pgr + m) : mk<V>(T(0), T(0));
         T res[2];
         const T vc[2] = {vv.x, vv.y}, exc[2] = {ex.x, ex.y}, eyc[2] = {ey.x, ey.y};
         const T pxc[2] = {px.x, px.y}, pyc[2] = {py.x, py.y}, ec[2] = {e.x, e.y};
+        const T pwc[2] = {pw.x, pw.y};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const T dot = exc[h] * pxc[h] + eyc[h] * pyc[h];
@@ -329,7 +332,7 @@ k_row(const __grid_constant__ RowParams p) {
           const T gp2 = pxc[h] * pxc[h] + pyc[h] * pyc[h];
           const T num = vc[h] + dot;
           if (op.kind == ROP_N2)
-            res[h] = -g * ec[h] + T(0.5) * (num * num / (T(1) + ge2) - gp2);
+            res[h] = -g * ec[h] + T(0.5) * (num * num / (T(1) + ge2) - gp2) - pwc[h];
           else
             res[h] = num / (T(1) + ge2);
         }

@@ -41,7 +41,7 @@ namespace {
 
 std::string g_create_error = "no error";
 
-enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2, PK_CONV = 3 };
+enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2, PK_CONV = 3, PK_WMK = 4 };
 
 // Device-side convergence test of the adaptive order (opt.adapt_tol > 0):
 // after order l, per member, inc = ||F{V_l}||^2 and tot = ||F{V_1 + .. + V_l}||^2
@@ -60,10 +60,22 @@ struct ConvParams {
   int *conv, *orders, *notconv;
   double* red;          // [n][kConvBlocks][2]
 };
-enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_CONV = 3, FAM_COUNT = 4 };
+// Pneumatic wavemaker: the surface pressure profile along x at one stage
+// time, out[x] = sum_j prof[j][x] sin(omega_j t_s + theta_j), t_s = *t + offset.
+struct WmkParams {
+  const double* prof;    // [J][nx] FP64 bells g a_j C_j exp(-(k_j d)^2 / 2)
+  const double* omega;   // [J]
+  const double* phase;   // [J]
+  const double* t;       // simulation time of the step start (device)
+  double offset;         // stage time minus step start
+  void* out;             // nx reals in the working precision
+  int J, nx;
+};
+enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_CONV = 3, FAM_WMK = 4, FAM_COUNT = 5 };
 const char* kFamilyNames[FAM_COUNT] = {"k_col (column FFT + spectral combine)",
                                        "k_row (row FFT + products)", "k_rk (RK4 stage)",
-                                       "k_conv (adaptive-order test)"};
+                                       "k_conv (adaptive-order test)",
+                                       "k_wavemaker (surface pressure profile)"};
 
 struct Pass {
   PassKind kind;
@@ -72,6 +84,7 @@ struct Pass {
   ColParams col;
   RkParams rk;
   ConvParams conv;
+  WmkParams wmk;
   double bytes;   // algorithmic device-memory traffic of the launch
   double xforms;  // 1-D transform passes over a whole field, times the field's points
 };
@@ -91,6 +104,9 @@ struct Group {
   int* d_orders = nullptr;   // adaptive order: orders used by the last diagnostic
   int* d_notconv = nullptr;  // adaptive order: tolerance not met at the highest order
   double* d_red = nullptr;   // adaptive order: partial norms
+  double* wm_prof = nullptr; // wavemaker bells [J][nx] (FP64)
+  void* wm_pg = nullptr;     // wavemaker pressure profile of the current stage (nx)
+  int wm_cap = 0;            // components wm_prof has room for
   std::map<std::string, void*> mixed;
   std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
@@ -142,6 +158,12 @@ struct sbi_ctx {
   std::map<std::string, Tuned> tuned;
   std::vector<std::string> tune_order;  // signatures in the order they were tuned
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  // simulation time (advanced by sbi_step) and the pneumatic wavemaker
+  double t_host = 0.0;
+  double* d_time = nullptr;
+  int wm_n = 0;
+  double* wm_params = nullptr;  // [omega_0..omega_{J-1}, theta_0..theta_{J-1}] on the device
+  int wm_params_cap = 0;
   bool filter_on() const { return opt.filt_beta1 > 0.0; }
 };
 
@@ -601,7 +623,16 @@ struct Planner {
   }
 
   // Row RHS + Col RHS: phi~_t = M F^{-1}{F{N2} + nu ik/k^2 . F{w grad phi~}}
-  void plan_rhs(std::vector<Pass>& out) {
+  void plan_rhs(std::vector<Pass>& out, double stage_offset = 0.0) {
+    if (c->wm_n > 0) {
+      Pass w{};
+      w.kind = PK_WMK;
+      w.nsize = g.nx;
+      w.wmk = WmkParams{g.wm_prof, c->wm_params, c->wm_params + c->wm_n, c->d_time, stage_offset,
+                        g.wm_pg, c->wm_n, g.nx};
+      w.bytes = (double)c->wm_n * g.nx * 8 + (double)g.nx * c->real_size;
+      out.push_back(w);
+    }
     RowB r = row_begin();
     c2r(r, 0, v_names(), g.Vphys);
     int s = 1;
@@ -615,6 +646,7 @@ struct Planner {
       for (char d : dims()) prod(r, q++, 0, 0, 1, 1.0, std::string("SP") + d);
     }
     out.push_back(row_end(r, true, false, sponge));
+    if (c->wm_n > 0) out.back().row.pg = g.wm_pg;
     std::vector<ColIn> ins = {{"N2", {term(0, 1.0, 0, 0, 0, 0)}}};
     if (sponge) {
       for (char d : dims())
@@ -788,10 +820,33 @@ __global__ void k_conv_update(ConvParams q) {
   }
 }
 
+// Wavemaker pressure at a stage time (FP64 sums and sines: omega t reaches
+// thousands of radians), rounded once to the working precision.
+template <typename T>
+__global__ void k_wavemaker(WmkParams q) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= q.nx) return;
+  const double t = *q.t + q.offset;
+  double acc = 0.0;
+  for (int j = 0; j < q.J; ++j) acc += q.prof[(size_t)j * q.nx + x] * sin(q.omega[j] * t + q.phase[j]);
+  reinterpret_cast<T*>(q.out)[x] = T(acc);
+}
+
+__global__ void k_advance_time(double* t, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t += dt;
+}
+
 // ---------------------------------------------------------------------------
 // Execution
 // ---------------------------------------------------------------------------
 int launch_pass(sbi_ctx* c, const Pass& p, cudaStream_t st) {
+  if (p.kind == PK_WMK) {
+    const WmkParams& q = p.wmk;
+    if (c->fp64) k_wavemaker<double><<<(q.nx + 255) / 256, 256, 0, st>>>(q);
+    else k_wavemaker<float><<<(q.nx + 255) / 256, 256, 0, st>>>(q);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SBI_OK : cuda_fail(c, e, "kernel launch");
+  }
   cudaError_t e = cudaSuccess;
   if (p.kind == PK_CONV) {
     const ConvParams& q = p.conv;
@@ -957,7 +1012,7 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
     Planner pl{c, g};
     for (int s = 1; s <= 4; ++s) {
       pl.plan_diag(all);
-      pl.plan_rhs(all);
+      pl.plan_rhs(all, (s == 1 ? 0.0 : (s == 4 ? 1.0 : 0.5)) * dt);  // stage times
       all.push_back(pl.plan_rk(RK_STAGE, s, dt, (s < 4 || !c->filter_on()) ? 1 : 0));
     }
     if (c->filter_on()) pl.plan_project(all, true);
@@ -974,7 +1029,13 @@ std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
 }
 
 int family_of(const Pass& p) {
-  return p.kind == PK_COL ? FAM_COL : (p.kind == PK_ROW ? FAM_ROW : (p.kind == PK_RK ? FAM_RK : FAM_CONV));
+  switch (p.kind) {
+    case PK_COL: return FAM_COL;
+    case PK_ROW: return FAM_ROW;
+    case PK_RK: return FAM_RK;
+    case PK_WMK: return FAM_WMK;
+    default: return FAM_CONV;
+  }
 }
 
 void free_graphs(sbi_ctx* c) {
@@ -1050,6 +1111,13 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
       cudaEventRecord(c->gevents[gi + 1], st);
       cudaStreamWaitEvent(c->cap, c->gevents[gi + 1], 0);
     }
+  }
+  // the simulation time of the next step (read by the wavemaker passes)
+  if (rc == SBI_OK && c->wm_n > 0) {
+    k_advance_time<<<1, 32, 0, c->cap>>>(c->d_time, dt);
+    const cudaError_t el = cudaGetLastError();
+    if (el != cudaSuccess) rc = cuda_fail(c, el, "kernel launch");
+    else ++npasses;
   }
   cudaError_t e = cudaStreamEndCapture(c->cap, &ge.graph);
   if (rc) return rc;
@@ -1593,6 +1661,7 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
   if (rc) return rc;
   for (int i = 0; i < n; ++i) {
     CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->t_host += dt;
     if (c->prof) {
       // the graph's event pairs hold this replay's per-pass device times
       CK(cudaStreamSynchronize(c->stream), "profile sync");
@@ -1644,6 +1713,97 @@ int sbi_invariants(sbi_ctx* c, int member, double* mass, double* energy) {
   const double dA = (g.Lx / g.nx) * (g.Ly / g.ny);
   *mass = m * dA;
   *energy = e * dA;
+  return SBI_OK;
+}
+
+int ensure_time(sbi_ctx* c) {
+  if (!c->d_time) {
+    c->d_time = (double*)dalloc(c, sizeof(double));
+    if (!c->d_time) return fail(c, SBI_ENOMEM, "device allocation failed");
+  }
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaMemcpy(c->d_time, &c->t_host, sizeof(double), cudaMemcpyHostToDevice), "copy time");
+  return SBI_OK;
+}
+
+int sbi_set_time(sbi_ctx* c, double t) {
+  if (!c) return SBI_EINVAL;
+  if (!std::isfinite(t)) return fail(c, SBI_EINVAL, "t must be finite");
+  c->t_host = t;
+  return ensure_time(c);
+}
+
+int sbi_get_time(const sbi_ctx* c, double* t) {
+  if (!c || !t) return SBI_EINVAL;
+  *t = c->t_host;
+  return SBI_OK;
+}
+
+int sbi_set_wavemaker(sbi_ctx* c, int ncomp, const double* amp, const double* omega,
+                      const double* phase, double x0) {
+  if (!c) return SBI_EINVAL;
+  if (ncomp < 0 || ncomp > 256) return fail(c, SBI_EINVAL, "ncomp must be in 0..256");
+  if (ncomp > 0 && (!amp || !omega || !phase)) return fail(c, SBI_EINVAL, "amp, omega and phase must not be NULL");
+  if (!std::isfinite(x0)) return fail(c, SBI_EINVAL, "x0 must be finite");
+  for (int j = 0; j < ncomp; ++j)
+    if (!std::isfinite(amp[j]) || !(omega[j] > 0.0) || !std::isfinite(omega[j]) || !std::isfinite(phase[j]))
+      return fail(c, SBI_EINVAL, "component %d: amp and phase must be finite, omega finite and > 0", j);
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaStreamSynchronize(c->cap), "sync");
+  free_graphs(c);   // the step's passes change
+  c->wm_n = 0;
+  if (ncomp == 0) return SBI_OK;
+  int rc = ensure_time(c);
+  if (rc) return rc;
+  if (ncomp > c->wm_params_cap) {
+    c->wm_params = (double*)dalloc(c, 2 * (size_t)ncomp * sizeof(double));
+    if (!c->wm_params) return fail(c, SBI_ENOMEM, "device allocation failed");
+    c->wm_params_cap = ncomp;
+  }
+  std::vector<double> par(2 * (size_t)ncomp);
+  for (int j = 0; j < ncomp; ++j) {
+    par[j] = omega[j];
+    par[ncomp + j] = phase[j];
+  }
+  CK(cudaMemcpy(c->wm_params, par.data(), par.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  const double bell = std::sqrt(std::exp(1.0) / (2.0 * M_PI));
+  for (auto& g : c->groups) {
+    if (ncomp > g.wm_cap) {
+      g.wm_prof = (double*)dalloc(c, (size_t)ncomp * g.nx * sizeof(double));
+      if (!g.wm_prof) return fail(c, SBI_ENOMEM, "device allocation failed");
+      g.wm_cap = ncomp;
+    }
+    if (!g.wm_pg) {
+      g.wm_pg = dalloc(c, (size_t)g.nx * c->real_size);
+      if (!g.wm_pg) return fail(c, SBI_ENOMEM, "device allocation failed");
+    }
+    // bells g a_j sqrt(e/2pi) [1 + 2 k_j h0 / sinh(2 k_j h0)] exp(-(k_j d)^2 / 2),
+    // omega_j^2 = g k_j tanh(k_j h0), d the periodic distance from x0
+    std::vector<double> prof((size_t)ncomp * g.nx);
+    for (int j = 0; j < ncomp; ++j) {
+      const double w2 = omega[j] * omega[j];
+      double k = w2 / c->gravity, shoal = 1.0;
+      if (std::isfinite(g.h0)) {
+        for (int it = 0; it < 100; ++it) {
+          const double t = std::tanh(k * g.h0);
+          const double dk = (c->gravity * k * t - w2) / (c->gravity * (t + k * g.h0 * (1.0 - t * t)));
+          k -= dk;
+          if (std::fabs(dk) <= 1e-15 * k) break;
+        }
+        shoal = 1.0 + 2.0 * k * g.h0 / std::sinh(2.0 * k * g.h0);
+      }
+      const double A = c->gravity * amp[j] * bell * shoal;
+      for (int x = 0; x < g.nx; ++x) {
+        const double xx = x * (g.Lx / g.nx);
+        double d = std::fmod(xx - x0 + 0.5 * g.Lx, g.Lx);
+        if (d < 0.0) d += g.Lx;
+        d -= 0.5 * g.Lx;
+        prof[(size_t)j * g.nx + x] = A * std::exp(-0.5 * (k * d) * (k * d));
+      }
+    }
+    CK(cudaMemcpy(g.wm_prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  }
+  c->wm_n = ncomp;
   return SBI_OK;
 }
 
@@ -1717,7 +1877,7 @@ int sbi_step_launches(const sbi_ctx* cc, int* launches) {
   bool oom = false;
   std::vector<Pass> ps = plan_step(c, 1.0, &oom);
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
-  *launches = (int)ps.size();
+  *launches = (int)ps.size() + (c->wm_n > 0 ? 1 : 0);  // + the time advance
   return SBI_OK;
 }
 

@@ -70,6 +70,8 @@ struct RowParams {
   int member0;          // first member of this launch within the group (for convergence flags)
   const int* active;    // per-member flag (nullptr: all active); inactive members skip the pass
   BufRef eta, delta, wgt;        // physical fields (ptr may be null)
+  const void* pg;       // surface pressure / rho along x (nx reals, the same for
+                        // every row), subtracted by ROP_N2; nullptr: none
   BufRef buf[kMaxRowBufs];
   RowOp ops[kMaxRowOps];
   const void* tw;

@@ -59,6 +59,10 @@ EXPORTS = {
     "sbi_vertical_velocity": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sbi_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "sbi_get_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "sbi_set_wavemaker": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.c_double]),
     "sbi_orders_used": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "sbi_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "sbi_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
@@ -276,6 +280,23 @@ class Context:
         m, e = C.c_double(), C.c_double()
         self._check(self.lib.sbi_invariants(self.ctx, member, C.byref(m), C.byref(e)))
         return m.value, e.value
+
+    def set_time(self, t):
+        self._check(self.lib.sbi_set_time(self.ctx, float(t)))
+
+    def get_time(self):
+        t = C.c_double()
+        self._check(self.lib.sbi_get_time(self.ctx, C.byref(t)))
+        return t.value
+
+    def set_wavemaker(self, amp, omega, phase, x0=0.0):
+        """sbi_set_wavemaker; empty sequences remove the wavemaker."""
+        arrs = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (amp, omega, phase)]
+        n = arrs[0].size
+        if any(a.size != n for a in arrs):
+            raise ValueError("amp, omega and phase must have the same length")
+        ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]
+        self._check(self.lib.sbi_set_wavemaker(self.ctx, n, *ptrs, float(x0)))
 
     def orders_used(self, member=0):
         o = C.c_int()

@@ -32,19 +32,27 @@ def rel(a, b):
 
 def problem_of(wl, m):
     g = O.Grid(m.nx, m.ny, m.Lx, m.Ly if m.ny > 1 else 1.0)
+    wm = None
+    if wl.wavemaker:
+        wm = O.Wavemaker(np.array(wl.wavemaker["amp"]), np.array(wl.wavemaker["omega"]),
+                         np.array(wl.wavemaker["phase"]), wl.wavemaker["x0"])
     return O.Problem(g, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
                      sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
-                     filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+                     filt_beta2=wl.filt_beta2, k_ref=wl.k_ref, wavemaker=wm)
 
 
 def context_of(sbi, wl, members, prec, **kw):
     ms = [wl.members[i] for i in members]
     grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in ms]
     depths = [(m.h0 - m.delta) if m.delta is not None else None for m in ms]
-    return sbi.Context(grids, wl.gravity, depths, h0=ms[0].h0, order=wl.order,
-                       alias_frac=wl.alpha, precision=prec, filt_beta1=wl.filt_beta1,
-                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref, sponge_w=wl.sponge_w,
-                       sponge_nu=wl.sponge_nu, **kw)
+    ctx = sbi.Context(grids, wl.gravity, depths, h0=ms[0].h0, order=wl.order,
+                      alias_frac=wl.alpha, precision=prec, filt_beta1=wl.filt_beta1,
+                      filt_beta2=wl.filt_beta2, k_ref=wl.k_ref, sponge_w=wl.sponge_w,
+                      sponge_nu=wl.sponge_nu, **kw)
+    if wl.wavemaker:
+        ctx.set_wavemaker(wl.wavemaker["amp"], wl.wavemaker["omega"], wl.wavemaker["phase"],
+                          wl.wavemaker["x0"])
+    return ctx
 
 
 def test_solitary_wave_run_energy_and_speed(sbi):
@@ -213,4 +221,67 @@ def test_bad_calls_fail_cleanly(sbi):
     assert ei.value.code == sbi.SBI_EINVAL
     with pytest.raises(sbi.SbiError) as ei:
         ctx.step(math.nan, 1)
+    assert ei.value.code == sbi.SBI_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_wavemaker_flume_matches_oracle(sbi, prec, tol):
+    # The flume of the submerged-bar section driven by the pneumatic wavemaker
+    # from rest, started at t0 != 0: the state after 60 steps and after 20 more
+    # (the device time carried across calls) equals the oracle's.
+    wl = W.bar_wavemaker_1d()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    ctx = context_of(sbi, wl, [0], prec)
+    t0 = 0.37
+    ctx.set_time(t0)
+    ctx.set_state(0, m.eta, m.phi)
+    ctx.step(wl.dt, 60)
+    assert abs(ctx.get_time() - (t0 + 60 * wl.dt)) < 1e-12
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, m.eta, m.phi, wl.dt, 60, t0=t0)
+    assert np.max(np.abs(eo)) > 1e-3          # waves have been generated
+    assert rel(e, eo) < tol and rel(p, po) < tol
+    ctx.step(wl.dt, 20)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eo, po, wl.dt, 20, t0=t0 + 60 * wl.dt)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_wavemaker_line_source_2d(sbi, prec, tol):
+    # Two components, off-centre bell, a 2-D variable-depth member in motion.
+    nx, ny, Lx, Ly, h0 = 64, 32, 8.0, 4.0, 0.6
+    grid = O.Grid(nx, ny, Lx, Ly)
+    delta = W.random_field(nx, ny, 101, amplitude=0.04)
+    amp, omega, phase, x0 = [0.004, 0.002], [3.0, 5.5], [0.2, 1.1], 1.3
+    wm = O.Wavemaker(np.array(amp), np.array(omega), np.array(phase), x0)
+    pb = O.Problem(grid, 9.81, h0, delta=delta, wavemaker=wm)
+    eta = O.project(pb, W.random_field(nx, ny, 102, amplitude=0.02))
+    phi = O.project(pb, W.random_field(nx, ny, 103, amplitude=0.1))
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec)
+    ctx.set_wavemaker(amp, omega, phase, x0)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.02, 6)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.02, 6)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+    # removing the wavemaker restores the free evolution
+    ctx.set_wavemaker([], [], [])
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.02, 2)
+    pb0 = O.Problem(grid, 9.81, h0, delta=delta)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb0, eta, phi, 0.02, 2)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+def test_wavemaker_bad_calls(sbi):
+    ctx = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0)
+    for args in (([0.01], [-1.0], [0.0]), ([math.nan], [2.0], [0.0]), ([0.01], [2.0], [math.inf])):
+        with pytest.raises(sbi.SbiError) as ei:
+            ctx.set_wavemaker(*args)
+        assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.set_time(math.nan)
     assert ei.value.code == sbi.SBI_EINVAL

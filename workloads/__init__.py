@@ -137,6 +137,8 @@ class Workload:
     k_ref: float = 1.0
     sponge_w: np.ndarray | None = None      # same grid as every member
     sponge_nu: float = 0.0
+    # pneumatic wavemaker: {"amp": [...], "omega": [...], "phase": [...], "x0": float}
+    wavemaker: dict | None = None
     notes: dict = field(default_factory=dict)
 
     @property
@@ -190,16 +192,25 @@ def solitary_1d(n: int = 256, L: float = 100.0, h: float = 1.0, a: float = 0.3,
 # 2. Submerged trapezoidal bar
 # --------------------------------------------------------------------------
 
-def bar_depth(x: np.ndarray, h0: float = 0.4) -> np.ndarray:
-    """Still-water depth h(x) of the trapezoidal bar (toe at 30 m)."""
+def bar_depth(x: np.ndarray, h0: float = 0.4, toe: float = 30.0) -> np.ndarray:
+    """Still-water depth h(x) of the trapezoidal bar: 1:20 up from the toe to a
+    0.1 m deep, 2 m long crest, then 1:10 down."""
     h = np.full_like(x, h0)
-    up = (x >= 30.0) & (x < 36.0)
-    h[up] = h0 - (x[up] - 30.0) / 20.0
-    top = (x >= 36.0) & (x < 38.0)
+    up = (x >= toe) & (x < toe + 6.0)
+    h[up] = h0 - (x[up] - toe) / 20.0
+    top = (x >= toe + 6.0) & (x < toe + 8.0)
     h[top] = 0.1
-    down = (x >= 38.0) & (x < 41.0)
-    h[down] = 0.1 + (x[down] - 38.0) / 10.0
+    down = (x >= toe + 8.0) & (x < toe + 11.0)
+    h[down] = 0.1 + (x[down] - (toe + 8.0)) / 10.0
     return h
+
+
+def gaussian_damping(x: np.ndarray, x0: float, k: float, L: float) -> np.ndarray:
+    """Weight of the damping pressure in the submerged-bar section: a Gaussian
+    exp(-(k (x - x0) / (4 pi))^2) centred at x0 (periodic distance), the
+    printed form being in units of 1/k_p."""
+    d = np.mod(x - x0 + 0.5 * L, L) - 0.5 * L
+    return np.exp(-(k * d / (4.0 * np.pi)) ** 2)
 
 
 def bar_1d(n: int = 4096, L: float = 80.0, h0: float = 0.4, a: float = 0.01,
@@ -220,6 +231,25 @@ def bar_1d(n: int = 4096, L: float = 80.0, h0: float = 0.4, a: float = 0.01,
                delta.reshape(1, n))
     return Workload("bar_1d", g, 0.005, 8000, [m], sponge_w=w.reshape(1, n),
                     sponge_nu=omega, notes={"k0": k0, "omega": omega})
+
+
+def bar_wavemaker_1d(n: int = 1024, L: float = 64.0, h0: float = 0.4, a: float = 0.01,
+                     T: float = 2.02, toe: float = 10.0, g: float = G) -> Workload:
+    """Numerical flume of the submerged-bar section: 64 m on 1024 points, still
+    depth 0.4 m, the bar with its toe at 10 m, waves of period T and amplitude
+    a from the pneumatic wavemaker split at both ends of the box (x0 = 0), the
+    Gaussian damping pressure centred at 7/8 L with strength omega.  Starts
+    from rest; dt = T/40."""
+    x = np.arange(n) * (L / n)
+    delta = h0 - bar_depth(x, h0, toe)
+    omega = 2.0 * np.pi / T
+    k0 = dispersion_k(omega, h0, g)
+    w = gaussian_damping(x, 7.0 / 8.0 * L, k0, L)
+    m = Member(n, 1, L, 1.0, h0, np.zeros((1, n)), np.zeros((1, n)), delta.reshape(1, n))
+    return Workload("bar_wavemaker_1d", g, T / 40.0, 4000, [m], sponge_w=w.reshape(1, n),
+                    sponge_nu=omega,
+                    wavemaker={"amp": [a], "omega": [omega], "phase": [0.0], "x0": 0.0},
+                    notes={"k0": k0, "omega": omega})
 
 
 # --------------------------------------------------------------------------
