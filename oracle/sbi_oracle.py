@@ -66,6 +66,16 @@ R10 Pneumatic wavemaker (Eq. for p_g, submerged-bar section): the printed
     source).  It enters the dynamic condition like p_d: phi~_t gets -p_g/rho,
     inside the dealiasing of that right-hand side.  With this scaling linear
     theory gives radiated waves of amplitude a_j on each side.
+R11 Integrating factor (Sec. 2.2, the reformulation of Eq. (prognostic) with
+    e^{-A(t-t0)}): A is the linearisation of the system about rest in
+    spectral space, d/dt (eta^, phi^) = [[0, k tanh(k h0)], [-g, 0]] (eta^, phi^)
+    on the dealiased modes (the first order of Sec. 2.4 and the -g eta of the
+    dynamic condition); everything else is the nonlinear part N: eta_t - V_1
+    and phi~_t + g eta.  e^{A tau} = [[cos w tau, (k t / w) sin w tau],
+    [-(g / w) sin w tau, cos w tau]] with w^2 = g k t (t = tanh k h0), and at
+    k = 0 [[1, 0], [-g tau, 1]].  The paper integrates the transformed system
+    with an adaptive embedded RK5(4); this oracle provides the integrating
+    factor with classical RK4 stages and a fixed step (the Lawson scheme).
 
 Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
 has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
@@ -344,6 +354,7 @@ class Problem:
     k_ref: float = 1.0
     adapt_tol: float = 0.0      # R9: 0 = fixed order
     wavemaker: "Wavemaker | None" = None   # R10
+    integrator: str = "rk4"                 # "rk4" (classical) or "lawson" (R11)
 
 
 def surface_rhs(pb: Problem, eta, phi, t: float = 0.0):
@@ -367,6 +378,65 @@ def project(pb: Problem, f):
     return ifft(m * fft(np.asarray(f, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)))
 
 
+def linear_propagator(pb: "Problem", tau: float):
+    """R11: entries (cos w tau, (k t / w) sin w tau, (g / w) sin w tau) of
+    e^{A tau} on the full FFT grid."""
+    KX, KY, K = wavenumbers(pb.grid)
+    t, _ = depth_multipliers(K, pb.h0)
+    w = np.sqrt(pb.gravity * K * t)
+    C = np.cos(w * tau)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Sk = np.where(K > 0, K * t * np.sin(w * tau) / np.where(w > 0, w, 1.0), 0.0)
+        Sg = np.where(K > 0, pb.gravity * np.sin(w * tau) / np.where(w > 0, w, 1.0), pb.gravity * tau)
+    return C, Sk, Sg
+
+
+def nonlinear_part(pb: "Problem", eta, phi, t: float):
+    """R11: N = (eta_t - V_1, phi~_t + g eta) in physical space, with V_1 the
+    first order of Sec. 2.4 and eta dealiased as in the dynamic condition."""
+    KX, KY, K = wavenumbers(pb.grid)
+    mask = dealias_mask(pb.grid, pb.alpha)
+    tk, _ = depth_multipliers(K, pb.h0)
+    V, phi_t = surface_rhs(pb, eta, phi, t)
+    V1 = ifft(mask * K * tk * fft(phi))
+    return V - V1, phi_t + pb.gravity * ifft(mask * fft(eta))
+
+
+def lawson_rk4_step(pb: "Problem", eta, phi, dt: float, t: float = 0.0):
+    """One step of the integrating-factor scheme (R11) with classical RK4
+    stages (Lawson): with E(tau) = e^{A tau} and h = dt,
+      k1 = N(u_n),  u2 = E(h/2)(u_n + h/2 k1),  k2 = N(u2),
+      u3 = E(h/2) u_n + h/2 k2,  k3 = N(u3),  u4 = E(h) u_n + h E(h/2) k3,
+      k4 = N(u4),  u_{n+1} = E(h) u_n + h/6 (E(h) k1 + 2 E(h/2)(k2 + k3) + k4),
+    the stages evaluated at t, t + h/2, t + h/2, t + h."""
+    half, full = linear_propagator(pb, 0.5 * dt), linear_propagator(pb, dt)
+
+    def E(P, a, b):
+        C, Sk, Sg = P
+        return C * a + Sk * b, -Sg * a + C * b
+
+    def N(a, b, tt):
+        ne, nph = nonlinear_part(pb, ifft(a), ifft(b), tt)
+        return fft(ne), fft(nph)
+
+    u = (fft(np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)),
+         fft(np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)))
+    k1 = N(*u, t)
+    u2 = E(half, u[0] + 0.5 * dt * k1[0], u[1] + 0.5 * dt * k1[1])
+    k2 = N(*u2, t + 0.5 * dt)
+    Eu_half = E(half, *u)
+    u3 = (Eu_half[0] + 0.5 * dt * k2[0], Eu_half[1] + 0.5 * dt * k2[1])
+    k3 = N(*u3, t + 0.5 * dt)
+    Eu_full = E(full, *u)
+    Ek3 = E(half, *k3)
+    u4 = (Eu_full[0] + dt * Ek3[0], Eu_full[1] + dt * Ek3[1])
+    k4 = N(*u4, t + dt)
+    Ek1 = E(full, *k1)
+    Ek23 = E(half, k2[0] + k3[0], k2[1] + k3[1])
+    new = tuple(Eu_full[i] + dt / 6.0 * (Ek1[i] + 2.0 * Ek23[i] + k4[i]) for i in range(2))
+    return ifft(new[0]), ifft(new[1])
+
+
 def rk4_step(f, y, dt, t=0.0):
     """Classical RK4 for y' = f(t, y) from time t; y is a tuple of arrays."""
     def axpy(a, x, b):
@@ -385,7 +455,10 @@ def step(pb: Problem, eta, phi, dt: float, n: int = 1, t0: float = 0.0):
     y = (np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx),
          np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx))
     for i in range(n):
-        y = rk4_step(lambda t, s: surface_rhs(pb, s[0], s[1], t), y, dt, t0 + i * dt)
+        if pb.integrator == "lawson":
+            y = lawson_rk4_step(pb, y[0], y[1], dt, t0 + i * dt)
+        else:
+            y = rk4_step(lambda t, s: surface_rhs(pb, s[0], s[1], t), y, dt, t0 + i * dt)
         y = (project(pb, y[0]), project(pb, y[1]))
     return y
 

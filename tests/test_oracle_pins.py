@@ -412,3 +412,47 @@ def test_wavemaker_pressure_shape():
     k3 = 16.0 / g
     assert abs(p3[i0] - g * 0.01 * math.sqrt(math.e / (2 * math.pi)) * math.sin(4.0 * t + 0.3)) < 1e-12
     assert abs(p3[i0 + 3] / p3[i0] - math.exp(-0.5 * (k3 * 3 * 20.0 / 256) ** 2)) < 1e-12
+
+
+@pytest.mark.parametrize("h0", [0.4, math.inf])
+def test_lawson_step_is_exact_for_linear_waves(h0):
+    # R11: the integrating factor carries the linear part exactly, so for an
+    # infinitesimal travelling wave one step of any length gives
+    # eta = a cos(kx - w dt), phi~ = (g a / w) sin(kx - w dt) with
+    # w^2 = g k tanh(k h0), here at w dt = 2.5 where classical RK4 is unstable.
+    g, a, nx, L, m = 9.81, 1e-8, 64, 4.0, 3
+    grid = O.Grid(nx, 1, L)
+    k = 2 * math.pi * m / L
+    w = math.sqrt(g * k * (math.tanh(k * h0) if math.isfinite(h0) else 1.0))
+    x = np.arange(nx) * L / nx
+    eta = a * np.cos(k * x)[None, :]
+    phi = (g * a / w) * np.sin(k * x)[None, :]
+    dt = 2.5 / w
+    pb = O.Problem(grid, g, h0, order=1, integrator="lawson")
+    e, p = O.step(pb, eta, phi, dt, 1)
+    assert np.max(np.abs(e[0] - a * np.cos(k * x - w * dt))) < 1e-6 * a
+    assert np.max(np.abs(p[0] - (g * a / w) * np.sin(k * x - w * dt))) < 1e-6 * g * a / w
+    pb_rk = O.Problem(grid, g, h0, order=1)
+    e_rk, _ = O.step(pb_rk, eta, phi, dt, 1)
+    assert np.max(np.abs(e_rk[0] - a * np.cos(k * x - w * dt))) > 0.1 * a
+
+
+def test_lawson_is_fourth_order_and_agrees_with_rk4():
+    # R11: on a nonlinear variable-depth problem the Lawson scheme converges
+    # at fourth order (a wrong stage weight or propagator would lower it) to
+    # the solution of classical RK4 at a tiny step.
+    nx, ny, Lx, Ly, h0 = 32, 16, 6.0, 3.0, 0.7
+    grid = O.Grid(nx, ny, Lx, Ly)
+    delta = W.random_field(nx, ny, 111, amplitude=0.05, band=0.3)
+    pb = O.Problem(grid, 9.81, h0, delta=delta, order=4, integrator="lawson")
+    eta = O.project(pb, W.random_field(nx, ny, 112, amplitude=0.04, band=0.3))
+    phi = O.project(pb, W.random_field(nx, ny, 113, amplitude=0.1, band=0.3))
+    T_end = 0.4
+    ref_pb = O.Problem(grid, 9.81, h0, delta=delta, order=4)
+    e_ref, p_ref = O.step(ref_pb, eta, phi, T_end / 128, 128)
+    errs = []
+    for n in (4, 8, 16):
+        e, p = O.step(pb, eta, phi, T_end / n, n)
+        errs.append(np.linalg.norm(e - e_ref) + np.linalg.norm(p - p_ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, (errs, r1, r2)
