@@ -40,6 +40,8 @@ def parse():
                     choices=["crossing_batch", "large_variable", "bar_1d", "stokes_2d",
                              "bar_wavemaker_1d", "solitary_1d"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--integrator", default="rk4", choices=["rk4", "lawson"],
+                    help="classical RK4 or the integrating factor with RK4 stages")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -236,7 +238,7 @@ def time_steps(ctx, torch, stream, dt, steps, warmup):
     return ev0.elapsed_time(ev1) / 1000.0
 
 
-def cpu_oracle_sample(wl, target_s=10.0):
+def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4"):
     """Time the FP64 oracle on a bounded sample: whole RK4 steps of members
     drawn in workload order, until about target_s seconds of CPU work."""
     from oracle import sbi_oracle as O
@@ -261,6 +263,7 @@ def cpu_oracle_sample(wl, target_s=10.0):
                            np.array(wl.wavemaker["amp"]), np.array(wl.wavemaker["omega"]),
                            np.array(wl.wavemaker["phase"]), wl.wavemaker["x0"]))
         t0 = time.perf_counter()
+        pb.integrator = integrator
         O.step(pb, m.eta, m.phi, wl.dt, 1)
         t_tot += time.perf_counter() - t0
         pts += m.nx * m.ny
@@ -280,7 +283,7 @@ def run_reference(args):
     total_t, total_pts = 0.0, 0
     samples = []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(wl, target_s=2.0)
+        r = cpu_oracle_sample(wl, target_s=2.0, integrator=args.integrator)
         if k >= args.warmup:
             pts_s = r["value"]
             samples.append(pts_s)
@@ -319,7 +322,8 @@ def main():
     wl = make_workload(args.workload, args.members, rank)
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
-    ctx = make_context(sbi, wl, prec, stream.cuda_stream)
+    integ = sbi.SBI_LAWSON_RK4 if args.integrator == "lawson" else sbi.SBI_RK4
+    ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ)
     for i, m in enumerate(wl.members):
         ctx.set_state(i, m.eta, m.phi)
     launches = ctx.step_launches()
@@ -385,10 +389,10 @@ def main():
     err = None
     fp64_arm = None
     if not args.no_fp64_arm and prec == sbi.SBI_FP32:
-        ctx64 = make_context(sbi, wl, sbi.SBI_FP64, stream.cuda_stream)
+        ctx64 = make_context(sbi, wl, sbi.SBI_FP64, stream.cuda_stream, integrator=integ)
         for i, m in enumerate(wl.members):
             ctx64.set_state(i, m.eta, m.phi)
-        ctx_err = make_context(sbi, wl, sbi.SBI_FP32, stream.cuda_stream)
+        ctx_err = make_context(sbi, wl, sbi.SBI_FP32, stream.cuda_stream, integrator=integ)
         ctx_err.set_state(0, wl.members[0].eta, wl.members[0].phi)
         ctx64_0 = ctx64
         V32 = ctx_err.vertical_velocity(0)
@@ -405,7 +409,8 @@ def main():
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if not args.no_e2e:
-        ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0)
+        ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0,
+                             integrator=integ)
         # every member's eta and phi~, concatenated in member order, in pinned memory
         eta_h = torch.from_numpy(np.concatenate([np.ravel(m.eta) for m in wl.members])).pin_memory()
         phi_h = torch.from_numpy(np.concatenate([np.ravel(m.phi) for m in wl.members])).pin_memory()
@@ -433,10 +438,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(wl, target_s=10.0)
+        cpu = cpu_oracle_sample(wl, target_s=10.0, integrator=args.integrator)
 
     cfg = workload_config(wl)
     cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
+    cfg["integrator"] = "lawson (integrating factor, RK4 stages)" if args.integrator == "lawson" else "classical RK4"
     cfg["autotune"] = autotune_summary(ctx.autotune_report())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,

@@ -54,6 +54,9 @@ extern "C" {
 #define SBI_FP32 0             /* FFTs, multipliers, products in FP32; FP64 state, RK4 sums, invariants */
 #define SBI_FP64 1             /* everything in FP64 (the plain path) */
 
+#define SBI_RK4 0              /* classical RK4 on (eta, phi~) */
+#define SBI_LAWSON_RK4 1       /* integrating factor (Sec. 2.2) with RK4 stages (Lawson) */
+
 typedef struct sbi_ctx sbi_ctx;   /* opaque */
 
 typedef struct {
@@ -89,6 +92,13 @@ typedef struct {
                             shapes change only how the work is split into blocks, never the
                             arithmetic, so results are identical with any choice.  0: use
                             the largest shape that fits (no timing runs). */
+    int    integrator;   /* SBI_RK4 (default): classical RK4 with a fixed step.
+                            SBI_LAWSON_RK4: the integrating factor of Sec. 2.2, e^{-A(t-t0)}
+                            with A the linearisation d/dt (eta^, phi^) = [[0, k tanh(k h0)],
+                            [-g, 0]] (eta^, phi^), applied exactly per mode, and classical RK4
+                            stages for the nonlinear part (Lawson's scheme); the paper uses an
+                            adaptive embedded RK5(4) for that part.  Not combined with
+                            adapt_tol > 0. */
 } sbi_options;
 
 /* Fill *opt with the defaults listed above. */

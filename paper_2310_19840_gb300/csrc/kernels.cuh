@@ -484,7 +484,8 @@ k_rk(const __grid_constant__ RkParams p) {
     c2r_input<T, NX>(x, fb, p.W, j, tw);
     row_group_sync<NX>();
     fft_block<n, R, -1>(x, fb, j, tw);
-    if (p.mode == RK_CORRECT) {
+    if (p.mode == RK_CORRECT || p.mode == RK_OFFSET) {
+      const bool keep = p.mode == RK_CORRECT;   // RK_OFFSET leaves the state unchanged
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
@@ -492,8 +493,8 @@ k_rk(const __grid_constant__ RkParams p) {
         SP e = act ? SP::load(E0, m) : SP::zero();
         e.add(0, c.x);
         e.add(1, c.y);
-        if (act) e.store(E0, m);
-        bad |= !e.finite();
+        if (act && keep) e.store(E0, m);
+        bad |= keep && !e.finite();
         xe[r] = mk<V>(T(e.value(0)), T(e.value(1)));
       }
       __syncthreads();
@@ -509,8 +510,8 @@ k_rk(const __grid_constant__ RkParams p) {
         SP q = act ? SP::load(P0, m) : SP::zero();
         q.add(0, c.x);
         q.add(1, c.y);
-        if (act) q.store(P0, m);
-        bad |= !q.finite();
+        if (act && keep) q.store(P0, m);
+        bad |= keep && !q.finite();
         xp[r] = mk<V>(T(q.value(0)), T(q.value(1)));
       }
     } else {
@@ -742,7 +743,16 @@ __global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
   for (int i = 0; i < ap; ++i) kp *= k;
   if (s.kpow < 0) kp = k > 0.0 ? 1.0 / kp : 0.0;
   double f = s.c * kp;
-  const double d = s.depth == 1 ? tk : (s.depth == 2 ? sk : (s.depth == 3 ? lam : 1.0));
+  double d = s.depth == 1 ? tk : (s.depth == 2 ? sk : (s.depth == 3 ? lam : 1.0));
+  if (s.depth >= 4) {
+    // entries of e^{A tau}; cos - 1 as -2 sin^2(w tau / 2) (no cancellation)
+    const double w = sqrt(s.gravity * k * tk);
+    const double wt = w * s.tau, sh = sin(0.5 * wt);
+    if (s.depth == 4) d = -2.0 * sh * sh;
+    else if (s.depth == 5) d = k > 0.0 ? k * tk * sin(wt) / w : 0.0;
+    else if (s.depth == 6) d = k > 0.0 ? s.gravity * sin(wt) / w : s.gravity * s.tau;
+    else d = cos(wt);
+  }
   for (int i = 0; i < s.gx; ++i) f *= kxv;
   for (int i = 0; i < s.gy; ++i) f *= kyv;
   const bool keep = kx < s.kx_keep && (ns < 0 ? -ns : ns) < s.ky_keep;

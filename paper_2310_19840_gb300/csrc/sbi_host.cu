@@ -215,6 +215,12 @@ struct Planner {
   sbi_ctx* c;
   Group& g;
   bool oom = false;      // an allocation failed (or a descriptor would overflow)
+  // stage of an integrating-factor step (1..4; 0 otherwise): the diagnostic
+  // then reads the stage state from st_eta / st_phi and its last order writes
+  // the nonlinear part V - V_1 under a per-stage name; the dynamic condition
+  // drops -g eta
+  int if_stage = 0;
+  std::string st_eta = "eta_m", st_phi = "phi_m";
 
   size_t vsize() const { return 2 * c->real_size; }
 
@@ -299,7 +305,7 @@ struct Planner {
     op.kind = ROP_N2;
     op.slot = (uint8_t)slot0;
     op.a = g.two_d ? 2 : 1;
-    op.coef = c->gravity;
+    op.coef = if_stage > 0 ? 0.0 : c->gravity;   // the nonlinear part has no -g eta
     op.dst = (uint8_t)add_buf(r, mref(dst));
     r.bytes += mixed_bytes();
     if (room(r)) r.p.ops[r.p.nops++] = op;
@@ -363,7 +369,8 @@ struct Planner {
   // Device table of a multiplier (created once per group and key).
   const void* table(const ColTerm& t) {
     char key[160];
-    snprintf(key, sizeof(key), "%.17g|%d|%d|%d|%d|%d", t.c, t.kpow, t.depth, t.gx, t.gy, t.mask);
+    snprintf(key, sizeof(key), "%.17g|%d|%d|%d|%d|%d|%.17g", t.c, t.kpow, t.depth, t.gx, t.gy, t.mask,
+             t.depth >= 4 ? t.tau : 0.0);
     auto it = g.tables.find(key);
     if (it != g.tables.end()) return it->second;
     void* p = dalloc(c, (size_t)g.W * g.ny * c->real_size);
@@ -382,6 +389,8 @@ struct Planner {
     s.filt_kf = c->filter_on() ? c->opt.filt_beta1 * c->opt.k_ref : 0.0;
     s.filt_beta2 = c->opt.filt_beta2;
     s.c = t.c;
+    s.tau = t.tau;
+    s.gravity = c->gravity;
     s.kpow = t.kpow;
     s.depth = t.depth;
     s.gx = t.gx;
@@ -467,8 +476,8 @@ struct Planner {
   // Col A: order 1 (Sec. 2.4) and the gradients of phi~ and eta.
   Pass plan_col_a() {
     const bool var = g.variable;
-    std::vector<ColIn> ins = {{"phi_m", {term(0, 1.0, 0, 0, 0, 0)}},
-                              {"eta_m", {term(1, 1.0, 0, 0, 0, 0)}}};
+    std::vector<ColIn> ins = {{st_phi, {term(0, 1.0, 0, 0, 0, 0)}},
+                              {st_eta, {term(1, 1.0, 0, 0, 0, 0)}}};
     std::vector<std::pair<std::string, ColTerm>> outs;
     outs.push_back({"V1", term(0, 1.0, 1, 1, 0, 0, 1)});  // k tanh(kh) phi^
     for (char d : dims()) {
@@ -557,20 +566,23 @@ struct Planner {
     // the last order is written as the sum V^_1 + ... + V^_M (mixed), the only
     // form in which it is used
     const bool last = l == M;
-    outs.push_back({last ? std::string("Vsum") : S("V%d", l), term(0, 1.0, 0, 0, 0, 0, 1)});
+    outs.push_back({last ? (if_stage > 0 ? S("Vnl%d", if_stage) : std::string("Vsum")) : S("V%d", l),
+                    term(0, 1.0, 0, 0, 0, 0, 1)});
     if (phi_out) {
       for (char d : dims())
         outs.push_back({S("db%d", l) + d, term(1, 1.0, 0, 0, d == 'x', d == 'y', 1)});
     }
     std::vector<std::string> pass;
-    if (last)
-      for (int q = 1; q < M; ++q) pass.push_back(S("V%d", q));
+    if (last)   // the integrating-factor stages leave out V_1 (the linear part)
+      for (int q = if_stage > 0 ? 2 : 1; q < M; ++q) pass.push_back(S("V%d", q));
     return col(ins, outs, phi_out ? 2 : 1, pass);
   }
 
   // mixed buffers whose sum is F_x{V}
   std::vector<std::string> v_names() const {
-    return {c->opt.order == 1 ? std::string("V1") : std::string("Vsum")};
+    if (c->opt.order == 1) return {std::string("V1")};
+    if (if_stage > 0) return {S("Vnl%d", if_stage), std::string("V1")};
+    return {std::string("Vsum")};
   }
 
   Pass plan_conv(int phase, int l) {
@@ -653,10 +665,14 @@ struct Planner {
         ins.push_back({std::string("SP") + d,
                        {term(0, c->opt.sponge_nu, -2, 0, d == 'x', d == 'y')}});
     }
-    out.push_back(col(ins, {{"phit", term(0, 1.0, 0, 0, 0, 0, 1)}}, 1));
+    out.push_back(col(ins, {{if_stage > 0 ? S("phit%d", if_stage) : std::string("phit"),
+                             term(0, 1.0, 0, 0, 0, 0, 1)}}, 1));
   }
 
-  Pass plan_rk(int mode, int stage, double dt, int tail) {
+  // cor_eta / cor_phi: the mixed corrections of RK_CORRECT / RK_OFFSET;
+  // w_eta / w_phi: where the tail writes the mixed working copies
+  Pass plan_rk(int mode, int stage, double dt, int tail, const char* cor_eta = "Ce",
+               const char* cor_phi = "Cp", const char* w_eta = "eta_m", const char* w_phi = "phi_m") {
     RkParams p;
     std::memset(&p, 0, sizeof(p));
     p.mode = mode;
@@ -672,16 +688,17 @@ struct Planner {
     p.acc_eta = dref(g.acc_eta);
     p.acc_phi = dref(g.acc_phi);
     p.V = pref(g.Vphys);
-    p.phit = mref(mode == RK_CORRECT ? "Ce" : "phit");
-    p.corr_phi = mref("Cp");
+    const bool corr = mode == RK_CORRECT || mode == RK_OFFSET;
+    p.phit = mref(corr ? cor_eta : "phit");
+    p.corr_phi = mref(cor_phi);
     p.eta_w = pref(g.eta_w);
-    p.eta_hat = mref("eta_m");
-    p.phi_hat = mref("phi_m");
+    p.eta_hat = mref(w_eta);
+    p.phi_hat = mref(w_phi);
     p.nonfinite = c->d_flags;
     p.tw = c->tw;
     // transforms along x: the stage's phi~_t (STAGE) or the two corrections
     // (CORRECT) back to physical space, and the working copies forward (tail)
-    const int nxf = (mode == RK_STAGE ? 1 : (mode == RK_CORRECT ? 2 : 0)) + (tail ? 2 : 0);
+    const int nxf = (mode == RK_STAGE ? 1 : (corr ? 2 : 0)) + (tail ? 2 : 0);
     const double xforms = (double)nxf * g.phys_elems() * g.n;
     double b = phys64_bytes() * 2;  // read master
     if (mode == RK_STAGE) {
@@ -690,6 +707,8 @@ struct Planner {
       if (stage == 4) b += phys64_bytes() * 2;                 // write master
     } else if (mode == RK_CORRECT) {
       b += mixed_bytes() * 2 + phys64_bytes() * 2;
+    } else if (mode == RK_OFFSET) {
+      b += mixed_bytes() * 2;
     }
     if (tail) b += phys_bytes() + 2 * mixed_bytes();
     Pass ps{};
@@ -709,6 +728,75 @@ struct Planner {
                       {{"Ce", term(0, 1.0, 0, depth, 0, 0, 2)}, {"Cp", term(1, 1.0, 0, depth, 0, 0, 2)}},
                       2));
     out.push_back(plan_rk(RK_CORRECT, 0, 0.0, 1));
+  }
+
+  // Integrating-factor (Lawson) combination after the right-hand side of stage
+  // s: with E(tau) = e^{A tau} (propagator tables), u_n = (eta_m, phi_m) and
+  // k_s = (Vnl<s>, phit<s>), the mixed offsets (De, Dp) from u_n of
+  //   s = 1: (E(h/2) - I) u_n + h/2 E(h/2) k1          (stage 2 state)
+  //   s = 2: (E(h/2) - I) u_n + h/2 k2                 (stage 3 state)
+  //   s = 3: (E(h) - I) u_n + h E(h/2) k3              (stage 4 state)
+  //   s = 4: (E(h) - I) u_n + h/6 (E(h) k1 + 2 E(h/2)(k2 + k3) + k4)   (u_{n+1})
+  // u_n's working spectra come from a row transform (unnormalised in x, like
+  // every column-pass input) while the k_s are column-pass outputs, normalised
+  // for the inverse row transform: their coefficients carry the factor nx.
+  Pass plan_if_combine(int s, double h) {
+    std::map<std::string, std::vector<ColTerm>> terms;
+    std::vector<std::string> order;
+    auto add = [&](const std::string& name, ColTerm t) {
+      if (!terms.count(name)) order.push_back(name);
+      terms[name].push_back(t);
+    };
+    auto prop = [&](int acc, double cc, int depth, double tau) {
+      ColTerm t = term(acc, cc, 0, depth, 0, 0);
+      t.tau = tau;
+      return t;
+    };
+    // (E(tau) - I) applied to the state's pair (a, b)
+    auto apply_E_minus_I = [&](const std::string& a, const std::string& b, double tau) {
+      add(a, prop(0, 1.0, 4, tau));
+      add(a, prop(1, -1.0, 6, tau));
+      add(b, prop(0, 1.0, 5, tau));
+      add(b, prop(1, 1.0, 4, tau));
+    };
+    const bool has_vnl = c->opt.order > 1;   // order 1: V - V_1 = 0
+    const double nrm = (double)g.nx;
+    // cc E(tau) k_q (prop_it) or cc k_q
+    auto k_pair = [&](int q, double cc, double tau, bool prop_it) {
+      const std::string ke = S("Vnl%d", q), kp = S("phit%d", q);
+      cc *= nrm;
+      if (prop_it) {
+        if (has_vnl) {
+          add(ke, prop(0, cc, 7, tau));
+          add(ke, prop(1, -cc, 6, tau));
+        }
+        add(kp, prop(0, cc, 5, tau));
+        add(kp, prop(1, cc, 7, tau));
+      } else {
+        if (has_vnl) add(ke, term(0, cc, 0, 0, 0, 0));
+        add(kp, term(1, cc, 0, 0, 0, 0));
+      }
+    };
+    const double half = 0.5 * h;
+    if (s == 1) {
+      apply_E_minus_I("eta_m", "phi_m", half);
+      k_pair(1, half, half, true);
+    } else if (s == 2) {
+      apply_E_minus_I("eta_m", "phi_m", half);
+      k_pair(2, half, 0.0, false);
+    } else if (s == 3) {
+      apply_E_minus_I("eta_m", "phi_m", h);
+      k_pair(3, h, half, true);
+    } else {
+      apply_E_minus_I("eta_m", "phi_m", h);
+      k_pair(1, h / 6.0, h, true);
+      k_pair(2, h / 3.0, half, true);
+      k_pair(3, h / 3.0, half, true);
+      k_pair(4, h / 6.0, 0.0, false);
+    }
+    std::vector<ColIn> ins;
+    for (const auto& name : order) ins.push_back({name, terms[name]});
+    return col(ins, {{"De", term(0, 1.0, 0, 0, 0, 0, 1)}, {"Dp", term(1, 1.0, 0, 0, 0, 0, 1)}}, 2);
   }
 
   void plan_sum_v(std::vector<Pass>& out, bool eulerian) {
@@ -1011,9 +1099,27 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
     std::vector<Pass> all;
     Planner pl{c, g};
     for (int s = 1; s <= 4; ++s) {
-      pl.plan_diag(all);
-      pl.plan_rhs(all, (s == 1 ? 0.0 : (s == 4 ? 1.0 : 0.5)) * dt);  // stage times
-      all.push_back(pl.plan_rk(RK_STAGE, s, dt, (s < 4 || !c->filter_on()) ? 1 : 0));
+      const double t_off = (s == 1 ? 0.0 : (s == 4 ? 1.0 : 0.5)) * dt;  // stage times
+      const int tail = (s < 4 || !c->filter_on()) ? 1 : 0;
+      if (c->opt.integrator == SBI_LAWSON_RK4) {
+        // integrating factor: stage 1 is u_n (eta_m, phi_m), the later stages'
+        // working copies live in (eta_s, phi_s)
+        pl.if_stage = s;
+        pl.st_eta = s == 1 ? "eta_m" : "eta_s";
+        pl.st_phi = s == 1 ? "phi_m" : "phi_s";
+        pl.plan_diag(all);
+        pl.plan_rhs(all, t_off);
+        all.push_back(pl.plan_if_combine(s, dt));
+        if (s < 4) all.push_back(pl.plan_rk(RK_OFFSET, s, dt, 1, "De", "Dp", "eta_s", "phi_s"));
+        else all.push_back(pl.plan_rk(RK_CORRECT, s, dt, tail, "De", "Dp"));
+        pl.if_stage = 0;
+        pl.st_eta = "eta_m";
+        pl.st_phi = "phi_m";
+      } else {
+        pl.plan_diag(all);
+        pl.plan_rhs(all, t_off);
+        all.push_back(pl.plan_rk(RK_STAGE, s, dt, tail));
+      }
     }
     if (c->filter_on()) pl.plan_project(all, true);
     if (pl.oom) *oom = true;
@@ -1269,6 +1375,10 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
   if (opt.filt_beta1 > 0.0 && !(opt.k_ref > 0.0 && opt.filt_beta2 > 0.0))
     return fail(nullptr, SBI_EINVAL, "filter needs k_ref > 0 and beta2 > 0");
   if (opt.adapt_tol < 0.0) return fail(nullptr, SBI_EINVAL, "adapt_tol must be >= 0");
+  if (opt.integrator != SBI_RK4 && opt.integrator != SBI_LAWSON_RK4)
+    return fail(nullptr, SBI_EINVAL, "integrator must be SBI_RK4 or SBI_LAWSON_RK4");
+  if (opt.integrator == SBI_LAWSON_RK4 && opt.adapt_tol > 0.0)
+    return fail(nullptr, SBI_EINVAL, "the integrating factor (integrator) is not combined with adapt_tol > 0");
   if ((opt.dev_alloc == nullptr) != (opt.dev_free == nullptr))
     return fail(nullptr, SBI_EINVAL, "dev_alloc and dev_free must be given together");
   for (int i = 0; i < n; ++i) {

@@ -87,10 +87,14 @@ struct ColTerm {
   uint8_t acc;    // accumulator index
   uint8_t gx, gy; // powers of (i kx), (i ky)
   int8_t kpow;    // power of |k| (negative powers vanish at k = 0)
-  uint8_t depth;  // 0: 1, 1: tanh(k h0), 2: sech(k h0), 3: Lambda(k) = exp(-(k/kf)^beta2)
+  uint8_t depth;  // 0: 1, 1: tanh(k h0), 2: sech(k h0), 3: Lambda(k) = exp(-(k/kf)^beta2);
+                  // entries of the linear propagator e^{A tau}, w^2 = g k tanh(k h0):
+                  // 4: cos(w tau) - 1, 5: (k tanh(k h0) / w) sin(w tau), 6: (g / w) sin(w tau)
+                  // (g tau at k = 0), 7: cos(w tau)
   uint8_t mask;   // 0: none, 1: dealias mask, 2: (mask * D - 1) projection correction
   uint8_t pad_;
   double c;
+  double tau;     // time of the propagator entries (depth 4..7) [s]
 };
 
 struct ColParams {
@@ -117,10 +121,15 @@ struct ColParams {
 struct TableSpec {
   int W, ny, kx_keep, ky_keep;
   double two_pi_over_Lx, two_pi_over_Ly, h0, filt_kf, filt_beta2, c;
+  double tau, gravity;  // propagator entries (depth 4..7)
   int kpow, depth, gx, gy, mask;
 };
 
-enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2 };
+// RK_ENTRY: working copies of the state; RK_STAGE: a classical RK4 stage;
+// RK_CORRECT: add two mixed corrections to the state, then working copies;
+// RK_OFFSET: working copies of the state plus two mixed offsets, the state
+// itself unchanged (the intermediate stages of the integrating-factor scheme)
+enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2, RK_OFFSET = 3 };
 
 struct RkParams {
   int rpc;              // rows per block
@@ -133,8 +142,8 @@ struct RkParams {
   BufRef eta0, phi0;    // FP64 master state
   BufRef acc_eta, acc_phi;      // FP64 RK4 sums
   BufRef V;             // physical V of this stage (T)
-  BufRef phit;          // mixed phi~_t of this stage (T complex)  / RK_CORRECT: eta correction
-  BufRef corr_phi;      // RK_CORRECT: phi correction (mixed)
+  BufRef phit;          // mixed phi~_t of this stage (T complex) / RK_CORRECT, RK_OFFSET: eta correction
+  BufRef corr_phi;      // RK_CORRECT, RK_OFFSET: phi correction (mixed)
   BufRef eta_w;         // physical working eta (T)
   BufRef eta_hat, phi_hat;      // mixed working spectra (T complex)
   int* nonfinite;       // set to 1 when the new state holds NaN/Inf

@@ -289,3 +289,91 @@ def test_adaptive_order_not_met_is_reported(sbi):
         ctx.vertical_velocity(0)
     assert ei.value.code == sbi.SBI_ENOTCONVERGED
     assert ctx.orders_used(0) == 7
+
+
+LAWSON_CASES = {
+    # name: (nx, ny, Lx, Ly, h0, variable, filter, sponge)
+    "flat2d": (64, 32, 6.0, 4.0, 0.8, False, False, False),
+    "var1d": (256, 1, 12.0, 1.0, 0.5, True, False, False),
+    "var2d_filter_sponge": (64, 32, 6.0, 4.0, 0.7, True, True, True),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("name", list(LAWSON_CASES))
+def test_lawson_steps_match_oracle(sbi, prec, tol, name):
+    # Integrating-factor (Lawson) RK4 steps on the GPU path against the oracle.
+    nx, ny, Lx, Ly, h0, variable, filt, sponge = LAWSON_CASES[name]
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, variable, seed=120)
+    kw = {}
+    if filt:
+        pb.filt_beta1, pb.filt_beta2, pb.k_ref = 8.0, 30.0, 1.0
+        kw.update(filt_beta1=8.0, filt_beta2=30.0, k_ref=1.0)
+    if sponge:
+        x = np.arange(nx) * Lx / nx
+        w = np.broadcast_to(np.exp(-((x - 0.75 * Lx) / (0.1 * Lx)) ** 2), (ny, nx)).copy()
+        pb.sponge_w, pb.sponge_nu = w, 2.0
+        kw.update(sponge_w=w, sponge_nu=2.0)
+    pb.integrator = "lawson"
+    eta, phi = O.project(pb, eta), O.project(pb, phi)
+    depth = [h0 - pb.delta] if variable else None
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, depth, h0=h0, precision=prec,
+                      integrator=sbi.SBI_LAWSON_RK4, **kw)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.03, 3)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.03, 3)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 2e-5)])
+def test_lawson_exact_linear_propagation(sbi, prec, tol):
+    # One integrating-factor step of w dt = 2.5 carries an infinitesimal
+    # travelling wave exactly (order 1), where classical RK4 cannot: the
+    # closed form holds to the size of the nonlinear terms, k a ~ 5e-8, and
+    # the FP64 path equals the oracle to round-off.
+    g, a, nx, L, m, h0 = 9.81, 1e-8, 64, 4.0, 3, 0.4
+    k = 2 * math.pi * m / L
+    w = math.sqrt(g * k * math.tanh(k * h0))
+    x = np.arange(nx) * L / nx
+    ctx = sbi.Context([(nx, 1, L, 1.0)], g, None, h0=h0, order=1, precision=prec,
+                      integrator=sbi.SBI_LAWSON_RK4)
+    ctx.set_state(0, a * np.cos(k * x), (g * a / w) * np.sin(k * x))
+    ctx.step(2.5 / w, 1)
+    e, p = ctx.get_state(0)
+    assert rel(e, a * np.cos(k * x - 2.5)) < tol
+    assert rel(p, (g * a / w) * np.sin(k * x - 2.5)) < tol
+    if prec == 1:
+        pb = O.Problem(O.Grid(nx, 1, L), g, h0, order=1, integrator="lawson")
+        eo, po = O.step(pb, a * np.cos(k * x), (g * a / w) * np.sin(k * x), 2.5 / w, 1)
+        assert rel(e, eo) < 1e-10 and rel(p, po) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_lawson_with_wavemaker_stage_times(sbi, prec, tol):
+    nx, Lx, h0 = 256, 16.0, 0.5
+    grid = O.Grid(nx, 1, Lx)
+    amp, omega, phase = [0.005], [4.0], [0.4]
+    wm = O.Wavemaker(np.array(amp), np.array(omega), np.array(phase), 0.0)
+    pb = O.Problem(grid, 9.81, h0, wavemaker=wm, integrator="lawson")
+    eta = O.project(pb, W.random_field(nx, 1, 130, amplitude=0.01))
+    phi = O.project(pb, W.random_field(nx, 1, 131, amplitude=0.05))
+    ctx = sbi.Context([(nx, 1, Lx, 1.0)], 9.81, None, h0=h0, precision=prec,
+                      integrator=sbi.SBI_LAWSON_RK4)
+    ctx.set_wavemaker(amp, omega, phase)
+    ctx.set_time(1.1)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.04, 5)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.04, 5, t0=1.1)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+def test_lawson_option_validation(sbi):
+    with pytest.raises(sbi.SbiError) as ei:
+        sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, integrator=7)
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, integrator=sbi.SBI_LAWSON_RK4,
+                    adapt_tol=1e-3)
+    assert ei.value.code == sbi.SBI_EINVAL
