@@ -292,7 +292,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl),
+            "config": dict(workload_config(wl), integrator=args.integrator),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: single-member RK4 steps of the workload's "
                                        "member shapes for about 2 s of CPU time"},
