@@ -76,6 +76,15 @@ R11 Integrating factor (Sec. 2.2, the reformulation of Eq. (prognostic) with
     k = 0 [[1, 0], [-g tau, 1]].  The paper integrates the transformed system
     with an adaptive embedded RK5(4); this oracle provides the integrating
     factor with classical RK4 stages and a fixed step (the Lawson scheme).
+R12 HOS diagnostic (the section comparing ESBI and HOS, Eqs. HOS-HOSZ), flat
+    bottom at the reference depth h0: the eigenfunctions are
+    cosh(k(z + h0)) / cosh(k h0) (deep water e^{kz}), so d^n/dz^n at z = 0
+    multiplies mode k by k^n T_n (T_n = tanh(k h0) for odd n, 1 for even n).
+    phi^(1) = phi~, phi^(m) = -sum_{n=1}^{m-1} eta^n/n! d^n_z phi^(m-n),
+    W = sum_m sum_{n=0}^{M-m} eta^n/n! d^{n+1}_z phi^(m); every phi^(m) and W
+    are dealiased with the mask of R5 after their forward transform, and the
+    ESBI quantity is V = W (1 + |grad eta|^2) - grad eta . grad phi~ (the
+    kinematic condition), dealiased as well.
 
 Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
 has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
@@ -265,6 +274,37 @@ def vertical_velocity(eta, phi, delta, h0, grid: Grid, order: int = MAX_ORDER,
     return Vsum
 
 
+def hos_surface_velocity(eta, phi, h0, grid: Grid, order: int = MAX_ORDER, alpha: float = 0.5):
+    """(V, W) by the HOS perturbation expansion (R12): W = dphi/dz at the
+    surface, V = sqrt(1+|grad eta|^2) dphi/dn as in Eq. (prognostic)."""
+    if not 1 <= order <= MAX_ORDER:
+        raise ValueError("order must be in 1..7")
+    eta = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    t, _ = depth_multipliers(K, h0)
+
+    def dz(f_hat, n):          # d^n/dz^n at z = 0 (R12)
+        return ifft(K ** n * (t if n % 2 == 1 else 1.0) * f_hat)
+
+    phis = [None, mask * fft(phi)]                      # Eq. HOSM, phi^(1) = phi~
+    for m in range(2, order + 1):
+        acc = np.zeros_like(eta)
+        for n in range(1, m):
+            acc -= eta ** n / math.factorial(n) * dz(phis[m - n], n)
+        phis.append(mask * fft(acc))
+    W = np.zeros_like(eta)                              # Eq. HOSZ
+    for m in range(1, order + 1):
+        for n in range(0, order - m + 1):
+            W += eta ** n / math.factorial(n) * dz(phis[m], n + 1)
+    W = ifft(mask * fft(W))
+    ge = gradient(mask * fft(eta), KX, KY, grid.dim)
+    gp = gradient(phis[1], KX, KY, grid.dim)
+    V = W * (1.0 + sum(a * a for a in ge)) - sum(a * b for a, b in zip(ge, gp))
+    return ifft(mask * fft(V)), W
+
+
 # --------------------------------------------------------------------------
 # Prognostic right-hand side (Sec. 2.2) and damping pressure (Eq. pd)
 # --------------------------------------------------------------------------
@@ -355,11 +395,19 @@ class Problem:
     adapt_tol: float = 0.0      # R9: 0 = fixed order
     wavemaker: "Wavemaker | None" = None   # R10
     integrator: str = "rk4"                 # "rk4" (classical) or "lawson" (R11)
+    diagnostic: str = "esbi"                # "esbi" (Sec. 2.4) or "hos" (R12, flat bottom)
+
+
+def diagnose(pb: "Problem", eta, phi):
+    """V of the problem's diagnostic: ESBI (Sec. 2.4) or HOS (R12)."""
+    if pb.diagnostic == "hos":
+        return hos_surface_velocity(eta, phi, pb.h0, pb.grid, pb.order, pb.alpha)[0]
+    return vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
 
 
 def surface_rhs(pb: Problem, eta, phi, t: float = 0.0):
     """(eta_t, phi~_t) of Eq. (prognostic) in physical space at time t."""
-    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
+    V = diagnose(pb, eta, phi)
     pg = None
     if pb.wavemaker is not None:
         pg = wavemaker_pressure(pb.wavemaker, pb.grid, pb.h0, pb.gravity, t)
@@ -467,7 +515,7 @@ def invariants(pb: Problem, eta, phi):
     """Mass int eta dA and energy 1/2 int (V phi~ + g eta^2) dA (Eq. energy)."""
     eta = np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
     phi = np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)
-    V = vertical_velocity(eta, phi, pb.delta, pb.h0, pb.grid, pb.order, pb.alpha, tol=pb.adapt_tol)
+    V = diagnose(pb, eta, phi)
     mass = float(np.sum(eta) * pb.grid.dA)
     energy = float(0.5 * np.sum(V * phi + pb.gravity * eta * eta) * pb.grid.dA)
     return mass, energy

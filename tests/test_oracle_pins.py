@@ -456,3 +456,51 @@ def test_lawson_is_fourth_order_and_agrees_with_rk4():
         errs.append(np.linalg.norm(e - e_ref) + np.linalg.norm(p - p_ref))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, (errs, r1, r2)
+
+
+@pytest.mark.parametrize("order", [1, 3, 5, 7])
+def test_hos_constant_elevation_matches_taylor(order):
+    # R12: with a constant elevation a over a flat bottom the HOS sum of order
+    # M keeps exactly the terms of degree <= M-1 in a of the exact
+    # W = V = k tanh(k(h + a)) (sympy), mode by mode.
+    vfun, _ = _taylor_tables()
+    g = O.Grid(32, 16, 2 * np.pi, 2 * np.pi)
+    x = np.arange(g.nx) * g.Lx / g.nx
+    y = np.arange(g.ny) * g.Ly / g.ny
+    X, Y = np.meshgrid(x, y)
+    for (a, h0) in [(0.05, 1.0), (-0.03, 0.6)]:
+        for (mx, my) in [(1, 1), (3, 2)]:
+            kk = math.hypot(mx, my)
+            carrier = np.cos(mx * X + my * Y)
+            V, Wz = O.hos_surface_velocity(np.full((g.ny, g.nx), a), carrier, h0, g, order=order,
+                                           alpha=1.0)
+            ref = sum(vfun[d](a, 0.0, kk, h0) for d in range(order))
+            for f in (V, Wz):
+                amp = np.sum(f * carrier) / np.sum(carrier * carrier)
+                assert abs(amp - ref) < 1e-12 * kk, (order, a, mx, my, amp, ref)
+                assert np.max(np.abs(f - amp * carrier)) < 1e-12 * kk
+
+
+@pytest.mark.parametrize("order,ratio", [(3, 8.0), (5, 32.0), (7, 128.0)])
+def test_hos_truncation_error_scaling_vs_laplace_solver(order, ratio):
+    # R12: scaling eta by s at fixed phi~, the HOS error against the exact
+    # Dirichlet-Neumann operator (independent Laplace solve) falls as s^M;
+    # both V and the Eulerian W = (V + eta_x phi_x) / (1 + eta_x^2).
+    L, nx, h0 = 2 * np.pi, 64, 1.0
+    x = np.arange(nx) * L / nx
+    eta0 = 0.3 * np.cos(x) + 0.2 * np.sin(2 * x + 0.4)
+    phi = np.cos(x) + 0.5 * np.sin(2 * x + 0.3)
+    phi_x = -np.sin(x) + np.cos(2 * x + 0.3)
+    g = O.Grid(nx, 1, L)
+    errs, errw = [], []
+    for s in (0.4, 0.2, 0.1):
+        eta = s * eta0
+        eta_x = s * (-0.3 * np.sin(x) + 0.4 * np.cos(2 * x + 0.4))
+        Ve = exact_vertical_velocity(eta, phi, None, h0, L, n_sigma=32)
+        We = (Ve + eta_x * phi_x) / (1 + eta_x ** 2)
+        Vh, Wh = O.hos_surface_velocity(eta, phi, h0, g, order=order, alpha=1.0)
+        errs.append(np.linalg.norm(Vh[0] - Ve) / np.linalg.norm(Ve))
+        errw.append(np.linalg.norm(Wh[0] - We) / np.linalg.norm(We))
+    for e in (errs, errw):
+        r1, r2 = e[0] / e[1], e[1] / e[2]
+        assert 0.6 * ratio < r1 < 1.5 * ratio and 0.7 * ratio < r2 < 1.4 * ratio, e
