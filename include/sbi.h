@@ -54,6 +54,9 @@ extern "C" {
 #define SBI_FP32 0             /* FFTs, multipliers, products in FP32; FP64 state, RK4 sums, invariants */
 #define SBI_FP64 1             /* everything in FP64 (the plain path) */
 
+#define SBI_DIAG_ESBI 0        /* V by the ESBI successive approximation (Sec. 2.4) */
+#define SBI_DIAG_HOS 1         /* V by the HOS perturbation expansion (flat bottom) */
+
 #define SBI_RK4 0              /* classical RK4 on (eta, phi~) */
 #define SBI_LAWSON_RK4 1       /* integrating factor (Sec. 2.2) with RK4 stages (Lawson) */
 
@@ -99,6 +102,13 @@ typedef struct {
                             stages for the nonlinear part (Lawson's scheme); the paper uses an
                             adaptive embedded RK5(4) for that part.  Not combined with
                             adapt_tol > 0. */
+    int    diagnostic;   /* SBI_DIAG_ESBI (default): V by the successive approximation of
+                            Sec. 2.4.  SBI_DIAG_HOS: V by the HOS perturbation expansion of
+                            the section comparing ESBI and HOS (its Eqs. HOS to HOSZ) on a flat
+                            bottom at h0: phi^(m) = -sum_n eta^n/n! d^n_z phi^(m-n), W =
+                            sum_{m+n<=M} eta^n/n! d^{n+1}_z phi^(m), V = W (1 + |grad eta|^2)
+                            - grad eta . grad phi~, all dealiased; order = M.  Variable depth
+                            or adapt_tol > 0 give SBI_EINVAL. */
 } sbi_options;
 
 /* Fill *opt with the defaults listed above. */

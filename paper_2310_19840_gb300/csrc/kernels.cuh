@@ -303,7 +303,7 @@ k_row(const __grid_constant__ RowParams p) {
       }
       }
     } else {
-      // ROP_N2 / ROP_WDOT: slots V, eta_x, [eta_y,] phi_x, [phi_y]
+      // ROP_N2 / ROP_WDOT / ROP_VFW: slots V (W for ROP_VFW), eta_x, [eta_y,] phi_x, [phi_y]
       const bool two_d = op.a == 2;
       const V* sV = slot_base + ((op.slot + 0) * rpc + rloc) * n;
       const V* sEx = slot_base + ((op.slot + 1) * rpc + rloc) * n;
@@ -333,6 +333,8 @@ k_row(const __grid_constant__ RowParams p) {
           const T num = vc[h] + dot;
           if (op.kind == ROP_N2)
             res[h] = -g * ec[h] + T(0.5) * (num * num / (T(1) + ge2) - gp2) - pwc[h];
+          else if (op.kind == ROP_VFW)
+            res[h] = vc[h] * (T(1) + ge2) - dot;
           else
             res[h] = num / (T(1) + ge2);
         }

@@ -310,6 +310,15 @@ struct Planner {
     r.bytes += mixed_bytes();
     if (room(r)) r.p.ops[r.p.nops++] = op;
   }
+  void vfw(RowB& r, int slot0, const std::string& dst) {
+    RowOp op{};
+    op.kind = ROP_VFW;
+    op.slot = (uint8_t)slot0;
+    op.a = g.two_d ? 2 : 1;
+    op.dst = (uint8_t)add_buf(r, mref(dst));
+    r.bytes += mixed_bytes();
+    if (room(r)) r.p.ops[r.p.nops++] = op;
+  }
   void wdot(RowB& r, int slot0, void* phys_out) {
     RowOp op{};
     op.kind = ROP_WDOT;
@@ -580,7 +589,8 @@ struct Planner {
 
   // mixed buffers whose sum is F_x{V}
   std::vector<std::string> v_names() const {
-    if (c->opt.order == 1) return {std::string("V1")};
+    const bool hos = c->opt.diagnostic == SBI_DIAG_HOS;
+    if (c->opt.order == 1 && !hos) return {std::string("V1")};
     if (if_stage > 0) return {S("Vnl%d", if_stage), std::string("V1")};
     return {std::string("Vsum")};
   }
@@ -610,7 +620,80 @@ struct Planner {
     return ps;
   }
 
+  // HOS diagnostic (flat bottom), the perturbation expansion of the section
+  // comparing ESBI and HOS: d^n/dz^n at z = 0 multiplies mode k by k^n T_n
+  // (T_n = tanh(k h0) for odd n, 1 for even n).
+  //   phi^(1) = phi~,  phi^(m) = -sum_{n=1}^{m-1} eta^n/n! d^n_z phi^(m-n),
+  //   W = sum_{n=0}^{M-1} eta^n/n! sum_{m=1}^{M-n} d^{n+1}_z phi^(m),
+  //   V = W (1 + |grad eta|^2) - grad eta . grad phi~,
+  // every phi^(m), W and V dealiased.  Column passes turn each order into its
+  // z-derivatives HD<m>_<n> (mixed); row passes form the products.
+  void plan_hos_diag(std::vector<Pass>& out) {
+    const int M = c->opt.order;
+    auto dz = [&](int n) { return term(0, 1.0, n, (n % 2) ? 1 : 0, 0, 0, 1); };
+    {
+      std::vector<ColIn> ins = {{st_phi, {term(0, 1.0, 0, 0, 0, 0)}},
+                                {st_eta, {term(1, 1.0, 0, 0, 0, 0)}}};
+      std::vector<std::pair<std::string, ColTerm>> outs;
+      for (int n = 1; n <= M; ++n) outs.push_back({S2("HD%d_%d", 1, n), dz(n)});
+      for (char d : dims()) {
+        const int gx = d == 'x', gy = d == 'y';
+        outs.push_back({std::string("dphi") + d, term(0, 1.0, 0, 0, gx, gy, 1)});
+        outs.push_back({std::string("deta") + d, term(1, 1.0, 0, 0, gx, gy, 1)});
+      }
+      out.push_back(col(ins, outs, 2));
+    }
+    for (int m = 2; m <= M; ++m) {
+      RowB r = row_begin();
+      for (int n = 1; n < m; ++n) {
+        c2r(r, 0, {S2("HD%d_%d", m - n, n)});
+        prod(r, 0, n, 0, 0, -1.0 / fact(n), S2("HP%d_%d", m, n));
+      }
+      out.push_back(row_end(r, true, false, false));
+      std::vector<ColIn> ins;
+      for (int n = 1; n < m; ++n) ins.push_back({S2("HP%d_%d", m, n), {term(0, 1.0, 0, 0, 0, 0)}});
+      std::vector<std::pair<std::string, ColTerm>> outs;
+      for (int n = 1; n <= M - m + 1; ++n) outs.push_back({S2("HD%d_%d", m, n), dz(n)});
+      out.push_back(col(ins, outs, 1));
+    }
+    {
+      RowB r = row_begin();
+      for (int n = 0; n < M; ++n) {
+        std::vector<std::string> src;
+        for (int m = 1; m <= M - n; ++m) src.push_back(S2("HD%d_%d", m, n + 1));
+        c2r(r, 0, src);
+        prod(r, 0, n, 0, 0, 1.0 / fact(n), S("HW%d", n));
+      }
+      out.push_back(row_end(r, true, false, false));
+      std::vector<ColIn> ins;
+      for (int n = 0; n < M; ++n) ins.push_back({S("HW%d", n), {term(0, 1.0, 0, 0, 0, 0)}});
+      out.push_back(col(ins, {{"HWs", term(0, 1.0, 0, 0, 0, 0, 1)}}, 1));
+    }
+    {
+      RowB r = row_begin();
+      c2r(r, 0, {"HWs"});
+      int s = 1;
+      for (char d : dims()) c2r(r, s++, {std::string("deta") + d});
+      for (char d : dims()) c2r(r, s++, {std::string("dphi") + d});
+      vfw(r, 0, "HVr");
+      out.push_back(row_end(r, false, false, false));
+      if (if_stage > 0) {
+        // integrating factor: the nonlinear part V - k tanh(kh) phi^ and V_1
+        std::vector<ColIn> ins = {{"HVr", {term(0, 1.0, 0, 0, 0, 0)}},
+                                  {st_phi, {term(0, -1.0, 1, 1, 0, 0), term(1, 1.0, 1, 1, 0, 0)}}};
+        out.push_back(col(ins, {{S("Vnl%d", if_stage), term(0, 1.0, 0, 0, 0, 0, 1)},
+                                {"V1", term(1, 1.0, 0, 0, 0, 0, 1)}}, 2));
+      } else {
+        out.push_back(col({{"HVr", {term(0, 1.0, 0, 0, 0, 0)}}}, {{"Vsum", term(0, 1.0, 0, 0, 0, 0, 1)}}, 1));
+      }
+    }
+  }
+
   void plan_diag(std::vector<Pass>& out) {
+    if (c->opt.diagnostic == SBI_DIAG_HOS) {
+      plan_hos_diag(out);
+      return;
+    }
     const bool adapt = c->opt.adapt_tol > 0.0 && c->opt.order > 1;
     if (adapt) out.push_back(plan_conv(0, 1));
     out.push_back(plan_col_a());
@@ -759,7 +842,8 @@ struct Planner {
       add(b, prop(0, 1.0, 5, tau));
       add(b, prop(1, 1.0, 4, tau));
     };
-    const bool has_vnl = c->opt.order > 1;   // order 1: V - V_1 = 0
+    // order 1 of the successive approximation: V - V_1 = 0 (not so for HOS)
+    const bool has_vnl = c->opt.order > 1 || c->opt.diagnostic == SBI_DIAG_HOS;
     const double nrm = (double)g.nx;
     // cc E(tau) k_q (prop_it) or cc k_q
     auto k_pair = [&](int q, double cc, double tau, bool prop_it) {
@@ -1017,7 +1101,7 @@ std::string pass_signature(const Pass& p) {
   char b[160];
   if (p.kind == PK_ROW) {
     std::string ops;
-    for (int o = 0; o < p.row.nops; ++o) ops += "CPNW"[p.row.ops[o].kind & 3];
+    for (int o = 0; o < p.row.nops; ++o) ops += "CPNWV"[p.row.ops[o].kind < 5 ? p.row.ops[o].kind : 0];
     snprintf(b, sizeof(b), "row nx=%d rows=%d slots=%d ops=%d ", p.nsize, p.row.rows_total, p.row.nslots,
              p.row.nops);
     return b + ops;
@@ -1377,6 +1461,10 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
   if (opt.adapt_tol < 0.0) return fail(nullptr, SBI_EINVAL, "adapt_tol must be >= 0");
   if (opt.integrator != SBI_RK4 && opt.integrator != SBI_LAWSON_RK4)
     return fail(nullptr, SBI_EINVAL, "integrator must be SBI_RK4 or SBI_LAWSON_RK4");
+  if (opt.diagnostic != SBI_DIAG_ESBI && opt.diagnostic != SBI_DIAG_HOS)
+    return fail(nullptr, SBI_EINVAL, "diagnostic must be SBI_DIAG_ESBI or SBI_DIAG_HOS");
+  if (opt.diagnostic == SBI_DIAG_HOS && opt.adapt_tol > 0.0)
+    return fail(nullptr, SBI_EINVAL, "the HOS diagnostic is not combined with adapt_tol > 0");
   if (opt.integrator == SBI_LAWSON_RK4 && opt.adapt_tol > 0.0)
     return fail(nullptr, SBI_EINVAL, "the integrating factor (integrator) is not combined with adapt_tol > 0");
   if ((opt.dev_alloc == nullptr) != (opt.dev_free == nullptr))
@@ -1443,6 +1531,10 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
       }
     }
     h0s[i] = h0;
+    if (var[i] && opt.diagnostic == SBI_DIAG_HOS) {
+      c->err = "the HOS diagnostic needs a flat bottom (h == NULL or constant h)";
+      return bail(SBI_EINVAL);
+    }
   }
 
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {

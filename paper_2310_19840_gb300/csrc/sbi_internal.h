@@ -26,7 +26,7 @@ namespace sbi {
 constexpr int kMaxRowOps = 48;
 constexpr int kMaxRowBufs = 40;
 constexpr int kMaxColTerms = 48;
-constexpr int kMaxColOuts = 8;
+constexpr int kMaxColOuts = 12;
 constexpr int kMaxColBufs = 32;
 constexpr int kMaxColAcc = 2;
 constexpr int kMaxSlots = 5;
@@ -41,6 +41,8 @@ enum RowOpKind : uint8_t {
                  // V, eta_x, phi_x (1-D); coef = gravity
   ROP_WDOT = 3,  // physical dst <- w-free Eulerian vertical velocity
                  // (V + grad eta.grad phi)/(1+|grad eta|^2) from the same slots
+  ROP_VFW = 4,   // mixed dst <- r2c(W (1 + |grad eta|^2) - grad eta.grad phi), the
+                 // kinematic V from the Eulerian W in the V slot (HOS diagnostic)
 };
 
 struct RowOp {

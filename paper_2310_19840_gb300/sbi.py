@@ -18,6 +18,7 @@ from . import build as _build
 SBI_OK, SBI_EINVAL, SBI_ENOMEM, SBI_ECUDA, SBI_ENONFINITE, SBI_ENOTCONVERGED, SBI_ETIMEOUT = range(7)
 SBI_FP32, SBI_FP64 = 0, 1
 SBI_RK4, SBI_LAWSON_RK4 = 0, 1
+SBI_DIAG_ESBI, SBI_DIAG_HOS = 0, 1
 
 
 class SbiError(RuntimeError):
@@ -42,7 +43,7 @@ class sbi_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("check_finite", C.c_int),
                 ("set_state_dealias", C.c_int),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("autotune", C.c_int), ("integrator", C.c_int)]
+                ("autotune", C.c_int), ("integrator", C.c_int), ("diagnostic", C.c_int)]
 
 
 EXPORTS = {
@@ -156,7 +157,7 @@ class Context:
     def __init__(self, grids, gravity, depths=None, *, h0=math.nan, order=7, alias_frac=0.5,
                  precision=SBI_FP32, adapt_tol=0.0, filt_beta1=0.0, filt_beta2=0.0, k_ref=1.0,
                  sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1,
-                 autotune=1, integrator=SBI_RK4):
+                 autotune=1, integrator=SBI_RK4, diagnostic=SBI_DIAG_ESBI):
         self.lib = load()
         if isinstance(grids, tuple):
             grids = [grids]
@@ -166,7 +167,7 @@ class Context:
                               adapt_tol=adapt_tol, filt_beta1=filt_beta1, filt_beta2=filt_beta2,
                               k_ref=k_ref, sponge_nu=sponge_nu, check_finite=check_finite,
                               set_state_dealias=set_state_dealias, autotune=autotune,
-                              integrator=integrator)
+                              integrator=integrator, diagnostic=diagnostic)
         keep = []
         if sponge_w is not None:
             w = np.ascontiguousarray(sponge_w, dtype=np.float64).ravel()

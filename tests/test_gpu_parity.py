@@ -377,3 +377,57 @@ def test_lawson_option_validation(sbi):
         sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, integrator=sbi.SBI_LAWSON_RK4,
                     adapt_tol=1e-3)
     assert ei.value.code == sbi.SBI_EINVAL
+
+
+HOS_CASES = [
+    # nx, ny, Lx, Ly, h0, order
+    (64, 32, 6.0, 4.0, 0.8, 7),
+    (64, 32, 6.0, 4.0, 0.8, 3),
+    (128, 1, 9.0, 1.0, 0.5, 7),
+    (64, 32, 6.0, 4.0, math.inf, 5),
+    (32, 16, 3.0, 2.0, 0.6, 1),
+]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("case", HOS_CASES)
+def test_hos_diagnostic_matches_oracle(sbi, prec, case):
+    # The HOS perturbation expansion (flat bottom) on the GPU path against the
+    # oracle's, V after one evaluation.
+    nx, ny, Lx, Ly, h0, order = case
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0 if math.isfinite(h0) else 1.0, False, seed=140)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, None, h0=h0, order=order, precision=prec,
+                      diagnostic=sbi.SBI_DIAG_HOS)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    Vo, _ = O.hos_surface_velocity(eta, phi, h0, grid, order=order)
+    assert rel(V, Vo) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("integrator", ["rk4", "lawson"])
+def test_hos_steps_match_oracle(sbi, prec, tol, integrator):
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, False, seed=150)
+    pb.diagnostic, pb.integrator = "hos", integrator
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, None, h0=h0, precision=prec,
+                      diagnostic=sbi.SBI_DIAG_HOS,
+                      integrator=sbi.SBI_LAWSON_RK4 if integrator == "lawson" else sbi.SBI_RK4)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.03, 3)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.03, 3)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+def test_hos_option_validation(sbi):
+    depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
+    with pytest.raises(sbi.SbiError) as ei:
+        sbi.Context([(32, 1, 3.0, 1.0)], 9.81, [depth], h0=0.7, diagnostic=sbi.SBI_DIAG_HOS)
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, diagnostic=sbi.SBI_DIAG_HOS, adapt_tol=1e-3)
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, diagnostic=5)
+    assert ei.value.code == sbi.SBI_EINVAL
