@@ -40,6 +40,8 @@ def parse():
                     choices=["crossing_batch", "large_variable", "bar_1d", "stokes_2d",
                              "bar_wavemaker_1d", "solitary_1d"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--diagnostic", default="esbi", choices=["esbi", "hos"],
+                    help="V by the ESBI successive approximation or the HOS expansion (flat bottom)")
     ap.add_argument("--integrator", default="rk4", choices=["rk4", "lawson"],
                     help="classical RK4 or the integrating factor with RK4 stages")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
@@ -238,7 +240,7 @@ def time_steps(ctx, torch, stream, dt, steps, warmup):
     return ev0.elapsed_time(ev1) / 1000.0
 
 
-def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4"):
+def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4", diagnostic="esbi"):
     """Time the FP64 oracle on a bounded sample: whole RK4 steps of members
     drawn in workload order, until about target_s seconds of CPU work."""
     from oracle import sbi_oracle as O
@@ -264,6 +266,7 @@ def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4"):
                            np.array(wl.wavemaker["phase"]), wl.wavemaker["x0"]))
         t0 = time.perf_counter()
         pb.integrator = integrator
+        pb.diagnostic = diagnostic
         O.step(pb, m.eta, m.phi, wl.dt, 1)
         t_tot += time.perf_counter() - t0
         pts += m.nx * m.ny
@@ -283,7 +286,7 @@ def run_reference(args):
     total_t, total_pts = 0.0, 0
     samples = []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(wl, target_s=2.0, integrator=args.integrator)
+        r = cpu_oracle_sample(wl, target_s=2.0, integrator=args.integrator, diagnostic=args.diagnostic)
         if k >= args.warmup:
             pts_s = r["value"]
             samples.append(pts_s)
@@ -292,7 +295,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(wl), integrator=args.integrator),
+            "config": dict(workload_config(wl), integrator=args.integrator, diagnostic=args.diagnostic),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: single-member RK4 steps of the workload's "
                                        "member shapes for about 2 s of CPU time"},
@@ -323,7 +326,8 @@ def main():
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
     integ = sbi.SBI_LAWSON_RK4 if args.integrator == "lawson" else sbi.SBI_RK4
-    ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ)
+    diag = sbi.SBI_DIAG_HOS if args.diagnostic == "hos" else sbi.SBI_DIAG_ESBI
+    ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag)
     for i, m in enumerate(wl.members):
         ctx.set_state(i, m.eta, m.phi)
     launches = ctx.step_launches()
@@ -389,10 +393,12 @@ def main():
     err = None
     fp64_arm = None
     if not args.no_fp64_arm and prec == sbi.SBI_FP32:
-        ctx64 = make_context(sbi, wl, sbi.SBI_FP64, stream.cuda_stream, integrator=integ)
+        ctx64 = make_context(sbi, wl, sbi.SBI_FP64, stream.cuda_stream, integrator=integ,
+                             diagnostic=diag)
         for i, m in enumerate(wl.members):
             ctx64.set_state(i, m.eta, m.phi)
-        ctx_err = make_context(sbi, wl, sbi.SBI_FP32, stream.cuda_stream, integrator=integ)
+        ctx_err = make_context(sbi, wl, sbi.SBI_FP32, stream.cuda_stream, integrator=integ,
+                               diagnostic=diag)
         ctx_err.set_state(0, wl.members[0].eta, wl.members[0].phi)
         ctx64_0 = ctx64
         V32 = ctx_err.vertical_velocity(0)
@@ -410,7 +416,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0,
-                             integrator=integ)
+                             integrator=integ, diagnostic=diag)
         # every member's eta and phi~, concatenated in member order, in pinned memory
         eta_h = torch.from_numpy(np.concatenate([np.ravel(m.eta) for m in wl.members])).pin_memory()
         phi_h = torch.from_numpy(np.concatenate([np.ravel(m.phi) for m in wl.members])).pin_memory()
@@ -438,11 +444,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(wl, target_s=10.0, integrator=args.integrator)
+        cpu = cpu_oracle_sample(wl, target_s=10.0, integrator=args.integrator,
+                                diagnostic=args.diagnostic)
 
     cfg = workload_config(wl)
     cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
     cfg["integrator"] = "lawson (integrating factor, RK4 stages)" if args.integrator == "lawson" else "classical RK4"
+    cfg["diagnostic"] = args.diagnostic
+    cfg["transforms_per_point_step"] = ctx.step_transforms(-1) / wl.points
     cfg["autotune"] = autotune_summary(ctx.autotune_report())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
