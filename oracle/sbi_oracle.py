@@ -76,6 +76,16 @@ R11 Integrating factor (Sec. 2.2, the reformulation of Eq. (prognostic) with
     k = 0 [[1, 0], [-g tau, 1]].  The paper integrates the transformed system
     with an adaptive embedded RK5(4); this oracle provides the integrating
     factor with classical RK4 stages and a fixed step (the Lawson scheme).
+R13 Adaptive integrating factor (Sec. 2.2: six-stage fifth-order RK with an
+    embedded fourth-order solution, step size from their difference): the
+    tableau is Cash and Karp's 5(4) pair; in the integrating-factor form
+    stage i is E(c_i h) u_n + h sum_j a_ij E((c_i - c_j) h) k_j and the
+    solutions E(h) u_n + h sum_j b_j E((1 - c_j) h) k_j (b of order 5 and 4).
+    The error of a step is max over eta and phi~ of ||u5 - u4|| / ||u_n||
+    (L2 over the member, fields whose norm is 0 skipped); a step is accepted
+    when the error is at most tol, and the next step is
+    h min(5, max(0.2, 0.9 (tol / err)^(1/5))) (5 h when err = 0), cut to end
+    at t_end.  The order-5 solution is kept.
 R12 HOS diagnostic (the section comparing ESBI and HOS, Eqs. HOS-HOSZ), flat
     bottom at the reference depth h0: the eigenfunctions are
     cosh(k(z + h0)) / cosh(k h0) (deep water e^{kz}), so d^n/dz^n at z = 0
@@ -394,7 +404,7 @@ class Problem:
     k_ref: float = 1.0
     adapt_tol: float = 0.0      # R9: 0 = fixed order
     wavemaker: "Wavemaker | None" = None   # R10
-    integrator: str = "rk4"                 # "rk4" (classical) or "lawson" (R11)
+    integrator: str = "rk4"                 # "rk4" (classical), "lawson" (R11) or "rk45" (R13)
     diagnostic: str = "esbi"                # "esbi" (Sec. 2.4) or "hos" (R12, flat bottom)
 
 
@@ -485,6 +495,93 @@ def lawson_rk4_step(pb: "Problem", eta, phi, dt: float, t: float = 0.0):
     return ifft(new[0]), ifft(new[1])
 
 
+# Cash-Karp 5(4) tableau (R13): nodes, stage weights, order-5 and order-4 weights
+CK_C = (0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0)
+CK_A = ((),
+        (1.0 / 5.0,),
+        (3.0 / 40.0, 9.0 / 40.0),
+        (3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0),
+        (-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0),
+        (1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0))
+CK_B5 = (37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0)
+CK_B4 = (2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0, 1.0 / 4.0)
+
+
+def if_rk45_step(pb: "Problem", eta, phi, dt: float, t: float = 0.0):
+    """One integrating-factor step with the 5(4) pair of R13: returns the
+    order-5 pair (eta, phi~) and the order-4 pair."""
+    def E(tau, a, b):
+        C, Sk, Sg = linear_propagator(pb, tau)
+        return C * a + Sk * b, -Sg * a + C * b
+
+    def N(a, b, tt):
+        ne, nph = nonlinear_part(pb, ifft(a), ifft(b), tt)
+        return fft(ne), fft(nph)
+
+    u = (fft(np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)),
+         fft(np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx)))
+    ks = []
+    for i in range(6):
+        st = list(E(CK_C[i] * dt, *u))
+        for j in range(i):
+            if CK_A[i][j] != 0.0:
+                ek = E((CK_C[i] - CK_C[j]) * dt, *ks[j])
+                st[0] = st[0] + dt * CK_A[i][j] * ek[0]
+                st[1] = st[1] + dt * CK_A[i][j] * ek[1]
+        ks.append(N(st[0], st[1], t + CK_C[i] * dt))
+    out = []
+    for b in (CK_B5, CK_B4):
+        acc = list(E(dt, *u))
+        for j in range(6):
+            if b[j] != 0.0:
+                ek = E((1.0 - CK_C[j]) * dt, *ks[j])
+                acc[0] = acc[0] + dt * b[j] * ek[0]
+                acc[1] = acc[1] + dt * b[j] * ek[1]
+        out.append((ifft(acc[0]), ifft(acc[1])))
+    return out[0], out[1]
+
+
+def step_error(eta0, phi0, y5, y4):
+    """R13: max over the fields of ||u5 - u4|| / ||u_n|| (fields of norm 0 skipped)."""
+    err = 0.0
+    for f0, a, b in ((eta0, y5[0], y4[0]), (phi0, y5[1], y4[1])):
+        n0 = float(np.linalg.norm(f0))
+        if n0 > 0.0:
+            err = max(err, float(np.linalg.norm(a - b)) / n0)
+    return err
+
+
+def next_step(h: float, err: float, tol: float) -> float:
+    """R13: the step after an error err at step h."""
+    if err == 0.0:
+        return 5.0 * h
+    return h * min(5.0, max(0.2, 0.9 * (tol / err) ** 0.2))
+
+
+def step_adaptive(pb: "Problem", eta, phi, t0: float, t_end: float, tol: float, h: float,
+                  max_steps: int = 100000):
+    """Integrate from t0 to t_end with the adaptive integrating factor of R13;
+    each accepted step is followed by the projection of R5/R8.  Returns
+    (eta, phi~, h_next, accepted, rejected)."""
+    y = (np.asarray(eta, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx),
+         np.asarray(phi, dtype=np.float64).reshape(pb.grid.ny, pb.grid.nx))
+    t, acc, rej = t0, 0, 0
+    while t < t_end and acc + rej < max_steps:
+        last = t + h >= t_end
+        hh = t_end - t if last else h
+        y5, y4 = if_rk45_step(pb, y[0], y[1], hh, t)
+        err = step_error(y[0], y[1], y5, y4)
+        if err <= tol:
+            y = (project(pb, y5[0]), project(pb, y5[1]))
+            t = t_end if last else t + hh
+            acc += 1
+            h = next_step(hh, err, tol) if not last else max(h, next_step(hh, err, tol))
+        else:
+            rej += 1
+            h = next_step(hh, err, tol)
+    return y[0], y[1], h, acc, rej
+
+
 def rk4_step(f, y, dt, t=0.0):
     """Classical RK4 for y' = f(t, y) from time t; y is a tuple of arrays."""
     def axpy(a, x, b):
@@ -505,6 +602,8 @@ def step(pb: Problem, eta, phi, dt: float, n: int = 1, t0: float = 0.0):
     for i in range(n):
         if pb.integrator == "lawson":
             y = lawson_rk4_step(pb, y[0], y[1], dt, t0 + i * dt)
+        elif pb.integrator == "rk45":
+            y = if_rk45_step(pb, y[0], y[1], dt, t0 + i * dt)[0]
         else:
             y = rk4_step(lambda t, s: surface_rhs(pb, s[0], s[1], t), y, dt, t0 + i * dt)
         y = (project(pb, y[0]), project(pb, y[1]))

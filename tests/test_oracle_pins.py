@@ -504,3 +504,81 @@ def test_hos_truncation_error_scaling_vs_laplace_solver(order, ratio):
     for e in (errs, errw):
         r1, r2 = e[0] / e[1], e[1] / e[2]
         assert 0.6 * ratio < r1 < 1.5 * ratio and 0.7 * ratio < r2 < 1.4 * ratio, e
+
+
+def test_rk45_tableau_conditions():
+    # R13: Cash-Karp 5(4) pair, the consistency conditions of an explicit RK
+    # pair: rows of A sum to the nodes, both weight vectors sum to 1, and the
+    # order conditions sum b c = 1/2, sum b c^2 = 1/3, sum b c^3 = 1/4 hold for
+    # both (order 4 and 5), sum b c^4 = 1/5 for the order-5 weights only.
+    c, A, b5, b4 = O.CK_C, O.CK_A, O.CK_B5, O.CK_B4
+    for i in range(6):
+        assert abs(sum(A[i]) - c[i]) < 1e-15
+    for b in (b5, b4):
+        assert abs(sum(b) - 1.0) < 1e-15
+        for q, val in ((1, 0.5), (2, 1 / 3), (3, 0.25)):
+            assert abs(sum(bi * ci ** q for bi, ci in zip(b, c)) - val) < 1e-14
+    assert abs(sum(bi * ci ** 4 for bi, ci in zip(b5, c)) - 0.2) < 1e-14
+    assert abs(sum(bi * ci ** 4 for bi, ci in zip(b4, c)) - 0.2) > 1e-4
+
+
+@pytest.mark.parametrize("h0", [0.4, math.inf])
+def test_rk45_exact_for_linear_waves(h0):
+    # R13: the integrating factor carries an infinitesimal travelling wave
+    # exactly for any step, and both solutions of the pair agree.
+    g, a, nx, L, m = 9.81, 1e-8, 64, 4.0, 3
+    grid = O.Grid(nx, 1, L)
+    k = 2 * math.pi * m / L
+    w = math.sqrt(g * k * (math.tanh(k * h0) if math.isfinite(h0) else 1.0))
+    x = np.arange(nx) * L / nx
+    pb = O.Problem(grid, g, h0, order=1, integrator="rk45")
+    y5, y4 = O.if_rk45_step(pb, a * np.cos(k * x)[None, :], (g * a / w) * np.sin(k * x)[None, :], 3.0 / w)
+    assert np.max(np.abs(y5[0][0] - a * np.cos(k * x - 3.0))) < 1e-6 * a
+    assert np.max(np.abs(y4[0][0] - y5[0][0])) < 1e-6 * a
+
+
+def _rk45_case():
+    nx, ny, Lx, Ly, h0 = 32, 16, 6.0, 3.0, 0.7
+    grid = O.Grid(nx, ny, Lx, Ly)
+    delta = W.random_field(nx, ny, 111, amplitude=0.05, band=0.3)
+    pb = O.Problem(grid, 9.81, h0, delta=delta, order=4, integrator="rk45")
+    eta = O.project(pb, W.random_field(nx, ny, 112, amplitude=0.04, band=0.3))
+    phi = O.project(pb, W.random_field(nx, ny, 113, amplitude=0.1, band=0.3))
+    return grid, delta, pb, eta, phi
+
+
+def test_rk45_fifth_order_and_embedded_estimate():
+    # R13: the order-5 solution converges at fifth order to the classical RK4
+    # solution at a tiny step (error ratio ~32 per halving); the embedded
+    # estimate |u5 - u4| of one step shrinks like h^5 too.
+    grid, delta, pb, eta, phi = _rk45_case()
+    T_end = 0.4
+    ref = O.step(O.Problem(grid, 9.81, 0.7, delta=delta, order=4), eta, phi, T_end / 1024, 1024)
+    errs = []
+    for n in (4, 8, 16):
+        e, p = O.step(pb, eta, phi, T_end / n, n)
+        errs.append(np.linalg.norm(e - ref[0]) + np.linalg.norm(p - ref[1]))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 22.0 < r1 < 45.0 and 22.0 < r2 < 45.0, (errs, r1, r2)
+    est = []
+    for h in (0.2, 0.1, 0.05):
+        y5, y4 = O.if_rk45_step(pb, eta, phi, h)
+        est.append(O.step_error(eta, phi, y5, y4))
+    q1, q2 = est[0] / est[1], est[1] / est[2]
+    assert 20.0 < q1 < 48.0 and 20.0 < q2 < 48.0, (est, q1, q2)
+
+
+def test_rk45_adaptive_run():
+    # R13: the adaptive run lands on t_end, its error against the reference is
+    # of the order of the tolerance, and a looser tolerance takes fewer steps.
+    grid, delta, pb, eta, phi = _rk45_case()
+    T_end = 0.6
+    ref = O.step(O.Problem(grid, 9.81, 0.7, delta=delta, order=4), eta, phi, T_end / 512, 512)
+    steps = {}
+    for tol in (1e-6, 1e-8):
+        e, p, h, acc, rej = O.step_adaptive(pb, eta, phi, 0.0, T_end, tol, 0.05)
+        err = max(np.linalg.norm(e - ref[0]) / np.linalg.norm(ref[0]),
+                  np.linalg.norm(p - ref[1]) / np.linalg.norm(ref[1]))
+        assert err < 50 * tol, (tol, err)
+        steps[tol] = acc
+    assert steps[1e-6] < steps[1e-8]
