@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--diagnostic", default="esbi", choices=["esbi", "hos"],
                     help="V by the ESBI successive approximation or the HOS expansion (flat bottom)")
-    ap.add_argument("--integrator", default="rk4", choices=["rk4", "lawson"],
-                    help="classical RK4 or the integrating factor with RK4 stages")
+    ap.add_argument("--integrator", default="rk4", choices=["rk4", "lawson", "rk45"],
+                    help="classical RK4, the integrating factor with RK4 stages, or with the "
+                         "5(4) pair at a fixed step")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -325,7 +326,7 @@ def main():
     wl = make_workload(args.workload, args.members, rank)
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
-    integ = sbi.SBI_LAWSON_RK4 if args.integrator == "lawson" else sbi.SBI_RK4
+    integ = {"rk4": sbi.SBI_RK4, "lawson": sbi.SBI_LAWSON_RK4, "rk45": sbi.SBI_IF_RK45}[args.integrator]
     diag = sbi.SBI_DIAG_HOS if args.diagnostic == "hos" else sbi.SBI_DIAG_ESBI
     ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag)
     for i, m in enumerate(wl.members):
@@ -449,7 +450,8 @@ def main():
 
     cfg = workload_config(wl)
     cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
-    cfg["integrator"] = "lawson (integrating factor, RK4 stages)" if args.integrator == "lawson" else "classical RK4"
+    cfg["integrator"] = {"rk4": "classical RK4", "lawson": "lawson (integrating factor, RK4 stages)",
+                         "rk45": "integrating factor, Cash-Karp 5(4) pair, fixed step"}[args.integrator]
     cfg["diagnostic"] = args.diagnostic
     cfg["transforms_per_point_step"] = ctx.step_transforms(-1) / wl.points
     cfg["autotune"] = autotune_summary(ctx.autotune_report())

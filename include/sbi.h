@@ -59,6 +59,9 @@ extern "C" {
 
 #define SBI_RK4 0              /* classical RK4 on (eta, phi~) */
 #define SBI_LAWSON_RK4 1       /* integrating factor (Sec. 2.2) with RK4 stages (Lawson) */
+#define SBI_IF_RK45 2          /* integrating factor with the six-stage 5(4) pair of Sec. 2.2
+                                  (Cash-Karp): fixed steps in sbi_step, adaptive ones in
+                                  sbi_step_adaptive */
 
 typedef struct sbi_ctx sbi_ctx;   /* opaque */
 
@@ -100,8 +103,9 @@ typedef struct {
                             with A the linearisation d/dt (eta^, phi^) = [[0, k tanh(k h0)],
                             [-g, 0]] (eta^, phi^), applied exactly per mode, and classical RK4
                             stages for the nonlinear part (Lawson's scheme); the paper uses an
-                            adaptive embedded RK5(4) for that part.  Not combined with
-                            adapt_tol > 0. */
+                            adaptive embedded RK5(4) for that part, which SBI_IF_RK45
+                            provides.  The integrating factors are not combined with
+                            adapt_tol > 0, SBI_IF_RK45 not with the wavemaker. */
     int    diagnostic;   /* SBI_DIAG_ESBI (default): V by the successive approximation of
                             Sec. 2.4.  SBI_DIAG_HOS: V by the HOS perturbation expansion of
                             the section comparing ESBI and HOS (its Eqs. HOS to HOSZ) on a flat
@@ -227,6 +231,25 @@ int sbi_step_bytes(const sbi_ctx* ctx, int family, double* bytes);
  * bandwidth model in which every transform pass streams its field once in
  * and once out. */
 int sbi_step_transforms(const sbi_ctx* ctx, int family, double* point_transforms);
+
+/* Adaptive integrating-factor steps (integrator = SBI_IF_RK45) from the
+ * context time to t_end (Sec. 2.2: six-stage fifth-order RK with an embedded
+ * fourth-order solution, step size from their difference).  Each attempt
+ * computes both solutions; its error is the largest over members and over
+ * eta, phi~ of ||u5 - u4|| / ||u_n|| (L2 over the member's kept modes).  The
+ * step is accepted (the order-5 solution kept) when the error is at most
+ * tol; the next step is h min(5, max(0.2, 0.9 (tol/err)^(1/5))), the last one
+ * cut to end at t_end.  A batch shares one step size.
+ *   t_end     end time [s]; nothing happens when it is not after the context time
+ *   tol       > 0, relative error per step
+ *   h_inout   in: the first trial step [s]; out: the proposed next step
+ *   accepted, rejected   out (may be NULL): attempts taken
+ * Synchronizes once per attempt (the error is read on the host).
+ * SBI_EINVAL for bad arguments or another integrator; SBI_ENOTCONVERGED when
+ * the step underflows; SBI_ENONFINITE when the error or the state is not
+ * finite. */
+int sbi_step_adaptive(sbi_ctx* ctx, double t_end, double tol, double* h_inout, int* accepted,
+                      int* rejected);
 
 /* Number of kernel launches in one captured step. */
 int sbi_step_launches(const sbi_ctx* ctx, int* launches);

@@ -27,6 +27,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <map>
 #include <string>
 #include <vector>
@@ -41,7 +42,31 @@ namespace {
 
 std::string g_create_error = "no error";
 
-enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2, PK_CONV = 3, PK_WMK = 4 };
+enum PassKind { PK_ROW = 0, PK_COL = 1, PK_RK = 2, PK_CONV = 3, PK_WMK = 4, PK_NORM = 5 };
+
+// Cash-Karp 5(4) pair (the adaptive integrating factor): nodes, stage
+// weights, order-5 and order-4 solution weights
+constexpr double kCkC[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+constexpr double kCkA[6][5] = {{0, 0, 0, 0, 0},
+                               {1.0 / 5.0, 0, 0, 0, 0},
+                               {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+                               {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
+                               {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
+                               {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0,
+                                253.0 / 4096.0}};
+constexpr double kCkB5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+constexpr double kCkB4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0,
+                             277.0 / 14336.0, 1.0 / 4.0};
+
+// Step norms of the adaptive scheme: per member, over the kept modes,
+// |Ee|^2, |Ep|^2, |eta^|^2, |phi^|^2 (Parseval weights 1 for kx = 0, 2 else)
+struct NormParams {
+  const void *ee, *ep, *ue, *up;
+  long long stride;   // complex elements per member
+  int W, ny, n;
+  double* part;       // [n][kConvBlocks][4]
+  double* out;        // [n][4]
+};
 
 // Device-side convergence test of the adaptive order (opt.adapt_tol > 0):
 // after order l, per member, inc = ||F{V_l}||^2 and tot = ||F{V_1 + .. + V_l}||^2
@@ -74,7 +99,7 @@ struct WmkParams {
 enum Family { FAM_COL = 0, FAM_ROW = 1, FAM_RK = 2, FAM_CONV = 3, FAM_WMK = 4, FAM_COUNT = 5 };
 const char* kFamilyNames[FAM_COUNT] = {"k_col (column FFT + spectral combine)",
                                        "k_row (row FFT + products)", "k_rk (RK4 stage)",
-                                       "k_conv (adaptive-order test)",
+                                       "k_conv (adaptive-order test / step norms)",
                                        "k_wavemaker (surface pressure profile)"};
 
 struct Pass {
@@ -85,8 +110,17 @@ struct Pass {
   RkParams rk;
   ConvParams conv;
   WmkParams wmk;
+  NormParams norm;
   double bytes;   // algorithmic device-memory traffic of the launch
   double xforms;  // 1-D transform passes over a whole field, times the field's points
+};
+
+// A table whose values depend on the step h: tau = r h, coefficient c0 h^p.
+struct DynTable {
+  void* ptr;
+  TableSpec spec;
+  double r;
+  int p;
 };
 
 struct Group {
@@ -97,6 +131,7 @@ struct Group {
   std::vector<int> members;  // context member ids
   double *eta0 = nullptr, *phi0 = nullptr, *acc_eta = nullptr, *acc_phi = nullptr;
   void *eta_w = nullptr, *Vphys = nullptr, *delta = nullptr, *wout = nullptr;
+  void* eta_ws = nullptr;    // physical working eta of the adaptive scheme's later stages (lazy)
   double* out64 = nullptr;   // conversion buffer for one member's field
   double* stage64 = nullptr; // conversion buffer for every member's field (batch calls; lazy)
   int* d_active = nullptr;   // per-member flags for single-member passes
@@ -107,6 +142,9 @@ struct Group {
   double* wm_prof = nullptr; // wavemaker bells [J][nx] (FP64)
   void* wm_pg = nullptr;     // wavemaker pressure profile of the current stage (nx)
   int wm_cap = 0;            // components wm_prof has room for
+  std::vector<DynTable> dyn; // h-dependent propagator tables (adaptive scheme)
+  double* d_norm45 = nullptr; // adaptive scheme: per member |e_eta|^2, |e_phi|^2, |eta|^2, |phi|^2
+  double* d_part45 = nullptr; // its block partials
   std::map<std::string, void*> mixed;
   std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
@@ -116,10 +154,19 @@ struct Group {
 struct GraphEntry {
   double dt;
   bool prof;
+  int kind = 0;                      // StepKind
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
+  std::vector<cudaEvent_t> ev;       // profiled graphs: event pair per pass
+  std::vector<int> ev_family;
 };
+
+// What a captured graph runs: a whole step of a fixed-step scheme; or, for
+// the adaptive integrating factor, its six stages with the order-5 offsets
+// and the step's error norms (A), then the acceptance of the step (B).
+enum StepKind { SK_STEP = 0, SK_RK45_A = 1, SK_RK45_B = 2 };
+
 
 }  // namespace
 
@@ -142,11 +189,9 @@ struct sbi_ctx {
   int* d_flags = nullptr;  // [0]: non-finite state
   double* d_partials = nullptr;
   size_t partial_cap = 0;
-  std::vector<GraphEntry> graphs;
+  std::list<GraphEntry> graphs;   // stable addresses: two graphs may be held at once
   // profiling
   bool prof = false;
-  std::vector<cudaEvent_t> ev;        // pairs per profiled pass of the last captured step
-  std::vector<int> ev_family;
   std::vector<double> prof_ms;
   std::vector<long long> prof_launches;
   std::vector<int> orders_used;
@@ -158,6 +203,7 @@ struct sbi_ctx {
   std::map<std::string, Tuned> tuned;
   std::vector<std::string> tune_order;  // signatures in the order they were tuned
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  double dyn_h = NAN;   // the step the dynamic tables were last computed for
   // simulation time (advanced by sbi_step) and the pneumatic wavemaker
   double t_host = 0.0;
   double* d_time = nullptr;
@@ -221,6 +267,17 @@ struct Planner {
   // drops -g eta
   int if_stage = 0;
   std::string st_eta = "eta_m", st_phi = "phi_m";
+  // the physical working eta the row passes read (nullptr: g.eta_w); the
+  // adaptive scheme's stages 2..6 use their own, so that a rejected attempt
+  // leaves u_n's copy intact
+  void* st_eta_w = nullptr;
+  void* stage_eta_w() {
+    if (!g.eta_ws) {
+      g.eta_ws = dalloc(c, g.phys_elems() * g.n * c->real_size);
+      if (!g.eta_ws) oom = true;
+    }
+    return g.eta_ws;
+  }
 
   size_t vsize() const { return 2 * c->real_size; }
 
@@ -335,7 +392,7 @@ struct Planner {
   }
   Pass row_end(RowB& r, bool use_eta, bool use_delta, bool use_w) {
     if (use_eta) {
-      r.p.eta = pref(g.eta_w);
+      r.p.eta = pref(st_eta_w ? st_eta_w : g.eta_w);
       r.bytes += phys_bytes();
     }
     if (use_delta && g.variable) {
@@ -378,8 +435,12 @@ struct Planner {
   // Device table of a multiplier (created once per group and key).
   const void* table(const ColTerm& t) {
     char key[160];
-    snprintf(key, sizeof(key), "%.17g|%d|%d|%d|%d|%d|%.17g", t.c, t.kpow, t.depth, t.gx, t.gy, t.mask,
-             t.depth >= 4 ? t.tau : 0.0);
+    // dynamic tables (pad_ = 1 + p) depend on the step h: tau = r h with the
+    // ratio r in t.tau, coefficient t.c h^p; their values are written by
+    // update_dyn_tables whenever h changes
+    const bool dyn = t.pad_ != 0;
+    snprintf(key, sizeof(key), "%s%.17g|%d|%d|%d|%d|%d|%.17g", dyn ? (t.pad_ == 2 ? "h1|" : "h0|") : "",
+             t.c, t.kpow, t.depth, t.gx, t.gy, t.mask, (dyn || t.depth >= 4) ? t.tau : 0.0);
     auto it = g.tables.find(key);
     if (it != g.tables.end()) return it->second;
     void* p = dalloc(c, (size_t)g.W * g.ny * c->real_size);
@@ -405,9 +466,14 @@ struct Planner {
     s.gx = t.gx;
     s.gy = t.gy;
     s.mask = t.mask;
+    g.tables[key] = p;
+    if (dyn) {
+      g.dyn.push_back(DynTable{p, s, t.tau, t.pad_ - 1});
+      c->dyn_h = NAN;   // the new table has no values yet
+      return p;
+    }
     cudaError_t e = c->fp64 ? launch_coef_table<double>(p, s, c->cap) : launch_coef_table<float>(p, s, c->cap);
     if (e != cudaSuccess) oom = true;
-    g.tables[key] = p;
     return p;
   }
 
@@ -755,7 +821,8 @@ struct Planner {
   // cor_eta / cor_phi: the mixed corrections of RK_CORRECT / RK_OFFSET;
   // w_eta / w_phi: where the tail writes the mixed working copies
   Pass plan_rk(int mode, int stage, double dt, int tail, const char* cor_eta = "Ce",
-               const char* cor_phi = "Cp", const char* w_eta = "eta_m", const char* w_phi = "phi_m") {
+               const char* cor_phi = "Cp", const char* w_eta = "eta_m", const char* w_phi = "phi_m",
+               void* w_phys = nullptr) {
     RkParams p;
     std::memset(&p, 0, sizeof(p));
     p.mode = mode;
@@ -774,7 +841,7 @@ struct Planner {
     const bool corr = mode == RK_CORRECT || mode == RK_OFFSET;
     p.phit = mref(corr ? cor_eta : "phit");
     p.corr_phi = mref(cor_phi);
-    p.eta_w = pref(g.eta_w);
+    p.eta_w = pref(w_phys ? w_phys : g.eta_w);
     p.eta_hat = mref(w_eta);
     p.phi_hat = mref(w_phi);
     p.nonfinite = c->d_flags;
@@ -881,6 +948,72 @@ struct Planner {
     std::vector<ColIn> ins;
     for (const auto& name : order) ins.push_back({name, terms[name]});
     return col(ins, {{"De", term(0, 1.0, 0, 0, 0, 0, 1)}, {"Dp", term(1, 1.0, 0, 0, 0, 0, 1)}}, 2);
+  }
+
+  // Adaptive integrating factor, Cash-Karp 5(4) pair: mixed offsets from u_n
+  // (eta_m, phi_m) with the stored k_j = (Vnl<j>, phit<j>) (nx-normalised
+  // like in plan_if_combine), E(tau) from h-dependent tables:
+  //   target 2..6: stage state  (E(c_i h) - I) u_n + h sum_j a_ij E((c_i - c_j) h) k_j -> (De, Dp)
+  //   target 7:    order 5      (E(h) - I) u_n + h sum_j b5_j E((1 - c_j) h) k_j      -> (De, Dp)
+  //   target 8:    error        h sum_j (b5_j - b4_j) E((1 - c_j) h) k_j            -> (Ee, Ep)
+  Pass plan_ck_combine(int target) {
+    std::map<std::string, std::vector<ColTerm>> terms;
+    std::vector<std::string> order;
+    auto add = [&](const std::string& name, ColTerm t) {
+      if (!terms.count(name)) order.push_back(name);
+      terms[name].push_back(t);
+    };
+    auto dyn = [&](int acc, double cc, int depth, double r, int p) {
+      ColTerm t = term(acc, cc, 0, depth, 0, 0);
+      t.tau = r;
+      t.pad_ = (uint8_t)(1 + p);
+      return t;
+    };
+    const double ci = target <= 6 ? kCkC[target - 1] : 1.0;
+    if (target <= 7) {
+      add("eta_m", dyn(0, 1.0, 4, ci, 0));
+      add("eta_m", dyn(1, -1.0, 6, ci, 0));
+      add("phi_m", dyn(0, 1.0, 5, ci, 0));
+      add("phi_m", dyn(1, 1.0, 4, ci, 0));
+    }
+    const bool has_vnl = c->opt.order > 1 || c->opt.diagnostic == SBI_DIAG_HOS;
+    const int nj = target <= 6 ? target - 1 : 6;
+    for (int j = 1; j <= nj; ++j) {
+      const double w = target <= 6 ? kCkA[target - 1][j - 1]
+                                   : (target == 7 ? kCkB5[j - 1] : kCkB5[j - 1] - kCkB4[j - 1]);
+      if (w == 0.0) continue;
+      const double r = ci - kCkC[j - 1];
+      const double cc = w * g.nx;
+      const std::string ke = S("Vnl%d", j), kp = S("phit%d", j);
+      if (has_vnl) {
+        add(ke, dyn(0, cc, 7, r, 1));
+        add(ke, dyn(1, -cc, 6, r, 1));
+      }
+      add(kp, dyn(0, cc, 5, r, 1));
+      add(kp, dyn(1, cc, 7, r, 1));
+    }
+    std::vector<ColIn> ins;
+    for (const auto& name : order) ins.push_back({name, terms[name]});
+    const bool err = target == 8;
+    return col(ins, {{err ? "Ee" : "De", term(0, 1.0, 0, 0, 0, 0, 1)},
+                     {err ? "Ep" : "Dp", term(1, 1.0, 0, 0, 0, 0, 1)}}, 2);
+  }
+
+  // Per-member FP64 squared norms of the error (Ee, Ep) and of u_n (eta_m,
+  // phi_m) on the kept modes (Parseval weights).
+  Pass plan_norm45() {
+    if (!g.d_norm45) {
+      g.d_norm45 = (double*)dalloc(c, (size_t)g.n * 4 * sizeof(double));
+      g.d_part45 = (double*)dalloc(c, (size_t)g.n * kConvBlocks * 4 * sizeof(double));
+      if (!g.d_norm45 || !g.d_part45) oom = true;
+    }
+    Pass ps{};
+    ps.kind = PK_NORM;
+    ps.nsize = g.ny;
+    ps.norm = NormParams{mixed("Ee"), mixed("Ep"), mixed("eta_m"), mixed("phi_m"),
+                         (long long)g.mixed_elems(), g.W, g.ny, g.n, g.d_part45, g.d_norm45};
+    ps.bytes = mixed_bytes() * 4;
+    return ps;
   }
 
   void plan_sum_v(std::vector<Pass>& out, bool eulerian) {
@@ -1008,10 +1141,60 @@ __global__ void k_advance_time(double* t, double dt) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *t += dt;
 }
 
+// Step norms of the adaptive scheme: block partials in a fixed order, then
+// one thread per member sums the partials in block order.
+template <typename T>
+__global__ void k_norm45_partials(NormParams q) {
+  using V = cx<T>;
+  __shared__ double sm[4][256];
+  const int m = blockIdx.y;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long ne = (long long)q.W * q.ny;
+  const V* src[4] = {reinterpret_cast<const V*>(q.ee), reinterpret_cast<const V*>(q.ep),
+                     reinterpret_cast<const V*>(q.ue), reinterpret_cast<const V*>(q.up)};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double w = (e / q.ny) == 0 ? 1.0 : 2.0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const V v = src[f][m * q.stride + e];
+      acc[f] += w * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) sm[f][threadIdx.x] = acc[f];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) sm[f][threadIdx.x] += sm[f][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) q.part[((size_t)m * kConvBlocks + blockIdx.x) * 4 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_norm45_finish(NormParams q) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= q.n) return;
+  for (int f = 0; f < 4; ++f) {
+    double s = 0.0;
+    for (int b = 0; b < kConvBlocks; ++b) s += q.part[((size_t)m * kConvBlocks + b) * 4 + f];
+    q.out[m * 4 + f] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Execution
 // ---------------------------------------------------------------------------
 int launch_pass(sbi_ctx* c, const Pass& p, cudaStream_t st) {
+  if (p.kind == PK_NORM) {
+    const NormParams& q = p.norm;
+    if (c->fp64) k_norm45_partials<double><<<dim3(kConvBlocks, q.n), 256, 0, st>>>(q);
+    else k_norm45_partials<float><<<dim3(kConvBlocks, q.n), 256, 0, st>>>(q);
+    k_norm45_finish<<<(q.n + 127) / 128, 128, 0, st>>>(q);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SBI_OK : cuda_fail(c, e, "kernel launch");
+  }
   if (p.kind == PK_WMK) {
     const WmkParams& q = p.wmk;
     if (c->fp64) k_wavemaker<double><<<(q.nx + 255) / 256, 256, 0, st>>>(q);
@@ -1177,11 +1360,46 @@ int tune_pass(sbi_ctx* c, Pass& p, cudaStream_t st) {
 }
 
 // Passes of one step for each member group (groups are independent).
-std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom) {
+std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom, int kind = SK_STEP) {
   std::vector<std::vector<Pass>> out;
   for (auto& g : c->groups) {
     std::vector<Pass> all;
     Planner pl{c, g};
+    if (kind == SK_RK45_A) {
+      // six stages: the diagnostic and right-hand side of stage i give k_i;
+      // the offsets of stage i + 1 follow; then the order-5 offsets, the
+      // error offsets and the step norms
+      for (int s = 1; s <= 6; ++s) {
+        pl.if_stage = s;
+        pl.st_eta = s == 1 ? "eta_m" : "eta_s";
+        pl.st_phi = s == 1 ? "phi_m" : "phi_s";
+        pl.st_eta_w = s == 1 ? nullptr : pl.stage_eta_w();
+        pl.plan_diag(all);
+        pl.plan_rhs(all, 0.0);
+        pl.if_stage = 0;
+        pl.st_eta = "eta_m";
+        pl.st_phi = "phi_m";
+        pl.st_eta_w = nullptr;
+        if (s < 6) {
+          all.push_back(pl.plan_ck_combine(s + 1));
+          all.push_back(pl.plan_rk(RK_OFFSET, s, 0.0, 1, "De", "Dp", "eta_s", "phi_s", pl.stage_eta_w()));
+        }
+      }
+      all.push_back(pl.plan_ck_combine(7));
+      all.push_back(pl.plan_ck_combine(8));
+      all.push_back(pl.plan_norm45());
+      if (pl.oom) *oom = true;
+      out.push_back(std::move(all));
+      continue;
+    }
+    if (kind == SK_RK45_B) {
+      // accept the step: the order-5 offsets into the state
+      all.push_back(pl.plan_rk(RK_CORRECT, 4, 0.0, c->filter_on() ? 0 : 1, "De", "Dp"));
+      if (c->filter_on()) pl.plan_project(all, true);
+      if (pl.oom) *oom = true;
+      out.push_back(std::move(all));
+      continue;
+    }
     for (int s = 1; s <= 4; ++s) {
       const double t_off = (s == 1 ? 0.0 : (s == 4 ? 1.0 : 0.5)) * dt;  // stage times
       const int tail = (s < 4 || !c->filter_on()) ? 1 : 0;
@@ -1214,8 +1432,30 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
 
 std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
   std::vector<Pass> all;
+  if (c->opt.integrator == SBI_IF_RK45) {
+    for (int kind : {SK_RK45_A, SK_RK45_B})
+      for (auto& v : plan_step_groups(c, dt, oom, kind)) all.insert(all.end(), v.begin(), v.end());
+    return all;
+  }
   for (auto& v : plan_step_groups(c, dt, oom)) all.insert(all.end(), v.begin(), v.end());
   return all;
+}
+
+// Write the values of the h-dependent tables for the step h (stream-ordered
+// before the graph that reads them).
+int update_dyn_tables(sbi_ctx* c, double h, cudaStream_t st) {
+  if (h == c->dyn_h) return SBI_OK;
+  for (auto& g : c->groups)
+    for (const auto& d : g.dyn) {
+      TableSpec s = d.spec;
+      s.tau = d.r * h;
+      s.c = d.spec.c * (d.p ? h : 1.0);
+      const cudaError_t e = c->fp64 ? launch_coef_table<double>(d.ptr, s, st)
+                                    : launch_coef_table<float>(d.ptr, s, st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "table kernel");
+    }
+  c->dyn_h = h;
+  return SBI_OK;
 }
 
 int family_of(const Pass& p) {
@@ -1224,7 +1464,7 @@ int family_of(const Pass& p) {
     case PK_ROW: return FAM_ROW;
     case PK_RK: return FAM_RK;
     case PK_WMK: return FAM_WMK;
-    default: return FAM_CONV;
+    default: return FAM_CONV;   // adaptive-order tests and step norms
   }
 }
 
@@ -1232,18 +1472,16 @@ void free_graphs(sbi_ctx* c) {
   for (auto& ge : c->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
     if (ge.graph) cudaGraphDestroy(ge.graph);
+    for (auto e : ge.ev) cudaEventDestroy(e);
   }
   c->graphs.clear();
-  for (auto e : c->ev) cudaEventDestroy(e);
-  c->ev.clear();
-  c->ev_family.clear();
 }
 
-int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
+int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP) {
   for (auto& ge : c->graphs)
-    if (ge.dt == dt && ge.prof == c->prof) { *out = &ge; return SBI_OK; }
+    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind) { *out = &ge; return SBI_OK; }
   bool oom = false;
-  std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, &oom);
+  std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, &oom, kind);
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
   CK(cudaStreamSynchronize(c->stream), "sync before capture");
@@ -1255,16 +1493,19 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
     }
   size_t npasses = 0;
   for (auto& v : gps) npasses += v.size();
-  if (c->prof) {
-    free_graphs(c);  // a profiled graph owns the event pairs
+  GraphEntry ge;
+  ge.dt = dt;
+  ge.prof = c->prof;
+  ge.kind = kind;
+  if (c->prof) {   // the profiled graph owns one event pair per pass
     for (size_t gi = 0; gi < gps.size(); ++gi)
       for (size_t i = 0; i < gps[gi].size(); ++i) {
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a), "event");
         CK(cudaEventCreate(&b), "event");
-        c->ev.push_back(a);
-        c->ev.push_back(b);
-        c->ev_family.push_back(family_of(gps[gi][i]));
+        ge.ev.push_back(a);
+        ge.ev.push_back(b);
+        ge.ev_family.push_back(family_of(gps[gi][i]));
       }
   }
   // one branch per group: fork from the capture stream, join back
@@ -1278,9 +1519,6 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
     CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "event");
     c->gevents.push_back(e2);
   }
-  GraphEntry ge;
-  ge.dt = dt;
-  ge.prof = c->prof;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = SBI_OK;
   // the groups run as concurrent branches; a profiled replay runs them one
@@ -1293,9 +1531,9 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
     if (branch) cudaStreamWaitEvent(st, c->gevents[0], 0);
     for (size_t i = 0; i < gps[gi].size() && rc == SBI_OK; ++i, ++evi) {
       // external event records become timing nodes of the graph
-      if (c->prof) cudaEventRecordWithFlags(c->ev[2 * evi], st, cudaEventRecordExternal);
+      if (c->prof) cudaEventRecordWithFlags(ge.ev[2 * evi], st, cudaEventRecordExternal);
       rc = launch_pass(c, gps[gi][i], st);
-      if (c->prof) cudaEventRecordWithFlags(c->ev[2 * evi + 1], st, cudaEventRecordExternal);
+      if (c->prof) cudaEventRecordWithFlags(ge.ev[2 * evi + 1], st, cudaEventRecordExternal);
     }
     if (branch) {
       cudaEventRecord(c->gevents[gi + 1], st);
@@ -1303,19 +1541,48 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out) {
     }
   }
   // the simulation time of the next step (read by the wavemaker passes)
-  if (rc == SBI_OK && c->wm_n > 0) {
+  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP) {
     k_advance_time<<<1, 32, 0, c->cap>>>(c->d_time, dt);
     const cudaError_t el = cudaGetLastError();
     if (el != cudaSuccess) rc = cuda_fail(c, el, "kernel launch");
     else ++npasses;
   }
   cudaError_t e = cudaStreamEndCapture(c->cap, &ge.graph);
-  if (rc) return rc;
-  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-  CK(cudaGraphInstantiate(&ge.exec, ge.graph, 0), "graph instantiate");
+  auto drop_events = [&]() {
+    for (auto ev : ge.ev) cudaEventDestroy(ev);
+  };
+  if (rc) {
+    drop_events();
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    drop_events();
+    return cuda_fail(c, e, "end capture");
+  }
+  e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+  if (e != cudaSuccess) {
+    drop_events();
+    return cuda_fail(c, e, "graph instantiate");
+  }
   ge.launches = (int)npasses;
   c->graphs.push_back(ge);
   *out = &c->graphs.back();
+  return SBI_OK;
+}
+
+// Launch a captured graph; a profiled graph's event pairs are read back and
+// added to the per-family totals.
+int launch_graph(sbi_ctx* c, GraphEntry* ge) {
+  CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+  if (c->prof) {
+    CK(cudaStreamSynchronize(c->stream), "profile sync");
+    for (size_t q = 0; q < ge->ev_family.size(); ++q) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ge->ev[2 * q], ge->ev[2 * q + 1]), "event time");
+      c->prof_ms[ge->ev_family[q]] += ms;
+      c->prof_launches[ge->ev_family[q]] += 1;
+    }
+  }
   return SBI_OK;
 }
 
@@ -1459,13 +1726,13 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
   if (opt.filt_beta1 > 0.0 && !(opt.k_ref > 0.0 && opt.filt_beta2 > 0.0))
     return fail(nullptr, SBI_EINVAL, "filter needs k_ref > 0 and beta2 > 0");
   if (opt.adapt_tol < 0.0) return fail(nullptr, SBI_EINVAL, "adapt_tol must be >= 0");
-  if (opt.integrator != SBI_RK4 && opt.integrator != SBI_LAWSON_RK4)
-    return fail(nullptr, SBI_EINVAL, "integrator must be SBI_RK4 or SBI_LAWSON_RK4");
+  if (opt.integrator != SBI_RK4 && opt.integrator != SBI_LAWSON_RK4 && opt.integrator != SBI_IF_RK45)
+    return fail(nullptr, SBI_EINVAL, "integrator must be SBI_RK4, SBI_LAWSON_RK4 or SBI_IF_RK45");
   if (opt.diagnostic != SBI_DIAG_ESBI && opt.diagnostic != SBI_DIAG_HOS)
     return fail(nullptr, SBI_EINVAL, "diagnostic must be SBI_DIAG_ESBI or SBI_DIAG_HOS");
   if (opt.diagnostic == SBI_DIAG_HOS && opt.adapt_tol > 0.0)
     return fail(nullptr, SBI_EINVAL, "the HOS diagnostic is not combined with adapt_tol > 0");
-  if (opt.integrator == SBI_LAWSON_RK4 && opt.adapt_tol > 0.0)
+  if (opt.integrator != SBI_RK4 && opt.adapt_tol > 0.0)
     return fail(nullptr, SBI_EINVAL, "the integrating factor (integrator) is not combined with adapt_tol > 0");
   if ((opt.dev_alloc == nullptr) != (opt.dev_free == nullptr))
     return fail(nullptr, SBI_EINVAL, "dev_alloc and dev_free must be given together");
@@ -1859,22 +2126,105 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
   if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
   if (n == 0) return SBI_OK;
   GraphEntry* ge = nullptr;
-  int rc = get_step_graph(c, dt, &ge);
-  if (rc) return rc;
-  for (int i = 0; i < n; ++i) {
-    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
-    c->t_host += dt;
-    if (c->prof) {
-      // the graph's event pairs hold this replay's per-pass device times
-      CK(cudaStreamSynchronize(c->stream), "profile sync");
-      for (size_t q = 0; q < c->ev_family.size(); ++q) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[2 * q], c->ev[2 * q + 1]), "event time");
-        c->prof_ms[c->ev_family[q]] += ms;
-        c->prof_launches[c->ev_family[q]] += 1;
-      }
+  int rc = SBI_OK;
+  if (c->opt.integrator == SBI_IF_RK45) {
+    // fixed steps of the adaptive scheme: the order-5 solution, the error
+    // estimate not used
+    GraphEntry *ga = nullptr, *gb = nullptr;
+    rc = get_step_graph(c, 0.0, &ga, SK_RK45_A);
+    if (!rc) rc = get_step_graph(c, 0.0, &gb, SK_RK45_B);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+      rc = update_dyn_tables(c, dt, c->stream);
+      if (!rc) rc = launch_graph(c, ga);
+      if (!rc) rc = launch_graph(c, gb);
+      if (rc) return rc;
+      c->t_host += dt;
+    }
+  } else {
+    rc = get_step_graph(c, dt, &ge);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+      rc = launch_graph(c, ge);
+      if (rc) return rc;
+      c->t_host += dt;
     }
   }
+  if (c->opt.check_finite) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+    CK(cudaStreamSynchronize(c->stream), "step");
+    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
+  }
+  return SBI_OK;
+}
+
+// The step after an error err at step h (the controller of the adaptive
+// integrating factor).
+double next_step_size(double h, double err, double tol) {
+  if (err == 0.0) return 5.0 * h;
+  return h * std::min(5.0, std::max(0.2, 0.9 * std::pow(tol / err, 0.2)));
+}
+
+int sbi_step_adaptive(sbi_ctx* c, double t_end, double tol, double* h_inout, int* accepted,
+                      int* rejected) {
+  if (!c) return SBI_EINVAL;
+  if (c->opt.integrator != SBI_IF_RK45)
+    return fail(c, SBI_EINVAL, "sbi_step_adaptive needs integrator = SBI_IF_RK45");
+  if (!h_inout || !(*h_inout > 0.0) || !std::isfinite(*h_inout))
+    return fail(c, SBI_EINVAL, "the initial step must be finite and > 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, SBI_EINVAL, "tol must be finite and > 0");
+  if (!std::isfinite(t_end)) return fail(c, SBI_EINVAL, "t_end must be finite");
+  GraphEntry *ga = nullptr, *gb = nullptr;
+  int rc = get_step_graph(c, 0.0, &ga, SK_RK45_A);
+  if (!rc) rc = get_step_graph(c, 0.0, &gb, SK_RK45_B);
+  if (rc) return rc;
+  double t = c->t_host, h = *h_inout;
+  const double span = t_end - t;
+  int acc = 0, rej = 0;
+  std::vector<double> nrm;
+  while (t < t_end) {
+    const bool last = t + h >= t_end;
+    const double hh = last ? t_end - t : h;
+    rc = update_dyn_tables(c, hh, c->stream);
+    if (!rc) rc = launch_graph(c, ga);
+    if (rc) return rc;
+    // error: max over members and fields of ||u5 - u4|| / ||u_n||; the offsets
+    // are normalised for the inverse row transform, u_n's spectra are not
+    // (factor nx)
+    double err = 0.0;
+    for (auto& g : c->groups) {
+      nrm.resize((size_t)g.n * 4);
+      CK(cudaMemcpyAsync(nrm.data(), g.d_norm45, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream), "copy norms");
+      CK(cudaStreamSynchronize(c->stream), "step norms");
+      for (int m = 0; m < g.n; ++m)
+        for (int f = 0; f < 2; ++f) {
+          const double u = nrm[(size_t)m * 4 + 2 + f], e = nrm[(size_t)m * 4 + f];
+          if (u > 0.0) err = std::max(err, std::sqrt(e / u) * g.nx);
+          else if (!(e >= 0.0)) err = NAN;
+        }
+    }
+    if (!std::isfinite(err)) return fail(c, SBI_ENONFINITE, "the step error is not finite");
+    if (err <= tol) {
+      rc = launch_graph(c, gb);
+      if (rc) return rc;
+      ++acc;
+      t = last ? t_end : t + hh;
+      h = last ? std::max(h, next_step_size(hh, err, tol)) : next_step_size(hh, err, tol);
+    } else {
+      ++rej;
+      h = next_step_size(hh, err, tol);
+    }
+    if (h < 1e-12 * std::fabs(span) || acc + rej > 10000000) {
+      c->t_host = t;
+      return fail(c, SBI_ENOTCONVERGED, "step size underflow at t = %.17g (h = %g)", t, h);
+    }
+  }
+  c->t_host = t;
+  *h_inout = h;
+  if (accepted) *accepted = acc;
+  if (rejected) *rejected = rej;
   if (c->opt.check_finite) {
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
@@ -1945,6 +2295,8 @@ int sbi_set_wavemaker(sbi_ctx* c, int ncomp, const double* amp, const double* om
                       const double* phase, double x0) {
   if (!c) return SBI_EINVAL;
   if (ncomp < 0 || ncomp > 256) return fail(c, SBI_EINVAL, "ncomp must be in 0..256");
+  if (ncomp > 0 && c->opt.integrator == SBI_IF_RK45)
+    return fail(c, SBI_EINVAL, "the wavemaker is not combined with integrator = SBI_IF_RK45");
   if (ncomp > 0 && (!amp || !omega || !phase)) return fail(c, SBI_EINVAL, "amp, omega and phase must not be NULL");
   if (!std::isfinite(x0)) return fail(c, SBI_EINVAL, "x0 must be finite");
   for (int j = 0; j < ncomp; ++j)

@@ -17,7 +17,7 @@ from . import build as _build
 
 SBI_OK, SBI_EINVAL, SBI_ENOMEM, SBI_ECUDA, SBI_ENONFINITE, SBI_ENOTCONVERGED, SBI_ETIMEOUT = range(7)
 SBI_FP32, SBI_FP64 = 0, 1
-SBI_RK4, SBI_LAWSON_RK4 = 0, 1
+SBI_RK4, SBI_LAWSON_RK4, SBI_IF_RK45 = 0, 1, 2
 SBI_DIAG_ESBI, SBI_DIAG_HOS = 0, 1
 
 
@@ -73,6 +73,8 @@ EXPORTS = {
     "sbi_step_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sbi_step_transforms": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sbi_step_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sbi_step_adaptive": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sbi_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
@@ -278,6 +280,13 @@ class Context:
 
     def step(self, dt, n=1):
         self._check(self.lib.sbi_step(self.ctx, float(dt), int(n)))
+
+    def step_adaptive(self, t_end, tol, h):
+        """sbi_step_adaptive: returns (proposed next step, accepted, rejected)."""
+        hh, acc, rej = C.c_double(float(h)), C.c_int(), C.c_int()
+        self._check(self.lib.sbi_step_adaptive(self.ctx, float(t_end), float(tol), C.byref(hh),
+                                               C.byref(acc), C.byref(rej)))
+        return hh.value, acc.value, rej.value
 
     def invariants(self, member=0):
         m, e = C.c_double(), C.c_double()

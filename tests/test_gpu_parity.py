@@ -431,3 +431,85 @@ def test_hos_option_validation(sbi):
     with pytest.raises(sbi.SbiError) as ei:
         sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, diagnostic=5)
     assert ei.value.code == sbi.SBI_EINVAL
+
+
+RK45_CASES = {
+    "flat2d_filter": (64, 32, 6.0, 4.0, 0.8, False, True),
+    "var1d": (256, 1, 12.0, 1.0, 0.5, True, False),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("name", list(RK45_CASES))
+def test_rk45_fixed_steps_match_oracle(sbi, prec, tol, name):
+    # Fixed steps of the integrating factor with the 5(4) pair (order-5
+    # solution) against the oracle.
+    nx, ny, Lx, Ly, h0, variable, filt = RK45_CASES[name]
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, variable, seed=170)
+    kw = {}
+    if filt:
+        pb.filt_beta1, pb.filt_beta2, pb.k_ref = 8.0, 30.0, 1.0
+        kw.update(filt_beta1=8.0, filt_beta2=30.0, k_ref=1.0)
+    pb.integrator = "rk45"
+    eta, phi = O.project(pb, eta), O.project(pb, phi)
+    depth = [h0 - pb.delta] if variable else None
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, depth, h0=h0, precision=prec,
+                      integrator=sbi.SBI_IF_RK45, **kw)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.04, 3)
+    e, p = ctx.get_state(0)
+    eo, po = O.step(pb, eta, phi, 0.04, 3)
+    assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+def _rk45_adaptive_case():
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.7
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, True, seed=180, amp_eta=0.05)
+    pb.integrator = "rk45"
+    return (nx, ny, Lx, Ly, h0), grid, pb, eta, phi
+
+
+def test_rk45_adaptive_fp64_follows_the_oracle(sbi):
+    # The FP64 path takes the same accepted and rejected steps as the
+    # oracle's controller, proposes the same next step and ends in the same
+    # state at t_end.
+    (nx, ny, Lx, Ly, h0), grid, pb, eta, phi = _rk45_adaptive_case()
+    t_end, tol, h = 0.5, 1e-6, 0.2
+    eo, po, ho, acc_o, rej_o = O.step_adaptive(pb, eta, phi, 0.0, t_end, tol, h)
+    assert rej_o >= 1
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=1,
+                      integrator=sbi.SBI_IF_RK45)
+    ctx.set_state(0, eta, phi)
+    hg, acc, rej = ctx.step_adaptive(t_end, tol, h)
+    assert (acc, rej) == (acc_o, rej_o)
+    assert abs(hg - ho) < 1e-6 * ho
+    assert abs(ctx.get_time() - t_end) < 1e-15
+    e, p = ctx.get_state(0)
+    assert rel(e, eo) < 1e-9 and rel(p, po) < 1e-9
+
+
+def test_rk45_adaptive_fp32_reaches_t_end(sbi):
+    (nx, ny, Lx, Ly, h0), grid, pb, eta, phi = _rk45_adaptive_case()
+    out = {}
+    for prec in (1, 0):
+        ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec,
+                          integrator=sbi.SBI_IF_RK45)
+        ctx.set_state(0, eta, phi)
+        ctx.step_adaptive(0.5, 1e-6, 0.2)
+        assert abs(ctx.get_time() - 0.5) < 1e-15
+        out[prec] = ctx.get_state(0)
+    assert rel(out[0][0], out[1][0]) < 1e-5 and rel(out[0][1], out[1][1]) < 1e-5
+
+
+def test_rk45_option_validation(sbi):
+    ctx = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0, integrator=sbi.SBI_IF_RK45)
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.set_wavemaker([0.01], [3.0], [0.0])
+    assert ei.value.code == sbi.SBI_EINVAL
+    with pytest.raises(sbi.SbiError) as ei:
+        ctx.step_adaptive(1.0, -1.0, 0.1)
+    assert ei.value.code == sbi.SBI_EINVAL
+    plain = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=1.0)
+    with pytest.raises(sbi.SbiError) as ei:
+        plain.step_adaptive(1.0, 1e-6, 0.1)
+    assert ei.value.code == sbi.SBI_EINVAL
