@@ -2019,11 +2019,14 @@ int sbi_set_state_all(sbi_ctx* c, const double* eta, const double* phi, int on_d
     const double* srcs[2] = {eta, phi};
     double* dsts[2] = {g.eta0, g.phi0};
     for (int q = 0; q < 2; ++q) {
-      // gather the group's members into the staging buffer, then convert
-      for (int li = 0; li < g.n; ++li) {
-        const int m = g.members[li];
-        CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[m], np * 8, kind, c->cap),
-           "copy state");
+      // gather the group's members into the staging buffer (one copy per run
+      // of members that are consecutive in the caller's buffer), then convert
+      for (int li = 0; li < g.n;) {
+        int run = 1;
+        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+        CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[g.members[li]], np * 8 * run,
+                           kind, c->cap), "copy state");
+        li += run;
       }
       cudaError_t e = c->fp64 ? state_convert<double>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap)
                               : state_convert<float>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap);
@@ -2058,10 +2061,12 @@ int sbi_get_state_all(sbi_ctx* c, double* eta, double* phi, int on_device) {
       cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream)
                               : state_convert<float>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream);
       CK(e, "state conversion");
-      for (int li = 0; li < g.n; ++li) {
-        const int m = g.members[li];
-        CK(cudaMemcpyAsync(dsts[q] + off[m], g.stage64 + (size_t)li * np, np * 8, kind, c->stream),
-           "copy state");
+      for (int li = 0; li < g.n;) {   // one copy per run of consecutive members
+        int run = 1;
+        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+        CK(cudaMemcpyAsync(dsts[q] + off[g.members[li]], g.stage64 + (size_t)li * np, np * 8 * run,
+                           kind, c->stream), "copy state");
+        li += run;
       }
     }
   }
