@@ -154,9 +154,23 @@ struct StockhamPass {
       // full pass of radix R
       const int k = j & (Ls - 1);
       if constexpr (Ls > 1) {
+        const int base = k * (N / (Ls * R));
+        if constexpr (R == 8) {
+          // w^1 and w^4 from the table, the other powers by products (at most
+          // three roundings each): 2 loads instead of 7
+          const V w1 = twiddle<SIGN>(tw, N, base), w4 = twiddle<SIGN>(tw, N, 4 * base);
+          const V w2 = cmul(w1, w1), w3 = cmul(w1, w2);
+          x[1] = cmul(x[1], w1);
+          x[2] = cmul(x[2], w2);
+          x[3] = cmul(x[3], w3);
+          x[4] = cmul(x[4], w4);
+          x[5] = cmul(x[5], cmul(w4, w1));
+          x[6] = cmul(x[6], cmul(w4, w2));
+          x[7] = cmul(x[7], cmul(w4, w3));
+        } else {
 #pragma unroll
-        for (int r = 1; r < R; ++r)
-          x[r] = cmul(x[r], twiddle<SIGN>(tw, N, (r * k) * (N / (Ls * R))));
+          for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, N, r * base));
+        }
       }
       Dft<R, SIGN, V>::run(x);
       const int base = (j - k) * R + k;
@@ -180,8 +194,16 @@ struct StockhamPass {
         const int b = j + q * T;
 #pragma unroll
         for (int m = 0; m < RP; ++m) v[m] = x[q + m * Q];
+        if constexpr (RP == 4) {
+          // w^b from the table, w^2b and w^3b by products
+          const V w1 = twiddle<SIGN>(tw, N, b), w2 = cmul(w1, w1);
+          v[1] = cmul(v[1], w1);
+          v[2] = cmul(v[2], w2);
+          v[3] = cmul(v[3], cmul(w1, w2));
+        } else {
 #pragma unroll
-        for (int m = 1; m < RP; ++m) v[m] = cmul(v[m], twiddle<SIGN>(tw, N, m * b));
+          for (int m = 1; m < RP; ++m) v[m] = cmul(v[m], twiddle<SIGN>(tw, N, m * b));
+        }
         Dft<RP, SIGN, V>::run(v);
 #pragma unroll
         for (int m = 0; m < RP; ++m) s[pad(b + m * Ls)] = v[m];
