@@ -46,6 +46,20 @@ __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
+// exp(SIGN 2 pi i q / 16) for q = 0..7 (q a compile-time constant after
+// unrolling)
+template <int SIGN, typename V>
+__device__ __forceinline__ V root16(int q) {
+  using S = decltype(V::x);
+  constexpr double c[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                           0.38268343236508977173, 0.0, -0.38268343236508977173,
+                           -0.70710678118654752440, -0.92387953251128675613};
+  constexpr double s[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
+                           0.92387953251128675613, 1.0, 0.92387953251128675613,
+                           0.70710678118654752440, 0.38268343236508977173};
+  return mk<V>(S(c[q]), SIGN > 0 ? S(s[q]) : S(-s[q]));
+}
+
 // ---------------------------------------------------------------------------
 // Radix-R DFT in registers, R in {1, 2, 4, 8, 16}, y_q = sum_r x_r w_R^{r q}.
 // ---------------------------------------------------------------------------
@@ -103,17 +117,9 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
     for (int i = 0; i < 8; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
     Dft<8, SIGN, V>::run(e);
     Dft<8, SIGN, V>::run(o);
-    // cos(2 pi q / 16), sin(2 pi q / 16) for q = 0..7
-    const S c[8] = {S(1.0), S(0.92387953251128675613), S(0.70710678118654752440),
-                    S(0.38268343236508977173), S(0.0), S(-0.38268343236508977173),
-                    S(-0.70710678118654752440), S(-0.92387953251128675613)};
-    const S s[8] = {S(0.0), S(0.38268343236508977173), S(0.70710678118654752440),
-                    S(0.92387953251128675613), S(1.0), S(0.92387953251128675613),
-                    S(0.70710678118654752440), S(0.38268343236508977173)};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      V w = mk<V>(c[q], SIGN > 0 ? s[q] : -s[q]);
-      V t = q == 0 ? o[0] : cmul(o[q], w);
+      V t = q == 0 ? o[0] : cmul(o[q], root16<SIGN, V>(q));
       x[q] = cadd(e[q], t);
       x[q + 8] = csub(e[q], t);
     }

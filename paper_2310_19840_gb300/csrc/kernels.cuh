@@ -171,6 +171,9 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
                                           const cx<T>* __restrict__ tw) {
   using V = cx<T>;
   using C = RowCfg<NX>;
+  // e^{+2 pi i k / NX} = e^{+2 pi i j / NX} e^{+pi i r / R}: with R = 8 one
+  // table load and products by the 16th roots of unity
+  const V wj = cconj(__ldg(tw + tw_off(NX) + j));
 #pragma unroll
   for (int r = 0; r < C::R; ++r) {
     const int k = j + r * C::TPR;
@@ -179,7 +182,10 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
     const V b = (k > 0 && kk < W) ? stg[kk] : mk<V>(T(0), T(0));
     const V bc = cconj(b);
     const V E = cadd(a, bc);
-    const V O = cmul(csub(a, bc), cconj(__ldg(tw + tw_off(NX) + k)));
+    V w;
+    if constexpr (C::R == 8) w = r == 0 ? wj : cmul(wj, root16<1, V>(r));
+    else w = cconj(__ldg(tw + tw_off(NX) + k));
+    const V O = cmul(csub(a, bc), w);
     x[r] = cconj(cadd(E, rot<1>(O)));
   }
 }
