@@ -132,6 +132,12 @@ template <int SIGN, typename V> struct Dft<16, SIGN, V> {
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int tw_off(int n) { return n - 2; }
 
+// FP32 transforms form most twiddle powers by complex products of a few
+// table entries, which trades load/store-pipe work for FMA work; FP64
+// transforms load every power, because FP64 arithmetic is the scarcer
+// resource on this part.
+template <typename V> inline constexpr bool kProductTwiddles = sizeof(V) == 8;
+
 template <int SIGN, typename V>
 __device__ __forceinline__ V twiddle(const V* __restrict__ tw, int N, int idx) {
   V w = __ldg(tw + tw_off(N) + idx);
@@ -161,7 +167,7 @@ struct StockhamPass {
       const int k = j & (Ls - 1);
       if constexpr (Ls > 1) {
         const int base = k * (N / (Ls * R));
-        if constexpr (R == 8) {
+        if constexpr (R == 8 && kProductTwiddles<V>) {
           // w^1 and w^4 from the table, the other powers by products (at most
           // three roundings each): 2 loads instead of 7
           const V w1 = twiddle<SIGN>(tw, N, base), w4 = twiddle<SIGN>(tw, N, 4 * base);
@@ -200,7 +206,7 @@ struct StockhamPass {
         const int b = j + q * T;
 #pragma unroll
         for (int m = 0; m < RP; ++m) v[m] = x[q + m * Q];
-        if constexpr (RP == 4) {
+        if constexpr (RP == 4 && kProductTwiddles<V>) {
           // w^b from the table, w^2b and w^3b by products
           const V w1 = twiddle<SIGN>(tw, N, b), w2 = cmul(w1, w1);
           v[1] = cmul(v[1], w1);

@@ -171,9 +171,10 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
                                           const cx<T>* __restrict__ tw) {
   using V = cx<T>;
   using C = RowCfg<NX>;
-  // e^{+2 pi i k / NX} = e^{+2 pi i j / NX} e^{+pi i r / R}: with R = 8 one
-  // table load and products by the 16th roots of unity
-  const V wj = cconj(__ldg(tw + tw_off(NX) + j));
+  // e^{+2 pi i k / NX} = e^{+2 pi i j / NX} e^{+pi i r / R}: in FP32 with
+  // R = 8 one table load and products by the 16th roots of unity
+  constexpr bool kProd = C::R == 8 && kProductTwiddles<V>;
+  const V wj = kProd ? cconj(__ldg(tw + tw_off(NX) + j)) : mk<V>(T(1), T(0));
 #pragma unroll
   for (int r = 0; r < C::R; ++r) {
     const int k = j + r * C::TPR;
@@ -183,7 +184,7 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
     const V bc = cconj(b);
     const V E = cadd(a, bc);
     V w;
-    if constexpr (C::R == 8) w = r == 0 ? wj : cmul(wj, root16<1, V>(r));
+    if constexpr (kProd) w = r == 0 ? wj : cmul(wj, root16<1, V>(r));
     else w = cconj(__ldg(tw + tw_off(NX) + k));
     const V O = cmul(csub(a, bc), w);
     x[r] = cconj(cadd(E, rot<1>(O)));
