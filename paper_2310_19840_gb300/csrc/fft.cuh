@@ -42,6 +42,11 @@ template <int SIGN, typename V> __device__ __forceinline__ V rot(V a) {
 }
 
 __host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
+// Every index of a Stockham pass splits as pad(a + c) = pad(a) + pad(c) with
+// a run-time part a and a compile-time part c: c a multiple of a power of two
+// P > a (the gathers j + r T, j < T; the last pass's b + m Ls, b < Ls), or
+// a = (j - k) R + k with c = r Ls (a multiple of Ls R plus k < Ls).  pad(c)
+// then folds into the address of the shared-memory access.
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -185,13 +190,14 @@ struct StockhamPass {
         }
       }
       Dft<R, SIGN, V>::run(x);
-      const int base = (j - k) * R + k;
+      const int sb = pad((j - k) * R) + pad(k);   // pad((j - k) R + k + r Ls) - pad(r Ls)
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[pad(base + r * Ls)] = x[r];
+      for (int r = 0; r < R; ++r) s[sb + pad(r * Ls)] = x[r];
       group_sync<WARP>();
       if constexpr (Ls * R < N) {
+        const int lb = pad(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = s[pad(j + r * T)];
+        for (int r = 0; r < R; ++r) x[r] = s[lb + pad(r * T)];
         group_sync<WARP>();
         StockhamPass<N, R, Ls * R, SIGN, V>::run(x, s, j, tw);
       }
@@ -218,7 +224,7 @@ struct StockhamPass {
         }
         Dft<RP, SIGN, V>::run(v);
 #pragma unroll
-        for (int m = 0; m < RP; ++m) s[pad(b + m * Ls)] = v[m];
+        for (int m = 0; m < RP; ++m) s[pad(j) + pad(q * T) + pad(m * Ls)] = v[m];
       }
       group_sync<WARP>();
     }

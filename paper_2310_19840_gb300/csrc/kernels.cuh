@@ -361,7 +361,7 @@ k_row(const __grid_constant__ RowParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V z = cconj(fb[pad(m)]);
+        const V z = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
         slot[m] = z;
         if (out) out[m] = z;
       }
@@ -498,7 +498,7 @@ k_rk(const __grid_constant__ RkParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = cconj(fb[pad(m)]);
+        const V c = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
         SP e = act ? SP::load(E0, m) : SP::zero();
         e.add(0, c.x);
         e.add(1, c.y);
@@ -515,7 +515,7 @@ k_rk(const __grid_constant__ RkParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = cconj(fb[pad(m)]);
+        const V c = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
         SP q = act ? SP::load(P0, m) : SP::zero();
         q.add(0, c.x);
         q.add(1, c.y);
@@ -534,7 +534,7 @@ k_rk(const __grid_constant__ RkParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V ft = cconj(fb[pad(m)]);
+        const V ft = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
         xe[r] = mk<V>(T(0), T(0));
         xp[r] = mk<V>(T(0), T(0));
         if (!act) continue;
@@ -683,7 +683,7 @@ k_col(const __grid_constant__ ColParams p) {
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
         const int ni = j + r * TPC;
-        const V v = (NY > 1) ? sc[pad(ni)] : x[0];
+        const V v = (NY > 1) ? sc[pad(j) + pad(r * TPC)] : x[0];   // sc[pad(ni)]
         acc[ni] = cadd(acc[ni], cmul_ipow(v, __ldg(tab + ni), ph));
       }
     }
@@ -704,7 +704,7 @@ k_col(const __grid_constant__ ColParams p) {
       group_sync<C::WARP>();
       fft_block<NY, RC, -1>(x, sc, j, tw);
 #pragma unroll
-      for (int r = 0; r < RC; ++r) x[r] = cconj(sc[pad(j + r * TPC)]);
+      for (int r = 0; r < RC; ++r) x[r] = cconj(sc[pad(j) + pad(r * TPC)]);
     } else {
       x[0] = cconj(x[0]);
     }
