@@ -420,6 +420,40 @@ def test_hos_steps_match_oracle(sbi, prec, tol, integrator):
     assert rel(e, eo) < tol and rel(p, po) < tol
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("diag", ["esbi", "hos"])
+@pytest.mark.parametrize("order", [4, 7])
+def test_steep_stokes_wave(sbi, prec, diag, order):
+    # A steep steady Stokes wave (kH/2 = 0.35, deep water, one wavelength on
+    # 64 points, 16 alias-free modes), the comparison of the section on ESBI
+    # and HOS: the GPU V against the oracle's, and against the exact V = -c eta_x
+    # of a wave of permanent form (Fourier-approximation solution).
+    from oracle import steady_wave as SW
+    n, L = 64, 2 * math.pi
+    w = SW.solve(k=1.0, H=0.7, g=9.81)
+    grid = O.Grid(n, 1, L)
+    pb = O.Problem(grid, 9.81, math.inf)
+    x = np.arange(n) * L / n
+    eta, phi = O.project(pb, w.eta(x)), O.project(pb, w.surface_potential(x))
+    ctx = sbi.Context([(n, 1, L, 1.0)], 9.81, None, h0=math.inf, order=order, precision=prec,
+                      diagnostic=sbi.SBI_DIAG_HOS if diag == "hos" else sbi.SBI_DIAG_ESBI)
+    ctx.set_state(0, eta, phi)
+    V = np.asarray(ctx.vertical_velocity(0)).ravel()
+    if diag == "hos":
+        Vo = O.hos_surface_velocity(eta, phi, math.inf, grid, order=order)[0].ravel()
+    else:
+        Vo = O.vertical_velocity(eta, phi, None, math.inf, grid, order=order).ravel()
+    assert rel(V, Vo) < TOL[prec]
+    Vx = w.vertical_velocity(x)
+    err = np.max(np.abs(V - Vx)) / np.max(np.abs(Vx))
+    err_o = np.max(np.abs(Vo - Vx)) / np.max(np.abs(Vx))
+    assert abs(err - err_o) < 1e-4 * (1.0 if prec == 0 else 1e-4)
+    if order == 7 or diag == "esbi":
+        assert err < 5e-3       # within 0.5 %
+    else:
+        assert err > 5e-3       # HOS at order 4 is not
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:

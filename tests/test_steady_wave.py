@@ -1,0 +1,105 @@
+"""Pins of the steady-wave reference (oracle/steady_wave.py) and, through it,
+of the oracle's ESBI and HOS diagnostics against a fully nonlinear exact
+solution: the comparison of the section on ESBI and HOS (one wavelength on
+64 points, 16 alias-free modes, steepness up to 0.35, orders 1..7)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sbi_oracle as O
+from oracle import steady_wave as sw
+from laplace_dtn import exact_vertical_velocity
+
+G = 9.81
+
+
+def test_linear_limit():
+    # eps -> 0: Airy waves, c^2 = g tanh(kd) / k and eta = (H/2) cos kx
+    for depth in (math.inf, 1.0, 0.4):
+        k, eps = 2.0, 1e-3
+        w = sw.solve(k=k, H=2 * eps / k, depth=depth, g=G)
+        t = 1.0 if math.isinf(depth) else math.tanh(k * depth)
+        assert abs(w.c / math.sqrt(G * t / k) - 1.0) < 5 * eps ** 2
+        assert abs(w.E[1] / (eps / k) - 1.0) < 5 * eps ** 2
+        assert np.max(np.abs(w.E[2:])) < 5 * eps ** 2 / k
+
+
+def test_deep_water_speed_is_fourth_order_beyond_stokes():
+    # deep water: c = sqrt(g/k) (1 + eps^2 / 2 + O(eps^4)), eps = kH/2
+    r = {}
+    for eps in (0.05, 0.1):
+        w = sw.solve(k=1.0, H=2 * eps, g=G)
+        r[eps] = w.c / math.sqrt(G) - 1.0 - 0.5 * eps ** 2
+    assert 14.0 < r[0.1] / r[0.05] < 18.0
+
+
+def test_second_order_harmonic_finite_depth():
+    # second-order Stokes theory: a2 = k a1^2 (3 - s^2) / (4 s^3), s = tanh(kd)
+    k, d, eps = 1.0, 1.0, 0.01
+    w = sw.solve(k=k, H=2 * eps / k, depth=d, g=G)
+    s = math.tanh(k * d)
+    assert abs(w.E[2] / (k * w.E[1] ** 2) / ((3 - s * s) / (4 * s ** 3)) - 1.0) < 5e-3
+
+
+def test_conditions_hold_between_collocation_points():
+    for depth, eps in ((math.inf, 0.35), (1.0, 0.2)):
+        w = sw.solve(k=1.0, H=2 * eps, depth=depth, g=G)
+        x = np.linspace(0.0, 2 * math.pi, 997)
+        f1, f2 = w.surface_conditions(x)
+        assert np.max(np.abs(f1)) / (w.c / w.k) < 1e-7
+        assert np.max(np.abs(f2)) / (G / w.k) < 1e-7
+
+
+@pytest.mark.parametrize("kd,eps", [(1.0, 0.2), (2.0, 0.25), (0.5, 0.05)])
+def test_exact_velocity_matches_independent_laplace_solution(kd, eps):
+    # V = -c eta_x of the steady wave against a direct Laplace solution on
+    # the wave's own (eta, phi~): two independent methods
+    n, L = 64, 2 * math.pi
+    w = sw.solve(k=1.0, H=2 * eps, depth=kd, g=G)
+    x = np.arange(n) * L / n
+    V = exact_vertical_velocity(w.eta(x), w.surface_potential(x), None, kd, L, n_sigma=24)
+    Vx = w.vertical_velocity(x)
+    assert np.max(np.abs(V - Vx)) / np.max(np.abs(Vx)) < 1e-7
+
+
+def _errors(eps, n=64):
+    L = 2 * math.pi
+    w = sw.solve(k=1.0, H=2 * eps, g=G)
+    grid = O.Grid(n, 1, L)
+    x = np.arange(n) * L / n
+    eta, phi, Vx = w.eta(x), w.surface_potential(x), w.vertical_velocity(x)
+    scale = np.max(np.abs(Vx))
+    esbi, hos = [], []
+    for M in range(1, 8):
+        V = O.vertical_velocity(eta, phi, None, math.inf, grid, order=M).ravel()
+        Vh, _ = O.hos_surface_velocity(eta, phi, math.inf, grid, order=M)
+        esbi.append(np.max(np.abs(V - Vx)) / scale)
+        hos.append(np.max(np.abs(Vh.ravel() - Vx)) / scale)
+    return np.array(esbi), np.array(hos)
+
+
+def test_esbi_and_hos_against_steady_wave_steepest():
+    esbi, hos = _errors(0.35)
+    # both diagnostics are within 0.5 % at order 7 at the steepest wave
+    assert esbi[6] < 5e-3 and hos[6] < 5e-3
+    # ESBI is the more accurate of the two at every order
+    assert np.all(esbi < hos)
+    # 0.5 % is met by ESBI at order 4, not by HOS
+    assert esbi[3] < 5e-3 < hos[3]
+    # the first orders converge; above order 5 ESBI gains nothing more
+    assert esbi[0] > esbi[1] > esbi[2] and hos[0] > hos[1] > hos[2] > hos[3] > hos[4]
+    assert np.max(esbi[4:]) < 2.0 * np.min(esbi[4:])
+
+
+def test_esbi_converges_with_order_for_moderate_waves():
+    # at eps = 0.1 every order reduces the error; the seventh reaches 1e-8,
+    # so a wrong coefficient at any order 2..7 would show
+    esbi, hos = _errors(0.1)
+    assert np.all(np.diff(esbi) < 0) and np.all(np.diff(hos) < 0)
+    assert esbi[6] < 1e-8 and esbi[5] > 5 * esbi[6]
+
+
+def test_error_grows_with_steepness():
+    e7 = [_errors(eps)[0][6] for eps in (0.1, 0.2, 0.3, 0.35)]
+    assert np.all(np.diff(e7) > 0) and e7[-1] < 5e-3
