@@ -95,6 +95,27 @@ R12 HOS diagnostic (the section comparing ESBI and HOS, Eqs. HOS-HOSZ), flat
     are dealiased with the mask of R5 after their forward transform, and the
     ESBI quantity is V = W (1 + |grad eta|^2) - grad eta . grad phi~ (the
     kinematic condition), dealiased as well.
+R15 Implicit form (Appendix A, the "iterative approach" that the successive
+    scheme of Sec. 2.4 replaces), flat bottom only (delta = 0, so the bottom
+    potential of Appendix B drops out) and without the remaining integral
+    I^(S).  Every printed flat-bottom term of V^(2)..V^(7) has the form
+    C_h k c F{eta^a F^{-1}{ mult F{eta^b X} }} with m = j - 1 = a + b and
+    X = V or the vector grad phi~ under ik. (an a = 0 term has no inner
+    transform): for a term of grad phi~ when m is odd, or of V when m is even,
+    c = (-1)^{a+1}/(a! b!) and mult = C_h^{-1} (a even) or D_h^{-1} (a odd)
+    times k^{m-2} (grad phi~) or k^{m-1} (V); for a term of grad phi~ when m
+    is even, or of V when m is odd, c = 1/(a! b!) and mult = e_h k^{m-2}
+    (grad phi~) or e_h k^{m-1} (V); e_h = e^{-2kh}, C_h = 1/(1 + e_h),
+    D_h = 1/(1 - e_h); V^(1) = k tanh(kh) F{phi~}.  (Each printed term was
+    checked against this pattern.)  k^{-1} multiplies only ik.F{...} terms
+    and is 0 at k = 0 (R4).  Every forward transform is dealiased (R5).  The
+    equation F{V} = G + L(V) (G: V^(1) and the grad phi~ terms; L: the V
+    terms) is solved either by the fixed-point iteration
+    V_{n+1} = F^{-1}{G + L(V_n)} from V_0 = F^{-1}{V^(1)}, stopped when the
+    relative L2 change ||V_{n+1} - V_n|| / ||V_{n+1}|| is at most tol, or by
+    GMRES on (I - F^{-1} L) V = F^{-1} G from the same start (relative
+    residual tol, no restart), counting applications of L.  The paper does
+    not say which iteration its "iterative approach" uses.
 
 Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
 has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
@@ -313,6 +334,123 @@ def hos_surface_velocity(eta, phi, h0, grid: Grid, order: int = MAX_ORDER, alpha
     gp = gradient(phis[1], KX, KY, grid.dim)
     V = W * (1.0 + sum(a * a for a in ge)) - sum(a * b for a, b in zip(ge, gp))
     return ifft(mask * fft(V)), W
+
+
+# --------------------------------------------------------------------------
+# Implicit convolution form (Appendix A, flat bottom) by iteration (R15)
+# --------------------------------------------------------------------------
+
+def implicit_system(eta, phi, h0, grid: Grid, order: int = MAX_ORDER, alpha: float = 0.5):
+    """The implicit equations of Appendix A on a flat bottom of depth h0
+    (math.inf: deep water), reading R15, as F{V} = G + L(V): returns the
+    spectrum G driven by phi~ (V^(1) and the grad phi~ terms of V^(2..M)) and
+    the linear map L from a physical V to the spectrum of the V terms."""
+    if not 1 <= order <= MAX_ORDER:
+        raise ValueError("order must be in 1..7")
+    eta = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    t, _ = depth_multipliers(K, h0)
+    if math.isinf(h0):
+        e_h = np.zeros_like(K)
+    else:
+        e_h = np.exp(-2.0 * K * h0)
+    C = 1.0 / (1.0 + e_h)                   # C_h
+    X = (1.0 + e_h, 1.0 - e_h)              # C_h^{-1} (a even), D_h^{-1} (a odd)
+    image = bool(np.any(e_h > 0.0))
+
+    def kpow(p):
+        if p >= 0:
+            return K ** p if p > 0 else np.ones_like(K)
+        with np.errstate(divide="ignore"):
+            return np.where(K > 0, 1.0 / np.where(K > 0, K, 1.0) ** (-p), 0.0)
+
+    def outer(a, spec):                     # F{eta^a F^{-1}{spec}}, dealiased
+        return mask * spec if a == 0 else mask * fft(eta ** a * ifft(spec))
+
+    M1 = order - 1
+    phi_hat = mask * fft(phi)
+    grad_phi = gradient(phi_hat, KX, KY, grid.dim)
+    P = [mask * ik_dot([eta ** b * g for g in grad_phi], KX, KY) for b in range(M1 + 1)]
+    # the part driven by phi~: V^(1) and the grad phi~ terms of V^(2..M)
+    G = K * t * phi_hat
+    for m in range(1, M1 + 1):
+        for a in range(m + 1):
+            b = m - a
+            f = math.factorial(a) * math.factorial(b)
+            if m % 2 == 1:
+                mult = (-1.0) ** (a + 1) / f * X[a % 2] * kpow(m - 2)
+            elif image:
+                mult = e_h / f * kpow(m - 2)
+            else:
+                continue
+            G = G + C * K * outer(a, mult * P[b])
+
+    def implicit_part(Vp):                  # the V terms of V^(2..M)
+        Q = [mask * fft(eta ** b * Vp) for b in range(M1 + 1)]
+        out = np.zeros_like(G)
+        for m in range(1, M1 + 1):
+            for a in range(m + 1):
+                b = m - a
+                f = math.factorial(a) * math.factorial(b)
+                if m % 2 == 0:
+                    mult = (-1.0) ** (a + 1) / f * X[a % 2] * kpow(m - 1)
+                elif image:
+                    mult = e_h / f * kpow(m - 1)
+                else:
+                    continue
+                out = out + C * K * outer(a, mult * Q[b])
+        return out
+
+    return mask * G, lambda Vp: mask * implicit_part(np.asarray(Vp, dtype=np.float64).reshape(grid.ny, grid.nx))
+
+
+def implicit_vertical_velocity(eta, phi, h0, grid: Grid, order: int = MAX_ORDER,
+                               alpha: float = 0.5, tol: float = 1e-12, maxit: int = 200,
+                               solver: str = "fixed_point"):
+    """V from the implicit equations of Appendix A (flat bottom), reading R15,
+    by the fixed-point iteration (``solver="fixed_point"``) or by GMRES
+    (``solver="gmres"``), both from V_0 = V^(1).
+
+    Returns (V, applications, history): the number of applications of L and,
+    per application, the relative L2 change of the iterate (fixed point) or
+    the relative residual (GMRES)."""
+    G, L = implicit_system(eta, phi, h0, grid, order, alpha)
+    KX, KY, K = wavenumbers(grid)
+    t, _ = depth_multipliers(K, h0)
+    V = ifft(dealias_mask(grid, alpha) * K * t * fft(np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)))
+    if solver == "gmres":
+        import scipy.sparse.linalg as spla
+        shape = (grid.ny, grid.nx)
+        npts = grid.nx * grid.ny
+        count = [0]
+
+        def apply(v):
+            count[0] += 1
+            return v - ifft(L(v.reshape(shape))).ravel()
+
+        history = []
+        A = spla.LinearOperator((npts, npts), matvec=apply, dtype=np.float64)
+        sol, info = spla.gmres(A, ifft(G).ravel(), x0=V.ravel(), rtol=tol, atol=0.0,
+                               restart=min(npts, maxit), maxiter=1,
+                               callback=history.append, callback_type="pr_norm")
+        if info < 0:
+            raise RuntimeError("gmres failed")
+        return sol.reshape(shape), count[0], history
+    if solver != "fixed_point":
+        raise ValueError("solver must be 'fixed_point' or 'gmres'")
+    increments = []
+    n = 0
+    for n in range(1, maxit + 1):
+        with np.errstate(over="ignore", invalid="ignore"):
+            Vn = ifft(G + L(V))
+            inc = float(np.linalg.norm(Vn - V) / max(np.linalg.norm(Vn), 1e-300))
+        V = Vn
+        increments.append(inc)
+        if inc <= tol or not math.isfinite(inc):   # converged, or diverged
+            break
+    return V, n, increments
 
 
 # --------------------------------------------------------------------------

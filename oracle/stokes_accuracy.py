@@ -3,7 +3,9 @@ waves: the comparison of the section on ESBI and HOS (deep water, one
 wavelength on 64 points, 16 alias-free modes).  Prints, for each steepness
 kH/2 and order M = 1..7, the largest error of V divided by the largest |V|,
 the exact V being -c eta_x of the Fourier-approximation solution
-(oracle/steady_wave.py).
+(oracle/steady_wave.py); then, for the implicit form of Appendix A (reading
+R15), how its iterations behave against the steepness and how accurate its
+solution is beside the successive scheme's.
 
 TEST INFRASTRUCTURE: a documentation script that calls only ``oracle/``.
 Usage: python -m oracle.stokes_accuracy
@@ -34,6 +36,22 @@ def errors(eps: float, n: int = 64, g: float = 9.81):
     return esbi, hos
 
 
+def implicit(eps: float, n: int = 64, g: float = 9.81):
+    L = 2 * math.pi
+    w = sw.solve(k=1.0, H=2 * eps, g=g)
+    grid = O.Grid(n, 1, L)
+    x = np.arange(n) * L / n
+    eta, phi, Vx = w.eta(x), w.surface_potential(x), w.vertical_velocity(x)
+    scale = np.max(np.abs(Vx))
+    _, _, inc = O.implicit_vertical_velocity(eta, phi, math.inf, grid, tol=1e-6, maxit=12)
+    fixed = next((i + 1 for i, v in enumerate(inc) if v <= 1e-6), None)
+    _, a3, _ = O.implicit_vertical_velocity(eta, phi, math.inf, grid, tol=1e-3, solver="gmres")
+    V, a6, _ = O.implicit_vertical_velocity(eta, phi, math.inf, grid, tol=1e-6, solver="gmres")
+    Vs = O.vertical_velocity(eta, phi, None, math.inf, grid)
+    return (fixed, a3, a6, float(np.max(np.abs(V.ravel() - Vx)) / scale),
+            float(np.max(np.abs(Vs.ravel() - Vx)) / scale))
+
+
 def main():
     print("| kH/2 | diagnostic | " + " | ".join(f"M={m}" for m in range(1, 8)) + " |")
     print("|---|---|" + "---:|" * 7)
@@ -41,6 +59,13 @@ def main():
         e, h = errors(eps)
         print(f"| {eps} | ESBI | " + " | ".join(f"{v:.2e}" for v in e) + " |")
         print(f"| {eps} | HOS | " + " | ".join(f"{v:.2e}" for v in h) + " |")
+    print()
+    print("| kH/2 | fixed-point iterations to 1e-6 | GMRES applications to 1e-3 | to 1e-6 "
+          "| error of the implicit solution | error of the successive scheme (M = 7) |")
+    print("|---|---:|---:|---:|---:|---:|")
+    for eps in (0.1, 0.2, 0.3, 0.35):
+        f, a3, a6, ei, es = implicit(eps)
+        print(f"| {eps} | {f if f is not None else 'diverges'} | {a3} | {a6} | {ei:.2e} | {es:.2e} |")
 
 
 if __name__ == "__main__":
