@@ -1709,6 +1709,10 @@ int upload_real(sbi_ctx* c, void* dst, const std::vector<double>& v, size_t offs
   return SBI_OK;
 }
 
+// a member group (one concurrent branch of the step graph) holds at most
+// 1/kBranchShare of the batch's points unless one member is larger
+constexpr size_t kBranchShare = 3;
+
 int create_impl(int n, const sbi_grid* grids, double gravity, const double* const* h,
                 const sbi_options* opt_in, sbi_ctx** out) {
   if (!out) return fail(nullptr, SBI_EINVAL, "out is NULL");
@@ -1810,18 +1814,47 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
     return bail(SBI_ECUDA);
   }
 
-  // group members with identical grids and depth settings
+  // group members with identical grids and depth settings.  The groups run
+  // as concurrent graph branches, so a grid that holds more than a third of
+  // the batch's points is split into consecutive chunks of nearly equal size
+  // (one group each): the branches then carry similar work.
   c->where.resize(n);
+  std::vector<int> sig(n, -1), rank(n, 0);
+  std::vector<int> sig_count;
+  std::vector<size_t> sig_pts;
+  size_t total_pts = 0, max_member = 0;
   for (int i = 0; i < n; ++i) {
+    const size_t pts = (size_t)grids[i].nx * grids[i].ny;
+    total_pts += pts;
+    max_member = std::max(max_member, pts);
+    for (int j = 0; j < i && sig[i] < 0; ++j)
+      if (grids[j].nx == grids[i].nx && grids[j].ny == grids[i].ny && grids[j].Lx == grids[i].Lx &&
+          (grids[i].ny == 1 || grids[j].Ly == grids[i].Ly) && h0s[j] == h0s[i] && var[j] == var[i])
+        sig[i] = sig[j];
+    if (sig[i] < 0) {
+      sig[i] = (int)sig_count.size();
+      sig_count.push_back(0);
+      sig_pts.push_back(0);
+    }
+    rank[i] = sig_count[sig[i]]++;
+    sig_pts[sig[i]] += pts;
+  }
+  const size_t branch_cap = std::max(max_member, (total_pts + kBranchShare - 1) / kBranchShare);
+  std::vector<int> per_chunk(sig_count.size());
+  for (size_t q = 0; q < sig_count.size(); ++q) {
+    const int chunks = (int)std::min<size_t>((size_t)sig_count[q], (sig_pts[q] + branch_cap - 1) / branch_cap);
+    per_chunk[q] = (sig_count[q] + chunks - 1) / chunks;
+  }
+  std::vector<std::pair<int, int>> group_key;   // (signature, chunk) of each group
+  for (int i = 0; i < n; ++i) {
+    const std::pair<int, int> key{sig[i], rank[i] / per_chunk[sig[i]]};
     int gi = -1;
-    for (size_t q = 0; q < c->groups.size(); ++q) {
-      Group& g = c->groups[q];
-      if (g.nx == grids[i].nx && g.ny == grids[i].ny && g.Lx == grids[i].Lx &&
-          (grids[i].ny == 1 || g.Ly == grids[i].Ly) && g.h0 == h0s[i] && g.variable == var[i]) {
+    for (size_t q = 0; q < group_key.size(); ++q)
+      if (group_key[q] == key) {
         gi = (int)q;
         break;
       }
-    }
+    if (gi < 0) group_key.push_back(key);
     if (gi < 0) {
       Group g;
       g.nx = grids[i].nx;
