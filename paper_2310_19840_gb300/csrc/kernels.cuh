@@ -447,8 +447,19 @@ template <> struct StatePair<float> {
 // ===========================================================================
 // RK4 stage pass (row layout).  State and sums in StatePair<T> storage.
 // ===========================================================================
+// RK stage geometry: blocks of kRkThreads threads (a whole row when a row
+// needs more); three resident blocks per SM in FP32 (at most 85 registers),
+// two in FP64 (128).
+template <int NX>
+struct RkCfg {
+  static constexpr int RPC = cmax(1, kRkThreads / RowCfg<NX>::TPR);
+  static constexpr int THREADS = RowCfg<NX>::TPR * RPC;
+  template <typename T>
+  static constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+};
+
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::MAX_THREADS)
+__global__ void __launch_bounds__(RkCfg<NX>::THREADS, RkCfg<NX>::template min_blocks<T>())
 k_rk(const __grid_constant__ RkParams p) {
   using V = cx<T>;
   using C = RowCfg<NX>;
@@ -838,7 +849,7 @@ cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
 template <typename T, int NX>
 cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
-  if (p.rpc < 1 || p.rpc > C::RPC_MAX) return cudaErrorInvalidValue;
+  if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
   k_rk<T, NX><<<blocks, C::TPR * p.rpc, sizeof(cx<T>) * (size_t)p.rpc * C::FBUF, st>>>(p);
   return cudaGetLastError();

@@ -831,7 +831,10 @@ struct Planner {
     p.rows_total = g.n * g.ny;
     p.ny = g.ny;
     p.W = g.W;
-    p.rpc = rpc_for(0);
+    {
+      const int tpr = c->fp64 ? row_tpr<double>(g.nx) : row_tpr<float>(g.nx);
+      p.rpc = std::max(1, kRkThreads / std::max(1, tpr));
+    }
     p.dt = dt;
     p.eta0 = dref(g.eta0);
     p.phi0 = dref(g.phi0);

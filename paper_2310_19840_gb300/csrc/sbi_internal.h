@@ -29,6 +29,8 @@ constexpr int kMaxColTerms = 48;
 constexpr int kMaxColOuts = 12;
 constexpr int kMaxColBufs = 32;
 constexpr int kMaxColAcc = 2;
+// threads of an RK stage block: rows per block = max(1, kRkThreads / threads per row)
+constexpr int kRkThreads = 256;
 constexpr int kMaxSlots = 5;
 constexpr uint8_t kNone = 255;
 
