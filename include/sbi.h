@@ -156,11 +156,14 @@ int sbi_get_state(sbi_ctx* ctx, int member, double* eta, double* phi, int on_dev
  * sum over members of nx*ny doubles: member 0's field (row-major), then
  * member 1's, and so on, in member order.  The result is the same as one
  * sbi_set_state / sbi_get_state per member; the work is batched per member
- * group (one staging buffer of the group's size, allocated on first use and
- * kept, one conversion and one dealias pass per group) and the stream is
- * synchronized once.  Host buffers in pinned memory make the copies
- * asynchronous DMA.  The paper has no counterpart (the calls batch its
- * per-problem initial condition and output). */
+ * group (one conversion launch per run of members that are consecutive in
+ * the buffer, one dealias pass per group) and the stream is synchronized
+ * once.  Device buffers (on_device = 1) and host buffers that the device can
+ * address (pinned, mapped memory) are read and written by the conversion
+ * kernels themselves; other host buffers go through a staging buffer of the
+ * group's size (allocated on first use and kept) by copies.  The paper has
+ * no counterpart (the calls batch its per-problem initial condition and
+ * output). */
 int sbi_set_state_all(sbi_ctx* ctx, const double* eta, const double* phi, int on_device);
 int sbi_get_state_all(sbi_ctx* ctx, double* eta, double* phi, int on_device);
 

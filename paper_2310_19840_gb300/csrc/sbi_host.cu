@@ -2036,6 +2036,21 @@ std::vector<size_t> member_offsets(const sbi_ctx* c) {
   return off;
 }
 
+// The device address of a caller's buffer that kernels can read and write
+// directly: device memory (on_device), or host memory that is pinned and
+// mapped (on this system it is reached over the host link); nullptr when the
+// buffer must go through a copy.
+double* device_view(void* p, int on_device) {
+  if (on_device) return static_cast<double*>(p);
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<double*>(a.devicePointer);
+  return nullptr;
+}
+
 int ensure_stage(sbi_ctx* c, Group& g) {
   if (!g.stage64) g.stage64 = (double*)dalloc(c, g.phys_elems() * g.n * 8);
   return g.stage64 ? SBI_OK : fail(c, SBI_ENOMEM, "device allocation failed");
@@ -2047,26 +2062,34 @@ int sbi_set_state_all(sbi_ctx* c, const double* eta, const double* phi, int on_d
   const std::vector<size_t> off = member_offsets(c);
   CK(cudaStreamSynchronize(c->stream), "sync");
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const double* srcs[2] = {eta, phi};
+  const double* views[2] = {device_view(const_cast<double*>(eta), on_device),
+                            device_view(const_cast<double*>(phi), on_device)};
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     Group& g = c->groups[gi];
-    int rc = ensure_stage(c, g);
-    if (rc) return rc;
     const size_t np = g.phys_elems();
-    const double* srcs[2] = {eta, phi};
     double* dsts[2] = {g.eta0, g.phi0};
     for (int q = 0; q < 2; ++q) {
-      // gather the group's members into the staging buffer (one copy per run
-      // of members that are consecutive in the caller's buffer), then convert
+      // per run of members that are consecutive in the caller's buffer: the
+      // conversion kernel reads the caller's buffer itself when it can, else
+      // the run is copied into the staging buffer and converted from there
+      if (!views[q]) {
+        int rc = ensure_stage(c, g);
+        if (rc) return rc;
+      }
       for (int li = 0; li < g.n;) {
         int run = 1;
         while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
-        CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[g.members[li]], np * 8 * run,
-                           kind, c->cap), "copy state");
+        const double* from = views[q] ? views[q] + off[g.members[li]] : g.stage64 + (size_t)li * np;
+        if (!views[q])
+          CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[g.members[li]], np * 8 * run,
+                             kind, c->cap), "copy state");
+        void* to = reinterpret_cast<char*>(dsts[q]) + (size_t)li * np * 8;   // 8 bytes per stored value
+        cudaError_t e = c->fp64 ? state_convert<double>(from, to, (long long)(np * run), false, c->cap)
+                                : state_convert<float>(from, to, (long long)(np * run), false, c->cap);
+        CK(e, "state conversion");
         li += run;
       }
-      cudaError_t e = c->fp64 ? state_convert<double>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap)
-                              : state_convert<float>(g.stage64, dsts[q], (long long)(np * g.n), false, c->cap);
-      CK(e, "state conversion");
     }
     // dealias (or only refresh the working copies of) every member of the group
     Planner pl{c, g};
@@ -2074,7 +2097,7 @@ int sbi_set_state_all(sbi_ctx* c, const double* eta, const double* phi, int on_d
     if (c->opt.set_state_dealias) pl.plan_project(ps, false);
     else ps.push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
     if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
-    rc = run_passes(c, ps, c->cap);
+    const int rc = run_passes(c, ps, c->cap);
     if (rc) return rc;
   }
   CK(cudaStreamSynchronize(c->cap), "set_state_all");
@@ -2086,14 +2109,30 @@ int sbi_get_state_all(sbi_ctx* c, double* eta, double* phi, int on_device) {
   if (!eta || !phi) return fail(c, SBI_EINVAL, "eta and phi must not be NULL");
   const std::vector<size_t> off = member_offsets(c);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* dsts[2] = {eta, phi};
+  double* views[2] = {device_view(eta, on_device), device_view(phi, on_device)};
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     Group& g = c->groups[gi];
-    int rc = ensure_stage(c, g);
-    if (rc) return rc;
     const size_t np = g.phys_elems();
     const double* srcs[2] = {g.eta0, g.phi0};
-    double* dsts[2] = {eta, phi};
     for (int q = 0; q < 2; ++q) {
+      if (views[q]) {
+        // the conversion kernel writes the caller's buffer itself, one
+        // launch per run of consecutive members
+        for (int li = 0; li < g.n;) {
+          int run = 1;
+          while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+          const void* from = reinterpret_cast<const char*>(srcs[q]) + (size_t)li * np * 8;
+          cudaError_t e = c->fp64
+              ? state_convert<double>(from, views[q] + off[g.members[li]], (long long)(np * run), true, c->stream)
+              : state_convert<float>(from, views[q] + off[g.members[li]], (long long)(np * run), true, c->stream);
+          CK(e, "state conversion");
+          li += run;
+        }
+        continue;
+      }
+      int rc = ensure_stage(c, g);
+      if (rc) return rc;
       cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream)
                               : state_convert<float>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream);
       CK(e, "state conversion");

@@ -164,10 +164,14 @@ def test_autotuned_block_shapes_give_identical_results(sbi, prec):
             assert np.array_equal(out[0][m][f], out[1][m][f])
 
 
+@pytest.mark.parametrize("buf", ["numpy", "pinned", "device"])
 @pytest.mark.parametrize("dealias", [0, 1])
-def test_batch_state_calls_equal_per_member_calls(sbi, dealias):
+def test_batch_state_calls_equal_per_member_calls(sbi, dealias, buf):
     # sbi_set_state_all / sbi_get_state_all on members of interleaved sizes
-    # give the same bits as one sbi_set_state / sbi_get_state per member.
+    # give the same bits as one sbi_set_state / sbi_get_state per member, from
+    # pageable host buffers (copied through staging), pinned host buffers and
+    # device buffers (read and written by the conversion kernels directly).
+    import torch
     specs = [(64, 32, 6.0, 4.0), (32, 16, 3.0, 2.0), (64, 32, 6.0, 4.0), (128, 1, 9.0, 1.0)]
     eta = [W.random_field(nx, ny, 80 + i, amplitude=0.03).ravel() for i, (nx, ny, _, _) in enumerate(specs)]
     phi = [W.random_field(nx, ny, 90 + i, amplitude=0.2).ravel() for i, (nx, ny, _, _) in enumerate(specs)]
@@ -175,10 +179,22 @@ def test_batch_state_calls_equal_per_member_calls(sbi, dealias):
     b = sbi.Context(specs, 9.81, None, h0=0.7, precision=0, set_state_dealias=dealias)
     for i in range(len(specs)):
         a.set_state(i, eta[i], phi[i])
-    b.set_state_all(np.concatenate(eta), np.concatenate(phi))
+
+    def wrap(x):
+        if buf == "numpy":
+            return x
+        t = torch.from_numpy(np.ascontiguousarray(x))
+        return t.pin_memory() if buf == "pinned" else t.cuda()
+
+    b.set_state_all(wrap(np.concatenate(eta)), wrap(np.concatenate(phi)))
     for ctx in (a, b):
         ctx.step(0.01, 2)
     ea, pa = a.get_state_all()
+    if buf != "numpy":
+        eb, pb_ = wrap(np.zeros_like(ea)), wrap(np.zeros_like(pa))
+        b.get_state_all(eb, pb_)
+        torch.cuda.synchronize()
+        assert np.array_equal(eb.cpu().numpy(), ea) and np.array_equal(pb_.cpu().numpy(), pa)
     for i in range(len(specs)):
         e1, p1 = a.get_state(i)
         e2, p2 = b.get_state(i)
