@@ -470,6 +470,34 @@ def test_steep_stokes_wave(sbi, prec, diag, order):
         assert err > 5e-3       # HOS at order 4 is not
 
 
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("depth,eps", [(math.inf, 0.3), (2.0, 0.2)])
+def test_steady_stokes_wave_translates(sbi, prec, tol, depth, eps):
+    # A steady Stokes wave stepped a quarter period on the GPU: the state
+    # matches the oracle's and the exactly translated wave (phi~ up to its
+    # uniform Bernoulli drift).
+    from oracle import steady_wave as SW
+    n, L, g = 64, 2 * math.pi, 9.81
+    w = SW.solve(k=1.0, H=2 * eps, depth=depth, g=g)
+    grid = O.Grid(n, 1, L)
+    pb = O.Problem(grid, g, depth)
+    x = np.arange(n) * L / n
+    eta0, phi0 = O.project(pb, w.eta(x)), O.project(pb, w.surface_potential(x))
+    dt = L / w.c / 64
+    ctx = sbi.Context([(n, 1, L, 1.0)], g, None, h0=depth, precision=prec)
+    ctx.set_state(0, eta0, phi0)
+    ctx.step(dt, 16)
+    e, p = (np.ravel(a) for a in ctx.get_state(0))
+    eo, po = (np.ravel(a) for a in O.step(pb, eta0, phi0, dt, 16))
+    assert rel(e, eo) < tol and rel(p, po) < tol
+    t = 16 * dt
+    ex = np.ravel(O.project(pb, w.eta(x - w.c * t)))
+    px = np.ravel(O.project(pb, w.surface_potential(x - w.c * t)))
+    assert np.max(np.abs(e - ex)) < 2e-4 * np.max(np.abs(ex))
+    d = (p - p.mean()) - (px - px.mean())
+    assert np.max(np.abs(d)) < 2e-4 * np.max(np.abs(px - px.mean()))
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:

@@ -103,3 +103,30 @@ def test_esbi_converges_with_order_for_moderate_waves():
 def test_error_grows_with_steepness():
     e7 = [_errors(eps)[0][6] for eps in (0.1, 0.2, 0.3, 0.35)]
     assert np.all(np.diff(e7) > 0) and e7[-1] < 5e-3
+
+
+@pytest.mark.parametrize("depth,eps", [(math.inf, 0.3), (2.0, 0.2), (1.0, 0.1)])
+def test_oracle_steps_translate_the_steady_wave(depth, eps):
+    # Stepped a quarter period (RK4, dt = T/64), the wave must be the steady
+    # wave shifted by c t.  phi~ also gains the uniform -(R - c^2/2) t: the
+    # Bernoulli constant of the fixed frame, which the dynamic condition of
+    # Sec. 2.2 leaves out (only grad phi~ enters the dynamics).
+    n, L = 64, 2 * math.pi
+    w = sw.solve(k=1.0, H=2 * eps, depth=depth, g=G)
+    grid = O.Grid(n, 1, L)
+    pb = O.Problem(grid, G, depth)
+    x = np.arange(n) * L / n
+    eta0, phi0 = O.project(pb, w.eta(x)), O.project(pb, w.surface_potential(x))
+    dt = L / w.c / 64
+    eta, phi = (np.ravel(a) for a in O.step(pb, eta0, phi0, dt, 16))
+    t = 16 * dt
+    ex = np.ravel(O.project(pb, w.eta(x - w.c * t)))
+    px = np.ravel(O.project(pb, w.surface_potential(x - w.c * t)))
+    assert np.max(np.abs(eta - ex)) < 2e-4 * np.max(np.abs(ex))
+    d = (phi - phi.mean()) - (px - px.mean())
+    assert np.max(np.abs(d)) < 2e-4 * np.max(np.abs(px - px.mean()))
+    drift = phi.mean() - px.mean()
+    C = (w.R - 0.5 * w.c ** 2) * t
+    assert abs(drift + C) < 1e-3 * abs(C) + 1e-5 * np.max(np.abs(px - px.mean()))
+    # the wave did move: a quarter wavelength changes eta by O(1)
+    assert np.max(np.abs(np.ravel(eta0) - ex)) > 0.5 * np.max(np.abs(ex))
