@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64 plain-path timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-diagnostics", action="store_true",
+                    help="instead of the step: time one V evaluation of the first member group by "
+                         "the successive scheme and by the implicit form of Appendix A "
+                         "(per fixed-point iteration), and print that JSON line")
     ap.add_argument("--members", default=None,
                     help="crossing_batch only: 'S,L' small (256^2) and large (512^2) members "
                          "instead of 64,32 (for profiling runs)")
@@ -227,6 +231,37 @@ def make_context(sbi, wl, precision, stream, **extra):
     return ctx
 
 
+def compare_diagnostics(ctx, wl, torch, args):
+    """Wall time of one V evaluation of member 0's group (every call queues
+    the whole group's passes and synchronises): the successive scheme of
+    Sec. 2.4 against the implicit form of Appendix A, whose cost per
+    fixed-point iteration is the slope between 1 and 11 iterations."""
+    def t(f, k=10):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k * 1e3
+    m0 = wl.members[0]
+    n_group = sum(1 for m in wl.members if (m.nx, m.ny) == (m0.nx, m0.ny))
+    esbi = t(lambda: ctx.vertical_velocity(0))
+    one = t(lambda: ctx.vertical_velocity_implicit(0, 1))
+    eleven = t(lambda: ctx.vertical_velocity_implicit(0, 11))
+    per_it = (eleven - one) / 10.0
+    _, inc = ctx.vertical_velocity_implicit(0, 11)
+    return {"metric": "V evaluation time of one member group", "unit": "ms",
+            "config": {"workload": wl.name, "grid": f"{m0.nx}x{m0.ny}", "order": wl.order,
+                       "members_of_that_grid": n_group,
+                       "evaluated": "the member group holding member 0"},
+            "esbi_successive_ms": esbi, "implicit_1_iteration_ms": one,
+            "implicit_ms_per_iteration": per_it, "implicit_setup_ms": one - per_it,
+            "implicit_increments_11": [float(v) for v in inc],
+            "note": "wall time per call including the copy of one member's V to the host"}
+
+
 def time_steps(ctx, torch, stream, dt, steps, warmup):
     for _ in range(warmup):
         ctx.step(dt, 1)
@@ -331,6 +366,10 @@ def main():
     ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag)
     for i, m in enumerate(wl.members):
         ctx.set_state(i, m.eta, m.phi)
+    if args.compare_diagnostics:
+        if rank == 0:
+            print(json.dumps(compare_diagnostics(ctx, wl, torch, args)))
+        return
     launches = ctx.step_launches()
     bytes_step = ctx.step_bytes(-1)
 

@@ -764,7 +764,11 @@ __global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
   if (s.kpow < 0) kp = k > 0.0 ? 1.0 / kp : 0.0;
   double f = s.c * kp;
   double d = s.depth == 1 ? tk : (s.depth == 2 ? sk : (s.depth == 3 ? lam : 1.0));
-  if (s.depth >= 4) {
+  if (s.depth >= 8) {
+    // factors of the implicit form of Appendix A: e_h = e^{-2 k h0}
+    const double eh = isinf(s.h0) ? 0.0 : exp(-2.0 * k * s.h0);
+    d = s.depth == 8 ? 1.0 + eh : (s.depth == 9 ? 1.0 - eh : (s.depth == 10 ? eh : 1.0 / (1.0 + eh)));
+  } else if (s.depth >= 4) {
     // entries of e^{A tau}; cos - 1 as -2 sin^2(w tau / 2) (no cancellation)
     const double w = sqrt(s.gravity * k * tk);
     const double wt = w * s.tau, sh = sin(0.5 * wt);

@@ -27,6 +27,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <list>
 #include <map>
 #include <string>
@@ -145,6 +146,7 @@ struct Group {
   std::vector<DynTable> dyn; // h-dependent propagator tables (adaptive scheme)
   double* d_norm45 = nullptr; // adaptive scheme: per member |e_eta|^2, |e_phi|^2, |eta|^2, |phi|^2
   double* d_part45 = nullptr; // its block partials
+  double* d_implicit = nullptr; // implicit form: per iteration and member |V_new - V_old|^2, |V_new|^2 (lazy)
   std::map<std::string, void*> mixed;
   std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
@@ -1030,6 +1032,116 @@ struct Planner {
     }
     out.push_back(row_end(r, false, false, false));
   }
+
+  // Implicit form of Appendix A on a flat bottom (the iteration the
+  // successive scheme replaces).  Every term of V^(2..M) is
+  // C_h k c F{eta^a F^{-1}{mult F{eta^b X}}}, m = a + b, X = V or (under ik.)
+  // grad phi~: for X = grad phi~ with m odd, or X = V with m even,
+  // c = (-1)^{a+1}/(a! b!) and mult = C_h^{-1} (a even) or D_h^{-1} (a odd)
+  // times k^{m-2} (grad phi~) or k^{m-1} (V); otherwise c = 1/(a! b!) and
+  // mult = e_h k^{m-2} or e_h k^{m-1}, e_h = e^{-2kh} (zero in deep water).
+  // The inner spectra S_a = sum_b c mult F{eta^b X} are formed by column
+  // passes (two per pass), the products eta^a F^{-1}{S_a} by a row pass and
+  // the outer C_h k sum by a last column pass.  F{V} = G + L(V): G (V^(1) and
+  // the grad phi~ terms) once, L(V) per iteration.
+  bool implicit_term(int acc, int a, int b, bool of_v, int gx, int gy, ColTerm* t) const {
+    const int m = a + b;
+    if (m == 0) return false;
+    const bool direct = of_v ? (m % 2 == 0) : (m % 2 == 1);
+    const int kp = of_v ? m - 1 : m - 2;
+    const double f = fact(a) * fact(b);
+    if (direct) {
+      *t = term(acc, ((a % 2) ? 1.0 : -1.0) / f, kp, (a % 2) ? 9 : 8, gx, gy, 1);
+      return true;
+    }
+    if (g.deep) return false;
+    *t = term(acc, 1.0 / f, kp, 10, gx, gy, 1);
+    return true;
+  }
+  // Inner spectra IS<a> (prefix) from the inputs src(b, d) for a = 0..M-1;
+  // returns which a have any term.
+  std::vector<bool> plan_implicit_inner(std::vector<Pass>& out, bool of_v, const std::string& prefix,
+                                        const std::function<std::string(int, char)>& src) {
+    const int M1 = c->opt.order - 1;
+    std::vector<bool> has(M1 + 1, false);
+    const std::vector<char> ds = of_v ? std::vector<char>{'s'} : dims();
+    for (int a0 = 0; a0 <= M1; a0 += 2) {
+      std::vector<ColIn> ins;
+      bool used[2] = {false, false};
+      for (int b = 0; b <= M1; ++b)
+        for (char d : ds) {
+          ColIn in{src(b, d), {}};
+          for (int acc = 0; acc < 2 && a0 + acc <= M1; ++acc) {
+            ColTerm t;
+            if (a0 + acc + b <= M1 && implicit_term(acc, a0 + acc, b, of_v, d == 'x', d == 'y', &t)) {
+              in.terms.push_back(t);
+              used[acc] = true;
+            }
+          }
+          if (!in.terms.empty()) ins.push_back(in);
+        }
+      if (ins.empty()) continue;
+      std::vector<std::pair<std::string, ColTerm>> outs;
+      for (int acc = 0; acc < 2 && a0 + acc <= M1; ++acc) {
+        if (!used[acc]) continue;
+        has[a0 + acc] = true;
+        outs.push_back({prefix + std::to_string(a0 + acc), term(acc, 1.0, 0, 0, 0, 0, 1)});
+      }
+      out.push_back(col(ins, outs, used[1] ? 2 : 1));
+    }
+    return has;
+  }
+  // F{eta^a F^{-1}{S_a}} (a >= 1) by one row pass: IU<a> (prefix_u)
+  void plan_implicit_outer(std::vector<Pass>& out, const std::vector<bool>& has, const std::string& prefix_s,
+                           const std::string& prefix_u) {
+    RowB r = row_begin();
+    bool any = false;
+    for (size_t a = 1; a < has.size(); ++a) {
+      if (!has[a]) continue;
+      c2r(r, 0, {prefix_s + std::to_string(a)});
+      prod(r, 0, (int)a, 0, 0, 1.0, prefix_u + std::to_string(a));
+      any = true;
+    }
+    if (any) out.push_back(row_end(r, true, false, false));
+  }
+  // the outer sum C_h k (nx S_0 + sum_{a>=1} F{eta^a s_a}) (+ extra inputs),
+  // written to dst with the pass-through buffers added
+  void plan_implicit_sum(std::vector<Pass>& out, const std::vector<bool>& has, const std::string& prefix_s,
+                         const std::string& prefix_u, std::vector<ColIn> ins, const std::string& dst,
+                         const std::vector<std::string>& passthrough) {
+    // S_0 is a column-pass output (x-spectrum / nx): scaled back to the
+    // unnormalised input convention of the column pass
+    if (!has.empty() && has[0]) ins.push_back({prefix_s + "0", {term(0, (double)g.nx, 1, 11, 0, 0)}});
+    for (size_t a = 1; a < has.size(); ++a)
+      if (has[a]) ins.push_back({prefix_u + std::to_string(a), {term(0, 1.0, 1, 11, 0, 0)}});
+    out.push_back(col(ins, {{dst, term(0, 1.0, 0, 0, 0, 0, 1)}}, 1, passthrough));
+  }
+  void plan_implicit_setup(std::vector<Pass>& out) {
+    const int M1 = c->opt.order - 1;
+    out.push_back(plan_col_a());   // V1 = F{V^(1)}, grad phi~ (mixed)
+    RowB r = row_begin();
+    for (char d : dims()) {
+      c2r(r, 0, {std::string("dphi") + d});
+      for (int b = 0; b <= M1; ++b)
+        prod(r, 0, b ? 1 : 0, 0, b ? 2 : 0, 1.0, S("IP%d", b) + d);   // eta^b grad phi~
+    }
+    out.push_back(row_end(r, true, false, false));
+    const std::vector<bool> has = plan_implicit_inner(
+        out, false, "IGS", [&](int b, char d) { return S("IP%d", b) + d; });
+    plan_implicit_outer(out, has, "IGS", "IGU");
+    plan_implicit_sum(out, has, "IGS", "IGU", {{st_phi, {term(0, 1.0, 1, 1, 0, 0)}}}, "IG", {});
+  }
+  void plan_implicit_iter(std::vector<Pass>& out, const std::string& src, const std::string& dst) {
+    const int M1 = c->opt.order - 1;
+    RowB r = row_begin();
+    c2r(r, 0, {src});
+    for (int b = 0; b <= M1; ++b) prod(r, 0, b ? 1 : 0, 0, b ? 2 : 0, 1.0, S("IQ%d", b));   // eta^b V
+    out.push_back(row_end(r, true, false, false));
+    const std::vector<bool> has = plan_implicit_inner(
+        out, true, "IS", [&](int b, char) { return S("IQ%d", b); });
+    plan_implicit_outer(out, has, "IS", "IU");
+    plan_implicit_sum(out, has, "IS", "IU", {}, dst, {"IG"});
+  }
 };
 
 
@@ -1174,6 +1286,42 @@ __global__ void k_norm45_partials(NormParams q) {
     __syncthreads();
   }
   if (threadIdx.x < 4) q.part[((size_t)m * kConvBlocks + blockIdx.x) * 4 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// Increment norms of the implicit iteration, one block per member: the
+// Parseval sums of |a - b|^2 and |a|^2 over the member's mixed field (kx = 0
+// once, kx > 0 twice), reduced in a fixed order.
+constexpr int kImplicitMaxIter = 64;
+template <typename T>
+__global__ void k_implicit_norms(const void* a, const void* b, long long stride, int W, int ny, double* out) {
+  using V = cx<T>;
+  __shared__ double sm[2][256];
+  const int m = blockIdx.x;
+  const V* pa = reinterpret_cast<const V*>(a) + m * stride;
+  const V* pb = reinterpret_cast<const V*>(b) + m * stride;
+  double d2 = 0.0, a2 = 0.0;
+  const long long ne = (long long)W * ny;
+  for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
+    const double w = (e / ny) == 0 ? 1.0 : 2.0;
+    const V u = pa[e], v = pb[e];
+    const double dr = double(u.x) - double(v.x), di = double(u.y) - double(v.y);
+    d2 += w * (dr * dr + di * di);
+    a2 += w * (double(u.x) * double(u.x) + double(u.y) * double(u.y));
+  }
+  sm[0][threadIdx.x] = d2;
+  sm[1][threadIdx.x] = a2;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + st];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * m] = sm[0][0];
+    out[2 * m + 1] = sm[1][0];
+  }
 }
 
 __global__ void k_norm45_finish(NormParams q) {
@@ -2170,17 +2318,12 @@ int sbi_get_state(sbi_ctx* c, int member, double* eta, double* phi, int on_devic
   return SBI_OK;
 }
 
-int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, int eulerian_w) {
-  int rc = check_member(c, member);
-  if (rc) return rc;
-  if (!V_out) return fail(c, SBI_EINVAL, "V_out is NULL");
-  const int gi = c->where[member].first;
-  Group& g = c->groups[gi];
-  rc = run_diag(c, gi, eulerian_w != 0);
-  if (rc) return rc;
+// one member's physical field of the working precision -> FP64 V_out
+// (host or device), queued on the library's stream
+int output_member_field(sbi_ctx* c, int member, const void* src, double* V_out, int on_device) {
+  Group& g = c->groups[c->where[member].first];
   const size_t np = g.phys_elems();
   const size_t off = (size_t)c->where[member].second * np;
-  void* src = eulerian_w ? g.wout : g.Vphys;
   double* dst = on_device ? V_out : g.out64;
   const int thr = 256;
   const long long blocks = ((long long)np + thr - 1) / thr;
@@ -2189,6 +2332,19 @@ int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, 
   CK(cudaGetLastError(), "convert");
   if (!on_device)
     CK(cudaMemcpyAsync(V_out, g.out64, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy V");
+  return SBI_OK;
+}
+
+int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, int eulerian_w) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!V_out) return fail(c, SBI_EINVAL, "V_out is NULL");
+  const int gi = c->where[member].first;
+  Group& g = c->groups[gi];
+  rc = run_diag(c, gi, eulerian_w != 0);
+  if (rc) return rc;
+  rc = output_member_field(c, member, eulerian_w ? g.wout : g.Vphys, V_out, on_device);
+  if (rc) return rc;
   int notconv = 0;
   if (g.d_notconv)
     CK(cudaMemcpyAsync(&notconv, g.d_notconv + c->where[member].second, sizeof(int),
@@ -2197,6 +2353,71 @@ int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, 
   if (notconv)
     return fail(c, SBI_ENOTCONVERGED, "adaptive order reached %d without meeting adapt_tol "
                 "(V is the order-%d sum)", c->opt.order, c->opt.order);
+  return SBI_OK;
+}
+
+int sbi_vertical_velocity_implicit(sbi_ctx* c, int member, int iterations, double* V_out, int on_device,
+                                   double* increments) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!V_out) return fail(c, SBI_EINVAL, "V_out is NULL");
+  if (iterations < 1 || iterations > kImplicitMaxIter)
+    return fail(c, SBI_EINVAL, "iterations must be in 1..%d", kImplicitMaxIter);
+  const int gi = c->where[member].first;
+  Group& g = c->groups[gi];
+  if (g.variable) return fail(c, SBI_EINVAL, "the implicit form is built for a flat bottom");
+  Planner pl{c, g};
+  std::vector<Pass> setup, first, ab, ba, fin;
+  pl.plan_implicit_setup(setup);
+  pl.plan_implicit_iter(first, "V1", "IVa");
+  pl.plan_implicit_iter(ab, "IVa", "IVb");
+  pl.plan_implicit_iter(ba, "IVb", "IVa");
+  const char* last = (iterations % 2) ? "IVa" : "IVb";
+  {
+    Planner::RowB r = pl.row_begin();
+    pl.c2r(r, 0, {last}, g.Vphys);
+    fin.push_back(pl.row_end(r, false, false, false));
+  }
+  if (!g.d_implicit)
+    g.d_implicit = (double*)dalloc(c, (size_t)kImplicitMaxIter * g.n * 2 * sizeof(double));
+  if (pl.oom || !g.d_implicit) return fail(c, SBI_ENOMEM, "device allocation failed");
+  CK(cudaStreamSynchronize(c->cap), "sync");
+  auto run = [&](std::vector<Pass>& v) {
+    for (auto& p : v) {
+      int r2 = tune_pass(c, p, c->stream);
+      if (!r2) r2 = launch_pass(c, p, c->stream);
+      if (r2) return r2;
+    }
+    return (int)SBI_OK;
+  };
+  rc = run(setup);
+  if (rc) return rc;
+  const long long stride = (long long)g.mixed_elems();
+  for (int it = 0; it < iterations; ++it) {
+    rc = run(it == 0 ? first : (it % 2 ? ab : ba));
+    if (rc) return rc;
+    const void* dst = pl.mixed(it % 2 ? "IVb" : "IVa");
+    const void* src = pl.mixed(it == 0 ? "V1" : (it % 2 ? "IVa" : "IVb"));
+    double* out = g.d_implicit + (size_t)it * g.n * 2;
+    if (c->fp64) k_implicit_norms<double><<<g.n, 256, 0, c->stream>>>(dst, src, stride, g.W, g.ny, out);
+    else k_implicit_norms<float><<<g.n, 256, 0, c->stream>>>(dst, src, stride, g.W, g.ny, out);
+    CK(cudaGetLastError(), "implicit norms");
+  }
+  rc = run(fin);
+  if (rc) return rc;
+  rc = output_member_field(c, member, g.Vphys, V_out, on_device);
+  if (rc) return rc;
+  std::vector<double> nrm((size_t)iterations * g.n * 2);
+  CK(cudaMemcpyAsync(nrm.data(), g.d_implicit, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+     "copy norms");
+  CK(cudaStreamSynchronize(c->stream), "vertical_velocity_implicit");
+  if (increments) {
+    const int li = c->where[member].second;
+    for (int it = 0; it < iterations; ++it) {
+      const double d2 = nrm[((size_t)it * g.n + li) * 2], a2 = nrm[((size_t)it * g.n + li) * 2 + 1];
+      increments[it] = a2 > 0.0 ? std::sqrt(d2 / a2) : 0.0;
+    }
+  }
   return SBI_OK;
 }
 

@@ -59,6 +59,8 @@ EXPORTS = {
     "sbi_set_state_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sbi_get_state_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sbi_vertical_velocity": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "sbi_vertical_velocity_implicit": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                                 C.POINTER(C.c_double)]),
     "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sbi_set_time": (C.c_int, [C.c_void_p, C.c_double]),
@@ -277,6 +279,17 @@ class Context:
         po, do, _ = _ptr(out)
         self._check(self.lib.sbi_vertical_velocity(self.ctx, member, po, do, int(eulerian_w)))
         return out
+
+    def vertical_velocity_implicit(self, member=0, iterations=1, out=None):
+        """sbi_vertical_velocity_implicit: V after `iterations` fixed-point
+        iterations of the implicit form (flat bottom) and the relative L2
+        change of each iteration."""
+        if out is None:
+            out = np.empty(self.shape(member))
+        po, do, _ = _ptr(out)
+        inc = (C.c_double * int(iterations))()
+        self._check(self.lib.sbi_vertical_velocity_implicit(self.ctx, member, int(iterations), po, do, inc))
+        return out, np.array(inc[:])
 
     def step(self, dt, n=1):
         self._check(self.lib.sbi_step(self.ctx, float(dt), int(n)))

@@ -498,6 +498,68 @@ def test_steady_stokes_wave_translates(sbi, prec, tol, depth, eps):
     assert np.max(np.abs(d)) < 2e-4 * np.max(np.abs(px - px.mean()))
 
 
+def _implicit_case(depth, eps, n=64):
+    from oracle import steady_wave as SW
+    L = 2 * math.pi
+    w = SW.solve(k=1.0, H=2 * eps, depth=depth, g=9.81)
+    grid = O.Grid(n, 1, L)
+    pb = O.Problem(grid, 9.81, depth)
+    x = np.arange(n) * L / n
+    return grid, O.project(pb, w.eta(x)), O.project(pb, w.surface_potential(x))
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+@pytest.mark.parametrize("depth,eps,order", [(math.inf, 0.1, 7), (2.0, 0.1, 7), (1.0, 0.05, 4)])
+def test_implicit_iteration_matches_oracle(sbi, prec, tol, depth, eps, order):
+    # The implicit form of Appendix A (flat bottom) by fixed-point iteration on
+    # a steady wave: V and the increment of every iteration against the oracle.
+    grid, eta, phi = _implicit_case(depth, eps)
+    its = 4
+    ctx = sbi.Context([(grid.nx, 1, grid.Lx, 1.0)], 9.81, None, h0=depth, order=order, precision=prec)
+    ctx.set_state(0, eta, phi)
+    V, inc = ctx.vertical_velocity_implicit(0, its)
+    Vo, _, inco = O.implicit_vertical_velocity(eta, phi, depth, grid, order=order, tol=0.0, maxit=its)
+    assert rel(V, Vo) < tol
+    assert np.all(np.abs(inc - np.array(inco)) < 1e3 * tol * np.array(inco) + tol)
+    assert inc[-1] < 1e-3 * inc[0]      # converging
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
+def test_implicit_iteration_2d_matches_oracle(sbi, prec, tol):
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, False, seed=170)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, None, h0=h0, precision=prec)
+    ctx.set_state(0, eta, phi)
+    V, inc = ctx.vertical_velocity_implicit(0, 3)
+    Vo, _, inco = O.implicit_vertical_velocity(eta, phi, h0, grid, tol=0.0, maxit=3)
+    assert rel(V, Vo) < tol
+    assert abs(inc[0] - inco[0]) < 1e3 * tol * inco[0]
+
+
+def test_implicit_iteration_diverges_like_the_oracle(sbi):
+    # kH/2 = 0.3: the fixed-point map is expansive; the GPU iterates follow
+    # the oracle's (FP64) while the increments grow
+    grid, eta, phi = _implicit_case(math.inf, 0.3)
+    ctx = sbi.Context([(grid.nx, 1, grid.Lx, 1.0)], 9.81, None, h0=math.inf, precision=1)
+    ctx.set_state(0, eta, phi)
+    V, inc = ctx.vertical_velocity_implicit(0, 4)
+    Vo, _, inco = O.implicit_vertical_velocity(eta, phi, math.inf, grid, tol=0.0, maxit=4)
+    assert rel(V, Vo) < 1e-8
+    assert np.all(np.abs(inc - np.array(inco)) < 1e-6 * np.array(inco))
+    assert inc[-1] > 0.1 and inc[-1] > inc[0]
+
+
+def test_implicit_iteration_validation(sbi):
+    depth = 0.7 - W.random_field(32, 1, 171, amplitude=0.05)
+    ctx = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, [depth], h0=0.7, precision=1)
+    with pytest.raises(sbi.SbiError):
+        ctx.vertical_velocity_implicit(0, 2)
+    flat = sbi.Context([(32, 1, 3.0, 1.0)], 9.81, None, h0=0.7, precision=1)
+    for bad in (0, 65):
+        with pytest.raises(sbi.SbiError):
+            flat.vertical_velocity_implicit(0, bad)
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:
