@@ -82,6 +82,29 @@ def test_solitary_wave_run_energy_and_speed(sbi):
     assert abs(speed - wl.notes["c"]) / wl.notes["c"] < 0.03
 
 
+@pytest.mark.parametrize("name,steps", [("stokes_2d", 200), ("solitary_1d", 400)])
+def test_fp32_run_tracks_fp64_run(sbi, name, steps):
+    # Over a run the FP32 path stays with the FP64 path: eta within 1e-4
+    # relative L2, and the relative energy drifts within 1e-4 of each other.
+    wl = getattr(W, name)()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    res = {}
+    for prec in (1, 0):
+        ctx = context_of(sbi, wl, [0], prec)
+        ctx.set_state(0, eta, phi)
+        _, E0 = ctx.invariants(0)
+        ctx.step(wl.dt, steps)
+        e, _ = ctx.get_state(0)
+        _, E1 = ctx.invariants(0)
+        res[prec] = (e, (E1 - E0) / E0)
+        ctx.close()
+    print(f"{name}: FP32 vs FP64 eta {rel(res[0][0], res[1][0]):.2e}, drifts {res[0][1]:.2e} {res[1][1]:.2e}")
+    assert rel(res[0][0], res[1][0]) < 1e-4
+    assert abs(res[0][1] - res[1][1]) < 1e-4
+
+
 @pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-5)])
 def test_submerged_bar_full_size_steps(sbi, prec, tol):
     # N=4096 bar with sponge layers: a few RK4 steps against the oracle.
