@@ -206,6 +206,17 @@ int sbi_step(sbi_ctx* ctx, double dt, int n);
  * Synchronizes the stream. */
 int sbi_invariants(sbi_ctx* ctx, int member, double* mass, double* energy);
 
+/* Crest of one member's current surface (the crest position and speed of the
+ * solitary-wave runs, Sec. 3.1): the largest sample of eta (the first in
+ * row-major order among equal samples) and its position refined along each
+ * axis by the parabola through the sample and its two periodic neighbours,
+ * x = (i + (f_- - f_+) / (2 (f_- - 2 f_0 + f_+))) dx (no shift where the
+ * denominator vanishes); y = 0 for a 1-D member.  *height is the sample.
+ * The crest speed is the change of x over time.  Computed in FP64 on the
+ * device in a fixed order.  NaN results for a non-finite state.
+ * Synchronizes the stream.  SBI_EINVAL for a NULL pointer. */
+int sbi_crest(sbi_ctx* ctx, int member, double* x, double* y, double* height);
+
 /* Simulation time t [s] of the context: 0 after creation, advanced by dt for
  * every step of sbi_step.  It sets the phase of the wavemaker pressure. */
 int sbi_set_time(sbi_ctx* ctx, double t);

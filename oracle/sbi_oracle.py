@@ -116,6 +116,13 @@ R15 Implicit form (Appendix A, the "iterative approach" that the successive
     GMRES on (I - F^{-1} L) V = F^{-1} G from the same start (relative
     residual tol, no restart), counting applications of L.  The paper does
     not say which iteration its "iterative approach" uses.
+R16 Crest (the crest position and speed of the solitary-wave runs, Sec. 3.1):
+    the largest sample of eta (the first in row-major order among equal
+    samples), its position refined along each axis by the parabola through
+    it and its two periodic neighbours, x = (i + (f_- - f_+) / (2 (f_- - 2 f_0
+    + f_+))) dx (no shift where the denominator vanishes); the reported
+    height is the sample itself.  The crest speed is the change of position
+    over time.
 
 Grid convention: fields are arrays of shape (ny, nx), x fastest; a 1-D problem
 has ny = 1 (Ly is then the unit width).  Horizontal vectors are lists of
@@ -746,6 +753,22 @@ def step(pb: Problem, eta, phi, dt: float, n: int = 1, t0: float = 0.0):
             y = rk4_step(lambda t, s: surface_rhs(pb, s[0], s[1], t), y, dt, t0 + i * dt)
         y = (project(pb, y[0]), project(pb, y[1]))
     return y
+
+
+def crest(grid: Grid, eta):
+    """(x, y, height) of the crest, reading R16 (y = 0 in 1-D)."""
+    f = np.asarray(eta, dtype=np.float64).reshape(grid.ny, grid.nx)
+    j, i = divmod(int(np.argmax(f)), grid.nx)
+
+    def shift(fm, f0, fp):
+        den = fm - 2.0 * f0 + fp
+        return 0.5 * (fm - fp) / den if den != 0.0 else 0.0
+
+    x = (i + shift(f[j, (i - 1) % grid.nx], f[j, i], f[j, (i + 1) % grid.nx])) * (grid.Lx / grid.nx)
+    y = 0.0
+    if grid.ny > 1:
+        y = (j + shift(f[(j - 1) % grid.ny, i], f[j, i], f[(j + 1) % grid.ny, i])) * (grid.Ly / grid.ny)
+    return x, y, float(f[j, i])
 
 
 def invariants(pb: Problem, eta, phi):

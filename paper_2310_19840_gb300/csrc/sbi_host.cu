@@ -147,6 +147,7 @@ struct Group {
   double* d_norm45 = nullptr; // adaptive scheme: per member |e_eta|^2, |e_phi|^2, |eta|^2, |phi|^2
   double* d_part45 = nullptr; // its block partials
   double* d_implicit = nullptr; // implicit form: per iteration and member |V_new - V_old|^2, |V_new|^2 (lazy)
+  double* d_crest = nullptr;    // crest position and height of one member (lazy)
   std::map<std::string, void*> mixed;
   std::map<std::string, void*> tables;   // multiplier tables by key
   size_t phys_elems() const { return (size_t)nx * ny; }
@@ -1324,6 +1325,58 @@ __global__ void k_implicit_norms(const void* a, const void* b, long long stride,
   }
 }
 
+// Crest of one member: the largest sample of eta (the first in row-major
+// order among equal samples), found by one block in a fixed order, and its
+// position refined along each axis by the parabola through the sample and
+// its periodic neighbours; out = (x, y, height), NaN when no sample compares
+// (a non-finite state).
+__device__ __forceinline__ double crest_shift(double fm, double f0, double fp) {
+  const double den = fm - 2.0 * f0 + fp;
+  return den != 0.0 ? 0.5 * (fm - fp) / den : 0.0;
+}
+__global__ void k_crest(const double* __restrict__ f, int nx, int ny, double dx, double dy, double* out) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  const int t = threadIdx.x;
+  const long long np = (long long)nx * ny;
+  double best = -INFINITY;
+  long long bi = np;
+  for (long long e = t; e < np; e += blockDim.x) {
+    const double v = f[e];
+    if (v > best) {   // a thread visits increasing e: the first maximum stays
+      best = v;
+      bi = e;
+    }
+  }
+  sv[t] = best;
+  si[t] = bi;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (t < st) {
+      const double v2 = sv[t + st];
+      const long long i2 = si[t + st];
+      if (v2 > sv[t] || (v2 == sv[t] && i2 < si[t])) {
+        sv[t] = v2;
+        si[t] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  const long long e = si[0];
+  if (e >= np) {
+    out[0] = out[1] = out[2] = NAN;
+    return;
+  }
+  const int j = (int)(e / nx), i = (int)(e % nx);
+  const double f0 = f[e];
+  out[0] = (i + crest_shift(f[(long long)j * nx + (i + nx - 1) % nx], f0, f[(long long)j * nx + (i + 1) % nx])) * dx;
+  out[1] = ny > 1 ? (j + crest_shift(f[(long long)((j + ny - 1) % ny) * nx + i], f0,
+                                     f[(long long)((j + 1) % ny) * nx + i])) * dy
+                  : 0.0;
+  out[2] = f0;
+}
+
 __global__ void k_norm45_finish(NormParams q) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= q.n) return;
@@ -2353,6 +2406,32 @@ int sbi_vertical_velocity(sbi_ctx* c, int member, double* V_out, int on_device, 
   if (notconv)
     return fail(c, SBI_ENOTCONVERGED, "adaptive order reached %d without meeting adapt_tol "
                 "(V is the order-%d sum)", c->opt.order, c->opt.order);
+  return SBI_OK;
+}
+
+int sbi_crest(sbi_ctx* c, int member, double* x, double* y, double* height) {
+  int rc = check_member(c, member);
+  if (rc) return rc;
+  if (!x || !y || !height) return fail(c, SBI_EINVAL, "x, y and height must not be NULL");
+  Group& g = c->groups[c->where[member].first];
+  const size_t np = g.phys_elems();
+  const size_t off = (size_t)c->where[member].second * np;
+  if (!g.d_crest) {
+    g.d_crest = (double*)dalloc(c, 3 * sizeof(double));
+    if (!g.d_crest) return fail(c, SBI_ENOMEM, "device allocation failed");
+    CK(cudaStreamSynchronize(c->cap), "sync");
+  }
+  cudaError_t e = c->fp64 ? state_convert<double>(g.eta0 + off, g.out64, (long long)np, true, c->stream)
+                          : state_convert<float>(g.eta0 + off, g.out64, (long long)np, true, c->stream);
+  CK(e, "state conversion");
+  k_crest<<<1, 256, 0, c->stream>>>(g.out64, g.nx, g.ny, g.Lx / g.nx, g.two_d ? g.Ly / g.ny : 0.0, g.d_crest);
+  CK(cudaGetLastError(), "crest");
+  double h[3];
+  CK(cudaMemcpyAsync(h, g.d_crest, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy crest");
+  CK(cudaStreamSynchronize(c->stream), "crest");
+  *x = h[0];
+  *y = h[1];
+  *height = h[2];
   return SBI_OK;
 }
 

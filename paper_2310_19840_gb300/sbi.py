@@ -61,6 +61,8 @@ EXPORTS = {
     "sbi_vertical_velocity": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "sbi_vertical_velocity_implicit": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                                  C.POINTER(C.c_double)]),
+    "sbi_crest": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double)]),
     "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sbi_set_time": (C.c_int, [C.c_void_p, C.c_double]),
@@ -279,6 +281,12 @@ class Context:
         po, do, _ = _ptr(out)
         self._check(self.lib.sbi_vertical_velocity(self.ctx, member, po, do, int(eulerian_w)))
         return out
+
+    def crest(self, member=0):
+        """sbi_crest: (x, y, height) of the crest of the current surface."""
+        x, y, h = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.sbi_crest(self.ctx, member, C.byref(x), C.byref(y), C.byref(h)))
+        return x.value, y.value, h.value
 
     def vertical_velocity_implicit(self, member=0, iterations=1, out=None):
         """sbi_vertical_velocity_implicit: V after `iterations` fixed-point

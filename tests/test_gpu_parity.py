@@ -561,6 +561,22 @@ def test_implicit_iteration_validation(sbi):
             flat.vertical_velocity_implicit(0, bad)
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("case", [(256, 1, 12.0, 1.0), (64, 32, 6.0, 4.0)])
+def test_crest_matches_oracle(sbi, prec, case):
+    # sbi_crest against the oracle's crest of the same state (read back)
+    nx, ny, Lx, Ly = case
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, 0.7, False, seed=180)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, None, h0=0.7, precision=prec)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.01, 2)
+    e, _ = ctx.get_state(0)
+    x, y, h = ctx.crest(0)
+    xo, yo, ho = O.crest(grid, e)
+    assert h == ho
+    assert abs(x - xo) <= 1e-12 * Lx and abs(y - yo) <= 1e-12 * Ly
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:

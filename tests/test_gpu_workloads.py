@@ -66,19 +66,17 @@ def test_solitary_wave_run_energy_and_speed(sbi):
     ctx = context_of(sbi, wl, [0], 1)
     ctx.set_state(0, eta, phi)
     _, E0 = ctx.invariants(0)
+    x0, _, _ = ctx.crest(0)
     ctx.step(wl.dt, 400)
     e, p = ctx.get_state(0)
     _, E1 = ctx.invariants(0)
     assert abs(E1 - E0) / E0 < 1e-4
     eo, po = O.step(pb, eta, phi, wl.dt, 400)
     assert rel(e, eo) < 1e-9 and rel(p, po) < 1e-9
-
-    def crest(f):
-        f = f[0]
-        i = int(np.argmax(f))
-        fm, f0, fp = f[i - 1], f[i], f[(i + 1) % f.size]
-        return (i + 0.5 * (fm - fp) / (fm - 2 * f0 + fp)) * m.Lx / m.nx
-    speed = (crest(e) - crest(eta)) / (400 * wl.dt)
+    # crest speed from the library's crest (sbi_crest), against sqrt(g (h + a))
+    x1, _, _ = ctx.crest(0)
+    assert abs(x1 - O.crest(pb.grid, e)[0]) < 1e-12 * m.Lx
+    speed = (x1 - x0) / (400 * wl.dt)
     assert abs(speed - wl.notes["c"]) / wl.notes["c"] < 0.03
 
 

@@ -582,3 +582,29 @@ def test_rk45_adaptive_run():
         assert err < 50 * tol, (tol, err)
         steps[tol] = acc
     assert steps[1e-6] < steps[1e-8]
+
+
+def test_crest_position():
+    # R16: the parabola through the largest sample and its neighbours places a
+    # smooth peak within a small fraction of a cell; the height is the sample
+    n, L = 64, 10.0
+    dx = L / n
+    grid = O.Grid(n, 1, L)
+    x = np.arange(n) * dx
+    for x0 in (3.0, 3.0 + 0.37 * dx, 9.9):
+        f = np.cos(2 * np.pi * (x - x0) / L)
+        cx, cy, h = O.crest(grid, f)
+        d = (cx - x0 + L / 2) % L - L / 2
+        assert abs(d) < 0.01 * dx and cy == 0.0 and h == f.max()
+        g = 0.3 / np.cosh(1.2 * ((x - x0 + L / 2) % L - L / 2)) ** 2
+        cx, _, h = O.crest(grid, g)
+        assert abs((cx - x0 + L / 2) % L - L / 2) < 0.05 * dx and h == g.max()
+    # 2-D: a Gaussian bump; the first of equal samples wins
+    grid2 = O.Grid(32, 16, 4.0, 2.0)
+    X, Y = np.meshgrid(np.arange(32) * 4.0 / 32, np.arange(16) * 2.0 / 16)
+    b = np.exp(-((X - 1.3) ** 2 + (Y - 0.7) ** 2) / 0.5)
+    cx, cy, h = O.crest(grid2, b)
+    assert abs(cx - 1.3) < 0.05 * 4.0 / 32 and abs(cy - 0.7) < 0.05 * 2.0 / 16 and h == b.max()
+    flat = np.zeros((16, 32))
+    flat[3, 5] = flat[7, 2] = 1.0
+    assert O.crest(grid2, flat)[:2] == (5 * 4.0 / 32, 3 * 2.0 / 16)
