@@ -1,0 +1,49 @@
+"""The JSON line bench.py prints: the reference arm (the oracle, on the CPU)
+and the GB300 arm (on a GPU), on the small solitary-wave workload."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+             "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"}
+
+
+def run(args, timeout):
+    out = subprocess.run([sys.executable, "bench.py"] + args, cwd=ROOT, capture_output=True,
+                         text=True, timeout=timeout)
+    assert out.returncode == 0, out.stderr[-3000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout[-3000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = run(["--impl", "reference", "--workload", "solitary_1d", "--steps", "1", "--warmup", "1"], 600)
+    assert BASE_KEYS <= d.keys() and d["impl"] == "reference"
+    assert d["metric"] == "grid-point RK4 steps/s" and d["unit"] == "pt-steps/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["config"]["workload"] == "solitary_1d"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.gpu
+def test_gb300_arm_line():
+    d = run(["--workload", "solitary_1d", "--steps", "5", "--warmup", "3", "--no-cpu-baseline"], 900)
+    assert BASE_KEYS <= d.keys()
+    assert d["metric"] == "grid-point RK4 steps/s" and d["unit"] == "pt-steps/s" and d["value"] > 0
+    assert d["n_gpus"] == 1 and d["steps"] == 5 and d["warmup"] == 3 and d["scaling"] == "weak"
+    assert d["config"]["workload"] == "solitary_1d" and d["data"] == "synthetic"
+    r = d["roofline"]
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= r.keys()
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
+    assert {"sm_mhz", "sm_max_mhz", "reasons"} <= d["clocks"].keys()
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+    assert d["gpu_launches"] > 0
