@@ -577,6 +577,36 @@ def test_crest_matches_oracle(sbi, prec, case):
     assert abs(x - xo) <= 1e-12 * Lx and abs(y - yo) <= 1e-12 * Ly
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("spec", [(16, 1, 2.0, 1.0), (16, 8, 2.0, 1.5), (32, 16, 3.0, 2.0)])
+def test_degenerate_states(sbi, prec, spec):
+    # the smallest grids with degenerate states: rest stays rest exactly; a
+    # uniform potential carries no flow (k = 0 has no multiplier, R4); a
+    # uniformly raised surface under one potential mode gives the oracle's V
+    nx, ny, Lx, Ly = spec
+    grid = O.Grid(nx, ny, Lx, Ly)
+    h0 = 0.6
+    ctx = sbi.Context([spec], 9.81, None, h0=h0, precision=prec)
+    z = np.zeros((ny, nx))
+    ctx.set_state(0, z, z)
+    assert np.all(ctx.vertical_velocity(0) == 0.0)
+    ctx.step(0.01, 3)
+    e, p = ctx.get_state(0)
+    assert np.all(e == 0.0) and np.all(p == 0.0)
+    ctx.set_state(0, z, z + 0.7)
+    assert np.max(np.abs(ctx.vertical_velocity(0))) < (1e-12 if prec == 1 else 1e-5)
+    X, Y = np.meshgrid(np.arange(nx) * Lx / nx, np.arange(ny) * Ly / ny)
+    phi = 0.1 * np.cos(2 * np.pi * X / Lx) + (0.05 * np.sin(2 * np.pi * Y / Ly) if ny > 1 else 0.0)
+    eta = z + 0.05
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    assert rel(V, O.vertical_velocity(eta, phi, None, h0, grid)) < TOL[prec]
+    m0, _ = ctx.invariants(0)
+    ctx.step(0.01, 3)
+    m1, _ = ctx.invariants(0)
+    assert abs(m1 - m0) <= 1e-12 * abs(m0) if prec == 1 else abs(m1 - m0) <= 1e-6 * abs(m0)
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:
