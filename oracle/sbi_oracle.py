@@ -116,6 +116,22 @@ R15 Implicit form (Appendix A, the "iterative approach" that the successive
     GMRES on (I - F^{-1} L) V = F^{-1} G from the same start (relative
     residual tol, no restart), counting applications of L.  The paper does
     not say which iteration its "iterative approach" uses.
+R17 Implicit form over a variable bottom (Appendices A and B together,
+    without I^(S) and I^(B)): the unknowns are V and the bottom potential
+    varphi~.  Besides the terms of R15, V^(j) (j = 2..M) carries
+    C_h k 2 (-1)^a/(a! b!) F{eta^a F^{-1}{sqrt(e_h) k^{j-3} ik.F{delta^b grad varphi~}}}
+    for odd b, a + b = j - 1; varphi~^(j) (j = 1..M-1) is D_h times
+      2/(a! c!) F{delta^c F^{-1}{sqrt(e_h) k^{j-2} F{eta^a V}}}          (even a),
+      2/(a! c!) F{delta^c F^{-1}{sqrt(e_h) k^{j-3} ik.F{eta^a grad phi~}}} (odd a),
+    c + a = j - 1, and for j >= 2
+      s/(c! b!) F{delta^c F^{-1}{X k^{j-3} ik.F{delta^b grad varphi~}}},
+    c + b = j - 1, with s X = -C_h^{-1} for odd b and +D_h^{-1} for even b.
+    (Each printed term was checked against these patterns.)  The printed
+    varphi~^(5) has -e_h on every varphi~ term instead; the two differ by
+    sum_{c+b=4} (-1)^b/(c! b!) delta^c K delta^b, K = k^2 ik., the fourth
+    nested commutator of a multiplication with a third-order differential
+    operator, which vanishes: both forms are the same operator (the printed
+    one is the default).  D_h = 1/(1 - e_h) is taken as 0 at k = 0 (R4).
 R16 Crest (the crest position and speed of the solitary-wave runs, Sec. 3.1):
     the largest sample of eta (the first in row-major order among equal
     samples), its position refined along each axis by the parabola through
@@ -413,51 +429,175 @@ def implicit_system(eta, phi, h0, grid: Grid, order: int = MAX_ORDER, alpha: flo
     return mask * G, lambda Vp: mask * implicit_part(np.asarray(Vp, dtype=np.float64).reshape(grid.ny, grid.nx))
 
 
+def implicit_system_variable(eta, phi, delta, h0, grid: Grid, order: int = MAX_ORDER,
+                             alpha: float = 0.5, b5: str = "pattern"):
+    """The implicit equations of Appendices A and B over a variable bottom
+    (reading R17) for the unknowns u = (V, varphi~) in physical space:
+    F{u} = G + L(u).  Returns (G, L) with G = (G_V, G_B) spectra and L(u)
+    the pair of spectra of the terms in V and varphi~.  ``b5`` selects the
+    reading of the varphi~ terms of varphi~^(5): "pattern" (the signs and
+    depth factors of the other orders) or "printed" (-e_h on every term)."""
+    if not 1 <= order <= MAX_ORDER:
+        raise ValueError("order must be in 1..7")
+    if math.isinf(h0):
+        raise ValueError("a variable bottom needs a finite reference depth")
+    shape = (grid.ny, grid.nx)
+    eta = np.asarray(eta, dtype=np.float64).reshape(shape)
+    phi = np.asarray(phi, dtype=np.float64).reshape(shape)
+    delta = np.asarray(delta, dtype=np.float64).reshape(shape)
+    KX, KY, K = wavenumbers(grid)
+    mask = dealias_mask(grid, alpha)
+    t, _ = depth_multipliers(K, h0)
+    e_h = np.exp(-2.0 * K * h0)
+    C = 1.0 / (1.0 + e_h)
+    X = (1.0 + e_h, 1.0 - e_h)               # C_h^{-1} (even), D_h^{-1} (odd)
+    with np.errstate(divide="ignore"):
+        D = np.where(K > 0, 1.0 / np.where(K > 0, 1.0 - e_h, 1.0), 0.0)   # D_h, 0 at k = 0 (R4)
+    se = np.sqrt(e_h)
+    M1 = order - 1
+    fa = math.factorial
+
+    def kpow(p):
+        if p >= 0:
+            return K ** p if p > 0 else np.ones_like(K)
+        with np.errstate(divide="ignore"):
+            return np.where(K > 0, 1.0 / np.where(K > 0, K, 1.0) ** (-p), 0.0)
+
+    def outer(f, a, spec):                   # F{f^a F^{-1}{spec}}, dealiased
+        return mask * spec if a == 0 else mask * fft(f ** a * ifft(spec))
+
+    def ikdot(f, b, vec):                    # ik . F{f^b vec}, dealiased
+        return mask * ik_dot([f ** b * v for v in vec], KX, KY)
+
+    phi_hat = mask * fft(phi)
+    gphi = gradient(phi_hat, KX, KY, grid.dim)
+    # G_V: V^(1) and the grad phi~ terms of V^(2..M) (Appendix A, flat part)
+    GV = K * t * phi_hat
+    GB = np.zeros_like(GV)
+    for m in range(1, M1 + 1):
+        for a in range(m + 1):
+            b = m - a
+            if m % 2 == 1:
+                mult = (-1.0) ** (a + 1) / (fa(a) * fa(b)) * X[a % 2] * kpow(m - 2)
+            else:
+                mult = e_h / (fa(a) * fa(b)) * kpow(m - 2)
+            GV = GV + C * K * outer(eta, a, mult * ikdot(eta, b, gphi))
+    # G_B: the grad phi~ terms of varphi~^(j), j = 2..M-1 (Appendix B)
+    for j in range(2, M1 + 1):
+        for a in range(1, j, 2):
+            c = j - 1 - a
+            GB = GB + D * outer(delta, c, 2.0 / (fa(a) * fa(c)) * se * kpow(j - 3) * ikdot(eta, a, gphi))
+
+    def L(u):
+        Vp, Bp = (np.asarray(w, dtype=np.float64).reshape(shape) for w in u)
+        gB = gradient(mask * fft(Bp), KX, KY, grid.dim)
+        LV = np.zeros_like(GV)
+        # V terms of Appendix A (as on a flat bottom)
+        for m in range(1, M1 + 1):
+            for a in range(m + 1):
+                b = m - a
+                if m % 2 == 0:
+                    mult = (-1.0) ** (a + 1) / (fa(a) * fa(b)) * X[a % 2] * kpow(m - 1)
+                else:
+                    mult = e_h / (fa(a) * fa(b)) * kpow(m - 1)
+                LV = LV + C * K * outer(eta, a, mult * mask * fft(eta ** b * Vp))
+        # delta grad varphi~ terms of V^(j), j = 2..M
+        for j in range(2, order + 1):
+            for b in range(1, j, 2):
+                a = j - 1 - b
+                LV = LV + C * K * outer(eta, a, 2.0 * (-1.0) ** a / (fa(a) * fa(b)) * se * kpow(j - 3)
+                                        * ikdot(delta, b, gB))
+        LB = np.zeros_like(GV)
+        for j in range(1, M1 + 1):
+            # V terms of varphi~^(j)
+            for a in range(0, j, 2):
+                c = j - 1 - a
+                LB = LB + D * outer(delta, c, 2.0 / (fa(a) * fa(c)) * se * kpow(j - 2) * mask * fft(eta ** a * Vp))
+            # varphi~ terms of varphi~^(j), j >= 2
+            if j >= 2:
+                for b in range(j):
+                    c = j - 1 - b
+                    if j == 5 and b5 == "printed":
+                        mult = -e_h / (fa(c) * fa(b))
+                    elif b % 2 == 1:
+                        mult = -X[0] / (fa(c) * fa(b))
+                    else:
+                        mult = X[1] / (fa(c) * fa(b))
+                    LB = LB + D * outer(delta, c, mult * kpow(j - 3) * ikdot(delta, b, gB))
+        return LV, LB
+
+    return (mask * GV, mask * GB), L
+
+
 def implicit_vertical_velocity(eta, phi, h0, grid: Grid, order: int = MAX_ORDER,
                                alpha: float = 0.5, tol: float = 1e-12, maxit: int = 200,
-                               solver: str = "fixed_point"):
-    """V from the implicit equations of Appendix A (flat bottom), reading R15,
-    by the fixed-point iteration (``solver="fixed_point"``) or by GMRES
-    (``solver="gmres"``), both from V_0 = V^(1).
+                               solver: str = "fixed_point", delta=None, b5: str = "printed"):
+    """V from the implicit equations of Appendix A (flat bottom, reading R15)
+    or of Appendices A and B together (variable bottom ``delta``, reading
+    R17; unknowns V and varphi~), by the fixed-point iteration
+    (``solver="fixed_point"``) or by GMRES (``solver="gmres"``), both from
+    the first orders V^(1) (and varphi~_1 = sech(k h0) F{phi~}).
 
     Returns (V, applications, history): the number of applications of L and,
     per application, the relative L2 change of the iterate (fixed point) or
     the relative residual (GMRES)."""
-    G, L = implicit_system(eta, phi, h0, grid, order, alpha)
+    shape = (grid.ny, grid.nx)
+    npts = grid.nx * grid.ny
     KX, KY, K = wavenumbers(grid)
-    t, _ = depth_multipliers(K, h0)
-    V = ifft(dealias_mask(grid, alpha) * K * t * fft(np.asarray(phi, dtype=np.float64).reshape(grid.ny, grid.nx)))
+    t, s = depth_multipliers(K, h0)
+    mask = dealias_mask(grid, alpha)
+    phi_hat = mask * fft(np.asarray(phi, dtype=np.float64).reshape(shape))
+    variable = delta is not None and bool(np.any(delta))
+    if variable:
+        G, Lv = implicit_system_variable(eta, phi, delta, h0, grid, order, alpha, b5)
+        u0 = [ifft(K * t * phi_hat), ifft(s * phi_hat)]
+        L = lambda u: list(Lv(u))
+    else:
+        G1, L1 = implicit_system(eta, phi, h0, grid, order, alpha)
+        G, u0 = [G1], [ifft(K * t * phi_hat)]
+        L = lambda u: [L1(u[0])]
+    nf = len(u0)
+
+    def pack(fields):
+        return np.concatenate([np.asarray(f, dtype=np.float64).ravel() for f in fields])
+
+    def unpack(v):
+        return [v[q * npts:(q + 1) * npts].reshape(shape) for q in range(nf)]
+
+    def step(u):                            # F^{-1}{G + L(u)}, per unknown
+        return [ifft(g + l) for g, l in zip(G, L(u))]
+
     if solver == "gmres":
         import scipy.sparse.linalg as spla
-        shape = (grid.ny, grid.nx)
-        npts = grid.nx * grid.ny
         count = [0]
+        Gp = pack([ifft(g) for g in G])
 
         def apply(v):
             count[0] += 1
-            return v - ifft(L(v.reshape(shape))).ravel()
+            return v - (pack(step(unpack(v))) - Gp)
 
         history = []
-        A = spla.LinearOperator((npts, npts), matvec=apply, dtype=np.float64)
-        sol, info = spla.gmres(A, ifft(G).ravel(), x0=V.ravel(), rtol=tol, atol=0.0,
-                               restart=min(npts, maxit), maxiter=1,
+        A = spla.LinearOperator((nf * npts, nf * npts), matvec=apply, dtype=np.float64)
+        sol, info = spla.gmres(A, Gp, x0=pack(u0), rtol=tol, atol=0.0,
+                               restart=min(nf * npts, maxit), maxiter=1,
                                callback=history.append, callback_type="pr_norm")
         if info < 0:
             raise RuntimeError("gmres failed")
-        return sol.reshape(shape), count[0], history
+        return unpack(sol)[0], count[0], history
     if solver != "fixed_point":
         raise ValueError("solver must be 'fixed_point' or 'gmres'")
+    u = u0
     increments = []
     n = 0
     for n in range(1, maxit + 1):
         with np.errstate(over="ignore", invalid="ignore"):
-            Vn = ifft(G + L(V))
-            inc = float(np.linalg.norm(Vn - V) / max(np.linalg.norm(Vn), 1e-300))
-        V = Vn
+            un = step(u)
+            inc = float(np.linalg.norm(un[0] - u[0]) / max(np.linalg.norm(un[0]), 1e-300))
+        u = un
         increments.append(inc)
         if inc <= tol or not math.isfinite(inc):   # converged, or diverged
             break
-    return V, n, increments
+    return u[0], n, increments
 
 
 # --------------------------------------------------------------------------
