@@ -174,15 +174,18 @@ int sbi_get_state_all(sbi_ctx* ctx, double* eta, double* phi, int on_device);
 int sbi_vertical_velocity(sbi_ctx* ctx, int member, double* V_out, int on_device,
                           int eulerian_w);
 
-/* V of one member from the implicit convolution equations of Appendix A on a
- * flat bottom (the "iterative approach" that the successive scheme of
- * Sec. 2.4 replaces), by `iterations` fixed-point iterations
+/* V of one member from the implicit convolution equations of Appendix A (the
+ * "iterative approach" that the successive scheme of Sec. 2.4 replaces), by
+ * `iterations` fixed-point iterations
  *   F{V_{n+1}} = G + L(V_n),  V_0 = V^(1) = F^{-1}{k tanh(k h0) F{phi~}},
  * where G holds V^(1) and the grad phi~ terms of V^(2..M) and L the terms in
  * V, every term C_h k c F{eta^a F^{-1}{mult F{eta^b X}}} with the
  * coefficients of Appendix A (e_h = e^{-2 k h0}, C_h = 1/(1 + e_h),
- * D_h = 1/(1 - e_h); the remaining integral I^(S) is left out) and every
- * forward transform dealiased.  M is the context's order.
+ * D_h = 1/(1 - e_h); the remaining integrals I^(S), I^(B) are left out) and
+ * every forward transform dealiased.  M is the context's order.  Over a
+ * variable bottom the bottom potential varphi~ of Appendix B is iterated
+ * with V (its delta grad varphi~ terms enter V^(j)), from
+ * varphi~_0 = F^{-1}{sech(k h0) F{phi~}}.
  *   iterations  1..64.
  *   V_out       nx*ny doubles (host or device as on_device), V after the last
  *               iteration.
@@ -191,8 +194,8 @@ int sbi_vertical_velocity(sbi_ctx* ctx, int member, double* V_out, int on_device
  * The iteration diverges when the steepness makes L expansive (roughly
  * k H / 2 > 0.1 on one wavelength of 64 points); the call still returns the
  * last iterate and SBI_OK unless a value is non-finite.  Every member of the
- * member's group is iterated.  Synchronizes the stream.  SBI_EINVAL for a
- * member with a variable bottom or iterations outside 1..64. */
+ * member's group is iterated.  Synchronizes the stream.  SBI_EINVAL for
+ * iterations outside 1..64. */
 int sbi_vertical_velocity_implicit(sbi_ctx* ctx, int member, int iterations, double* V_out,
                                    int on_device, double* increments);
 

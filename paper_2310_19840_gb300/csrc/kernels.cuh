@@ -767,7 +767,12 @@ __global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
   if (s.depth >= 8) {
     // factors of the implicit form of Appendix A: e_h = e^{-2 k h0}
     const double eh = isinf(s.h0) ? 0.0 : exp(-2.0 * k * s.h0);
-    d = s.depth == 8 ? 1.0 + eh : (s.depth == 9 ? 1.0 - eh : (s.depth == 10 ? eh : 1.0 / (1.0 + eh)));
+    if (s.depth == 8) d = 1.0 + eh;
+    else if (s.depth == 9) d = 1.0 - eh;
+    else if (s.depth == 10) d = eh;
+    else if (s.depth == 11) d = 1.0 / (1.0 + eh);
+    else if (s.depth == 12) d = isinf(s.h0) ? 0.0 : exp(-k * s.h0);   // sqrt(e_h)
+    else d = k > 0.0 ? 1.0 / (1.0 - eh) : 0.0;                          // D_h, 0 at k = 0
   } else if (s.depth >= 4) {
     // entries of e^{A tau}; cos - 1 as -2 sin^2(w tau / 2) (no cancellation)
     const double w = sqrt(s.gravity * k * tk);

@@ -1059,38 +1059,51 @@ struct Planner {
     *t = term(acc, 1.0 / f, kp, 10, gx, gy, 1);
     return true;
   }
-  // Inner spectra IS<a> (prefix) from the inputs src(b, d) for a = 0..M-1;
-  // returns which a have any term.
-  std::vector<bool> plan_implicit_inner(std::vector<Pass>& out, bool of_v, const std::string& prefix,
-                                        const std::function<std::string(int, char)>& src) {
-    const int M1 = c->opt.order - 1;
-    std::vector<bool> has(M1 + 1, false);
-    const std::vector<char> ds = of_v ? std::vector<char>{'s'} : dims();
-    for (int a0 = 0; a0 <= M1; a0 += 2) {
+  // Inner spectra <prefix><o>, o = 0..nout-1, two per column pass; every
+  // input gives its term for output o (acc: the pass's accumulator) or none.
+  // Returns which outputs have any term.
+  using TermFn = std::function<bool(int o, int acc, ColTerm* t)>;
+  std::vector<bool> plan_inner(std::vector<Pass>& out, int nout, const std::string& prefix,
+                               const std::vector<std::pair<std::string, TermFn>>& inputs) {
+    std::vector<bool> has(std::max(nout, 0), false);
+    for (int o0 = 0; o0 < nout; o0 += 2) {
       std::vector<ColIn> ins;
       bool used[2] = {false, false};
-      for (int b = 0; b <= M1; ++b)
-        for (char d : ds) {
-          ColIn in{src(b, d), {}};
-          for (int acc = 0; acc < 2 && a0 + acc <= M1; ++acc) {
-            ColTerm t;
-            if (a0 + acc + b <= M1 && implicit_term(acc, a0 + acc, b, of_v, d == 'x', d == 'y', &t)) {
-              in.terms.push_back(t);
-              used[acc] = true;
-            }
+      for (const auto& def : inputs) {
+        ColIn in{def.first, {}};
+        for (int acc = 0; acc < 2 && o0 + acc < nout; ++acc) {
+          ColTerm t;
+          if (def.second(o0 + acc, acc, &t)) {
+            in.terms.push_back(t);
+            used[acc] = true;
           }
-          if (!in.terms.empty()) ins.push_back(in);
         }
+        if (!in.terms.empty()) ins.push_back(in);
+      }
       if (ins.empty()) continue;
       std::vector<std::pair<std::string, ColTerm>> outs;
-      for (int acc = 0; acc < 2 && a0 + acc <= M1; ++acc) {
+      for (int acc = 0; acc < 2 && o0 + acc < nout; ++acc) {
         if (!used[acc]) continue;
-        has[a0 + acc] = true;
-        outs.push_back({prefix + std::to_string(a0 + acc), term(acc, 1.0, 0, 0, 0, 0, 1)});
+        has[o0 + acc] = true;
+        outs.push_back({prefix + std::to_string(o0 + acc), term(acc, 1.0, 0, 0, 0, 0, 1)});
       }
       out.push_back(col(ins, outs, used[1] ? 2 : 1));
     }
     return has;
+  }
+  // inputs of the V equation's inner spectra S_a: F{eta^b X} (X = V, or
+  // grad phi~ when phi_terms), b = 0..M-1
+  std::vector<std::pair<std::string, TermFn>> inner_eta_inputs(bool of_v, const std::string& name) {
+    const int M1 = c->opt.order - 1;
+    std::vector<std::pair<std::string, TermFn>> v;
+    const std::vector<char> ds = of_v ? std::vector<char>{'s'} : dims();
+    for (int b = 0; b <= M1; ++b)
+      for (char d : ds)
+        v.push_back({of_v ? S(name.c_str(), b) : S(name.c_str(), b) + d,
+                     [this, b, d, of_v, M1](int a, int acc, ColTerm* t) {
+                       return a + b <= M1 && implicit_term(acc, a, b, of_v, d == 'x', d == 'y', t);
+                     }});
+    return v;
   }
   // F{eta^a F^{-1}{S_a}} (a >= 1) by one row pass: IU<a> (prefix_u)
   void plan_implicit_outer(std::vector<Pass>& out, const std::vector<bool>& has, const std::string& prefix_s,
@@ -1127,10 +1140,124 @@ struct Planner {
         prod(r, 0, b ? 1 : 0, 0, b ? 2 : 0, 1.0, S("IP%d", b) + d);   // eta^b grad phi~
     }
     out.push_back(row_end(r, true, false, false));
-    const std::vector<bool> has = plan_implicit_inner(
-        out, false, "IGS", [&](int b, char d) { return S("IP%d", b) + d; });
+    const std::vector<bool> has = plan_inner(out, M1 + 1, "IGS", inner_eta_inputs(false, "IP%d"));
     plan_implicit_outer(out, has, "IGS", "IGU");
     plan_implicit_sum(out, has, "IGS", "IGU", {{st_phi, {term(0, 1.0, 1, 1, 0, 0)}}}, "IG", {});
+  }
+  // Variable bottom (Appendices A and B together): the unknowns V and the
+  // bottom potential varphi~, iterated as V and grad varphi~ (mixed).  With
+  // m the order of a term (j = m + 1):
+  //   V^(j) += C_h k 2 (-1)^a/(a! b!) F{eta^a F^{-1}{sqrt(e_h) k^{j-3} ik.F{delta^b grad varphi~}}}, b odd;
+  //   varphi~^(j) = D_h ( 2/(a! c!) F{delta^c F^{-1}{sqrt(e_h) k^{j-2} F{eta^a V}}}          (a even)
+  //                     + 2/(a! c!) F{delta^c F^{-1}{sqrt(e_h) k^{j-3} ik.F{eta^a grad phi~}}} (a odd)
+  //                     + s/(c! b!) F{delta^c F^{-1}{X k^{j-3} ik.F{delta^b grad varphi~}}} (j >= 2) ),
+  // s X = -C_h^{-1} (b odd), +D_h^{-1} (b even), and -e_h for every term of
+  // varphi~^(5) (the printed form; the same operator).
+  bool bottom_self_term(int acc, int cpow, int b, int gx, int gy, ColTerm* t) const {
+    const int j = cpow + b + 1;
+    if (j < 2 || j > c->opt.order - 1) return false;
+    const double f = fact(cpow) * fact(b);
+    if (j == 5) *t = term(acc, -1.0 / f, j - 3, 10, gx, gy, 1);
+    else if (b % 2) *t = term(acc, -1.0 / f, j - 3, 8, gx, gy, 1);
+    else *t = term(acc, 1.0 / f, j - 3, 9, gx, gy, 1);
+    return true;
+  }
+  // F{eta^a F^{-1}{S_a}} (a >= 1) and F{delta^c F^{-1}{T_c}} (c >= 1) by one row pass
+  void plan_implicit_outer2(std::vector<Pass>& out, const std::vector<bool>& has_s, const std::string& ps,
+                            const std::string& pu, const std::vector<bool>& has_t, const std::string& pt,
+                            const std::string& pw) {
+    RowB r = row_begin();
+    bool any = false;
+    for (size_t a = 1; a < has_s.size(); ++a)
+      if (has_s[a]) {
+        c2r(r, 0, {ps + std::to_string(a)});
+        prod(r, 0, (int)a, 0, 0, 1.0, pu + std::to_string(a));
+        any = true;
+      }
+    for (size_t cc = 1; cc < has_t.size(); ++cc)
+      if (has_t[cc]) {
+        c2r(r, 0, {pt + std::to_string(cc)});
+        prod(r, 0, 0, (int)cc, 0, 1.0, pw + std::to_string(cc));
+        any = true;
+      }
+    if (any) out.push_back(row_end(r, true, true, false));
+  }
+  // D_h (nx T_0 + sum_{c>=1} F{delta^c t_c}) (+ extra inputs) as its gradient
+  // (ik, masked) in dst_x, dst_y, or as the spectrum itself in dst_x when
+  // gradient is false
+  void plan_bottom_sum(std::vector<Pass>& out, const std::vector<bool>& has, const std::string& pt,
+                       const std::string& pw, std::vector<ColIn> ins, const std::string& dst_x,
+                       const std::string& dst_y, bool gradient) {
+    if (!has.empty() && has[0]) ins.push_back({pt + "0", {term(0, (double)g.nx, 0, 13, 0, 0)}});
+    for (size_t cc = 1; cc < has.size(); ++cc)
+      if (has[cc]) ins.push_back({pw + std::to_string(cc), {term(0, 1.0, 0, 13, 0, 0)}});
+    std::vector<std::pair<std::string, ColTerm>> outs;
+    if (!gradient) {
+      outs.push_back({dst_x, term(0, 1.0, 0, 0, 0, 0, 1)});
+    } else {
+      outs.push_back({dst_x, term(0, 1.0, 0, 0, 1, 0, 1)});
+      if (g.two_d) outs.push_back({dst_y, term(0, 1.0, 0, 0, 0, 1, 1)});
+    }
+    out.push_back(col(ins, outs, 1));
+  }
+  void plan_implicit_setup_var(std::vector<Pass>& out) {
+    plan_implicit_setup(out);   // V1, grad varphi~_1 (db1), eta^b grad phi~ (IP), G_V (IG)
+    const int M1 = c->opt.order - 1;
+    std::vector<std::pair<std::string, TermFn>> ins;
+    for (int a = 1; a <= M1; a += 2)
+      for (char d : dims())
+        ins.push_back({S("IP%d", a) + d, [this, a, d, M1](int cc, int acc, ColTerm* t) {
+                         const int j = a + cc + 1;
+                         if (j > M1) return false;
+                         *t = term(acc, 2.0 / (fact(a) * fact(cc)), j - 3, 12, d == 'x', d == 'y', 1);
+                         return true;
+                       }});
+    const std::vector<bool> has = plan_inner(out, M1, "IGT", ins);
+    plan_implicit_outer2(out, {}, "", "", has, "IGT", "IGW");
+    plan_bottom_sum(out, has, "IGT", "IGW", {}, "IGB", "", false);
+  }
+  void plan_implicit_iter_var(std::vector<Pass>& out, const std::string& srcV, const std::string& srcBx,
+                              const std::string& srcBy, const std::string& dstV, const std::string& dstBx,
+                              const std::string& dstBy) {
+    const int M1 = c->opt.order - 1;
+    RowB r = row_begin();
+    c2r(r, 0, {srcV});
+    for (int b = 0; b <= M1; ++b) prod(r, 0, b ? 1 : 0, 0, b ? 2 : 0, 1.0, S("IQ%d", b));   // eta^b V
+    for (char d : dims()) {
+      c2r(r, 0, {d == 'x' ? srcBx : srcBy});
+      for (int b = 0; b <= M1; ++b) prod(r, 0, 0, b ? 1 : 0, b ? 2 : 0, 1.0, S("IR%d", b) + d);   // delta^b grad varphi~
+    }
+    out.push_back(row_end(r, true, true, false));
+    // V equation: S_a from eta^b V and (odd b) delta^b grad varphi~
+    std::vector<std::pair<std::string, TermFn>> vin = inner_eta_inputs(true, "IQ%d");
+    for (int b = 1; b <= M1; b += 2)
+      for (char d : dims())
+        vin.push_back({S("IR%d", b) + d, [this, b, d, M1](int a, int acc, ColTerm* t) {
+                         if (a + b > M1) return false;
+                         *t = term(acc, ((a % 2) ? -2.0 : 2.0) / (fact(a) * fact(b)), a + b - 2, 12, d == 'x',
+                                   d == 'y', 1);
+                         return true;
+                       }});
+    const std::vector<bool> has_s = plan_inner(out, M1 + 1, "IS", vin);
+    // varphi~ equation: T_c from (even a) eta^a V and delta^b grad varphi~
+    std::vector<std::pair<std::string, TermFn>> bin;
+    for (int a = 0; a <= M1; a += 2)
+      bin.push_back({S("IQ%d", a), [this, a, M1](int cc, int acc, ColTerm* t) {
+                       const int j = a + cc + 1;
+                       if (j > M1) return false;
+                       *t = term(acc, 2.0 / (fact(a) * fact(cc)), j - 2, 12, 0, 0, 1);
+                       return true;
+                     }});
+    for (int b = 0; b <= M1; ++b)
+      for (char d : dims())
+        bin.push_back({S("IR%d", b) + d, [this, b, d](int cc, int acc, ColTerm* t) {
+                         return bottom_self_term(acc, cc, b, d == 'x', d == 'y', t);
+                       }});
+    const std::vector<bool> has_t = plan_inner(out, M1, "IT", bin);
+    plan_implicit_outer2(out, has_s, "IS", "IU", has_t, "IT", "IW");
+    plan_implicit_sum(out, has_s, "IS", "IU", {}, dstV, {"IG"});
+    // G_B enters as a column output (spectrum / nx): scaled by nx
+    plan_bottom_sum(out, has_t, "IT", "IW", {{"IGB", {term(0, (double)g.nx, 0, 0, 0, 0)}}}, dstBx, dstBy, true);
   }
   void plan_implicit_iter(std::vector<Pass>& out, const std::string& src, const std::string& dst) {
     const int M1 = c->opt.order - 1;
@@ -1138,8 +1265,7 @@ struct Planner {
     c2r(r, 0, {src});
     for (int b = 0; b <= M1; ++b) prod(r, 0, b ? 1 : 0, 0, b ? 2 : 0, 1.0, S("IQ%d", b));   // eta^b V
     out.push_back(row_end(r, true, false, false));
-    const std::vector<bool> has = plan_implicit_inner(
-        out, true, "IS", [&](int b, char) { return S("IQ%d", b); });
+    const std::vector<bool> has = plan_inner(out, M1 + 1, "IS", inner_eta_inputs(true, "IQ%d"));
     plan_implicit_outer(out, has, "IS", "IU");
     plan_implicit_sum(out, has, "IS", "IU", {}, dst, {"IG"});
   }
@@ -2444,13 +2570,20 @@ int sbi_vertical_velocity_implicit(sbi_ctx* c, int member, int iterations, doubl
     return fail(c, SBI_EINVAL, "iterations must be in 1..%d", kImplicitMaxIter);
   const int gi = c->where[member].first;
   Group& g = c->groups[gi];
-  if (g.variable) return fail(c, SBI_EINVAL, "the implicit form is built for a flat bottom");
   Planner pl{c, g};
   std::vector<Pass> setup, first, ab, ba, fin;
-  pl.plan_implicit_setup(setup);
-  pl.plan_implicit_iter(first, "V1", "IVa");
-  pl.plan_implicit_iter(ab, "IVa", "IVb");
-  pl.plan_implicit_iter(ba, "IVb", "IVa");
+  if (g.variable) {
+    // V and grad varphi~ iterated together (Appendices A and B)
+    pl.plan_implicit_setup_var(setup);
+    pl.plan_implicit_iter_var(first, "V1", "db1x", "db1y", "IVa", "IBxa", "IBya");
+    pl.plan_implicit_iter_var(ab, "IVa", "IBxa", "IBya", "IVb", "IBxb", "IByb");
+    pl.plan_implicit_iter_var(ba, "IVb", "IBxb", "IByb", "IVa", "IBxa", "IBya");
+  } else {
+    pl.plan_implicit_setup(setup);
+    pl.plan_implicit_iter(first, "V1", "IVa");
+    pl.plan_implicit_iter(ab, "IVa", "IVb");
+    pl.plan_implicit_iter(ba, "IVb", "IVa");
+  }
   const char* last = (iterations % 2) ? "IVa" : "IVb";
   {
     Planner::RowB r = pl.row_begin();

@@ -96,7 +96,8 @@ struct ColTerm {
                   // 4: cos(w tau) - 1, 5: (k tanh(k h0) / w) sin(w tau), 6: (g / w) sin(w tau)
                   // (g tau at k = 0), 7: cos(w tau); factors of the implicit form of
                   // Appendix A, e_h = e^{-2 k h0}: 8: 1 + e_h (C_h^-1), 9: 1 - e_h
-                  // (D_h^-1), 10: e_h, 11: 1 / (1 + e_h) (C_h)
+                  // (D_h^-1), 10: e_h, 11: 1 / (1 + e_h) (C_h), 12: sqrt(e_h),
+                  // 13: 1 / (1 - e_h) (D_h; 0 at k = 0)
   uint8_t mask;   // 0: none, 1: dealias mask, 2: (mask * D - 1) projection correction
   uint8_t pad_;
   double c;
