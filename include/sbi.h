@@ -49,7 +49,8 @@ extern "C" {
 #define SBI_ECUDA          3   /* a CUDA runtime call failed */
 #define SBI_ENONFINITE     4   /* NaN or Inf appeared in the state */
 #define SBI_ENOTCONVERGED  5   /* adaptive order reached M without meeting adapt_tol */
-#define SBI_ETIMEOUT       6   /* a bounded device-side wait expired */
+#define SBI_ETIMEOUT       6   /* a bounded device-side wait expired (reserved: no kernel of
+                                    * this library waits on another, so none is returned) */
 
 #define SBI_FP32 0             /* FFTs, multipliers, products in FP32; FP64 state, RK4 sums, invariants */
 #define SBI_FP64 1             /* everything in FP64 (the plain path) */
