@@ -1,7 +1,8 @@
 """Accuracy of the oracle's ESBI and HOS diagnostics against steady Stokes
 waves: the comparison of the section on ESBI and HOS (deep water, one
 wavelength on 64 points, 16 alias-free modes).  Prints, for each steepness
-kH/2 and order M = 1..7, the largest error of V divided by the largest |V|,
+kH/2 and order M = 1..7, the largest error of V divided by the largest |V|
+(deep water, then finite depth kd = 1, 2 at orders 3, 5, 7),
 the exact V being -c eta_x of the Fourier-approximation solution
 (oracle/steady_wave.py); then, for the implicit form of Appendix A (reading
 R15), how its iterations behave against the steepness and how accurate its
@@ -20,17 +21,17 @@ from . import sbi_oracle as O
 from . import steady_wave as sw
 
 
-def errors(eps: float, n: int = 64, g: float = 9.81):
+def errors(eps: float, n: int = 64, g: float = 9.81, depth: float = math.inf):
     L = 2 * math.pi
-    w = sw.solve(k=1.0, H=2 * eps, g=g)
+    w = sw.solve(k=1.0, H=2 * eps, depth=depth, g=g)
     grid = O.Grid(n, 1, L)
     x = np.arange(n) * L / n
     eta, phi, Vx = w.eta(x), w.surface_potential(x), w.vertical_velocity(x)
     scale = np.max(np.abs(Vx))
     esbi, hos = [], []
     for M in range(1, O.MAX_ORDER + 1):
-        V = O.vertical_velocity(eta, phi, None, math.inf, grid, order=M).ravel()
-        Vh, _ = O.hos_surface_velocity(eta, phi, math.inf, grid, order=M)
+        V = O.vertical_velocity(eta, phi, None, depth, grid, order=M).ravel()
+        Vh, _ = O.hos_surface_velocity(eta, phi, depth, grid, order=M)
         esbi.append(float(np.max(np.abs(V - Vx)) / scale))
         hos.append(float(np.max(np.abs(Vh.ravel() - Vx)) / scale))
     return esbi, hos
@@ -59,6 +60,13 @@ def main():
         e, h = errors(eps)
         print(f"| {eps} | ESBI | " + " | ".join(f"{v:.2e}" for v in e) + " |")
         print(f"| {eps} | HOS | " + " | ".join(f"{v:.2e}" for v in h) + " |")
+    print()
+    print("| kd | kH/2 | ESBI M=3 | M=5 | M=7 | HOS M=3 | M=5 | M=7 |")
+    print("|---|---|" + "---:|" * 6)
+    for kd in (1.0, 2.0):
+        for eps in (0.1, 0.2):
+            e, h = errors(eps, depth=kd)
+            print(f"| {kd} | {eps} | " + " | ".join(f"{v:.1e}" for v in (e[2], e[4], e[6], h[2], h[4], h[6])) + " |")
     print()
     print("| kH/2 | fixed-point iterations to 1e-6 | GMRES applications to 1e-3 | to 1e-6 "
           "| error of the implicit solution | error of the successive scheme (M = 7) |")

@@ -130,3 +130,22 @@ def test_oracle_steps_translate_the_steady_wave(depth, eps):
     assert abs(drift + C) < 1e-3 * abs(C) + 1e-5 * np.max(np.abs(px - px.mean()))
     # the wave did move: a quarter wavelength changes eta by O(1)
     assert np.max(np.abs(np.ravel(eta0) - ex)) > 0.5 * np.max(np.abs(ex))
+
+
+@pytest.mark.parametrize("kd", [1.0, 2.0])
+def test_esbi_ahead_of_hos_in_finite_depth(kd):
+    # beyond the paper's deep-water comparison: at kd = 1 and 2 the ESBI
+    # error stays below the HOS error at every order, and both converge
+    n, L = 64, 2 * math.pi
+    grid = O.Grid(n, 1, L)
+    x = np.arange(n) * L / n
+    for eps in (0.1, 0.2):
+        w = sw.solve(k=1.0, H=2 * eps, depth=kd, g=G)
+        eta, phi, Vx = w.eta(x), w.surface_potential(x), w.vertical_velocity(x)
+        sc = np.max(np.abs(Vx))
+        es = [np.max(np.abs(np.ravel(O.vertical_velocity(eta, phi, None, kd, grid, order=M)) - Vx)) / sc
+              for M in (3, 5, 7)]
+        hs = [np.max(np.abs(np.ravel(O.hos_surface_velocity(eta, phi, kd, grid, order=M)[0]) - Vx)) / sc
+              for M in (3, 5, 7)]
+        assert all(e < h for e, h in zip(es, hs))
+        assert es[0] > es[1] > es[2] and hs[0] > hs[1] > hs[2]
