@@ -149,3 +149,22 @@ def test_esbi_ahead_of_hos_in_finite_depth(kd):
               for M in (3, 5, 7)]
         assert all(e < h for e, h in zip(es, hs))
         assert es[0] > es[1] > es[2] and hs[0] > hs[1] > hs[2]
+
+
+def test_wider_mask_removes_the_plateau():
+    # kH/2 = 0.35 with 24 of 32 modes kept (alpha = 0.75): HOS meets 0.5 % at
+    # order 5 and ESBI keeps improving past order 5 (with alpha = 0.5 the mask
+    # truncates the wave's own harmonics and both level off)
+    n, L = 64, 2 * math.pi
+    w = sw.solve(k=1.0, H=0.7, g=G)
+    grid = O.Grid(n, 1, L)
+    x = np.arange(n) * L / n
+    eta, phi, Vx = w.eta(x), w.surface_potential(x), w.vertical_velocity(x)
+    sc = np.max(np.abs(Vx))
+
+    def err(V):
+        return np.max(np.abs(np.ravel(V) - Vx)) / sc
+    assert err(O.hos_surface_velocity(eta, phi, math.inf, grid, order=5, alpha=0.75)[0]) < 5e-3
+    e5 = err(O.vertical_velocity(eta, phi, None, math.inf, grid, order=5, alpha=0.75))
+    e7 = err(O.vertical_velocity(eta, phi, None, math.inf, grid, order=7, alpha=0.75))
+    assert e7 < 0.25 * e5 and e7 < 1e-4
