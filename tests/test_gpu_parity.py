@@ -637,6 +637,40 @@ def test_degenerate_states(sbi, prec, spec):
     assert abs(m1 - m0) <= 1e-12 * abs(m0) if prec == 1 else abs(m1 - m0) <= 1e-6 * abs(m0)
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("alpha", [1.0 / 3.0, 0.75, 1.0])
+def test_other_mask_widths_match_oracle(sbi, prec, alpha):
+    # The dealiasing fraction alias_frac (R5) away from 1/2: the steep wave
+    # (ESBI and HOS) and a 2-D variable bottom (ESBI) against the oracle.  A
+    # wide mask keeps modes whose order-7 terms amplify round-off: the bar is
+    # the usual one or 20 times the oracle's own change of V under an input
+    # perturbation at the path's rounding level, whichever is larger (at
+    # kH/2 = 0.3 and alpha = 1 an FP32-sized perturbation moves V by ~1e-3).
+    grid, eta, phi = _implicit_case(math.inf, 0.3)
+    unit = 2.0 ** -24 if prec == 0 else 2.0 ** -53
+    r = np.random.default_rng(210)
+    de = eta * (1 + unit * r.standard_normal(eta.shape))
+    dp = phi * (1 + unit * r.standard_normal(phi.shape))
+    for diag in (sbi.SBI_DIAG_ESBI, sbi.SBI_DIAG_HOS):
+        ctx = sbi.Context([(grid.nx, 1, grid.Lx, 1.0)], 9.81, None, h0=math.inf, precision=prec,
+                          alias_frac=alpha, diagnostic=diag, set_state_dealias=0)
+        ctx.set_state(0, eta, phi)
+        V = ctx.vertical_velocity(0)
+        if diag == sbi.SBI_DIAG_HOS:
+            f = lambda e, p: O.hos_surface_velocity(e, p, math.inf, grid, alpha=alpha)[0]
+        else:
+            f = lambda e, p: O.vertical_velocity(e, p, None, math.inf, grid, alpha=alpha)
+        Vo = f(eta, phi)
+        cond = rel(f(de, dp), Vo)
+        assert rel(V, Vo) < max(TOL[prec], 20.0 * cond)
+    nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
+    g2, pb, e2, p2 = _case(nx, ny, Lx, Ly, h0, True, seed=200)
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec, alias_frac=alpha,
+                      set_state_dealias=0)
+    ctx.set_state(0, e2, p2)
+    assert rel(ctx.vertical_velocity(0), O.vertical_velocity(e2, p2, pb.delta, h0, g2, alpha=alpha)) < TOL[prec]
+
+
 def test_hos_option_validation(sbi):
     depth = 0.7 - W.random_field(32, 1, 160, amplitude=0.05)
     with pytest.raises(sbi.SbiError) as ei:
