@@ -114,6 +114,13 @@ typedef struct {
                             sum_{m+n<=M} eta^n/n! d^{n+1}_z phi^(m), V = W (1 + |grad eta|^2)
                             - grad eta . grad phi~, all dealiased; order = M.  Variable depth
                             or adapt_tol > 0 give SBI_EINVAL. */
+    int    state_fp64;   /* SBI_FP32 only.  0 (default): the state (eta, phi~) and the RK sums
+                            are kept as double-single float pairs (about 48 bits), updated with
+                            error-free float transformations; dt/6 and the stage offsets c dt
+                            enter as double-single pairs too.  1: they are kept and updated
+                            in FP64 (the transforms, multipliers and products stay FP32).
+                            Both use 8 bytes per value; results differ only in the last bits
+                            of the state.  Ignored by SBI_FP64, whose state is FP64. */
 } sbi_options;
 
 /* Fill *opt with the defaults listed above. */

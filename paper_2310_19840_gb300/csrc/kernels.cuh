@@ -13,6 +13,7 @@
 
 #include <math.h>
 
+#include "bank_model.h"
 #include "fft.cuh"
 #include "sbi_internal.h"
 
@@ -42,17 +43,19 @@ struct RowCfg {
   static constexpr int min_blocks() { return sizeof(T) == 4 ? 2 : 0; }
 };
 
-// Row stride of the staging buffer: odd, so that the rows of a block fall on
-// different shared-memory banks when the copies land.
-__host__ __device__ constexpr int stage_stride(int W) { return W | 1; }
-
-// shared memory of a row block: per row the FFT scratch, the physical slots
-// and the staging row that receives the incoming mixed row
+// shared memory of a row block: per row the FFT scratch (row stride fbs), the
+// physical slots and the staging row (stride sws) that receives the incoming
+// mixed row.  The strides come from the bank model (bank_model.h).
 template <typename T, int NX>
-__host__ __device__ constexpr size_t row_smem(int rpc, int W, int nslots) {
+__host__ __device__ constexpr size_t row_smem(int rpc, int fbs, int sws, int nslots) {
   using C = RowCfg<NX>;
-  return sizeof(cx<T>) * (size_t)rpc *
-         ((size_t)C::FBUF + (size_t)nslots * C::n + (size_t)stage_stride(W));
+  return sizeof(cx<T>) * (size_t)rpc * ((size_t)fbs + (size_t)nslots * C::n + (size_t)sws);
+}
+// upper bound per row over every stride the bank model may pick
+template <typename T, int NX>
+__host__ __device__ constexpr size_t row_smem_bound(int W, int nslots) {
+  constexpr int E = 128 / (int)sizeof(cx<T>);
+  return row_smem<T, NX>(1, RowCfg<NX>::FBUF + E, W + E, nslots);
 }
 
 template <int NX>
@@ -175,6 +178,23 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
   // R = 8 one table load and products by the 16th roots of unity
   constexpr bool kProd = C::R == 8 && kProductTwiddles<V>;
   const V wj = kProd ? cconj(__ldg(tw + tw_off(NX) + j)) : mk<V>(T(1), T(0));
+  if (2 * W <= C::n) {
+    // At most half the packed modes are kept: X[k] and X[n-k] are never both
+    // nonzero, so Z[k] = X[k] (1 + i w) for k < W, conj(X[n-k]) (1 - i w) for
+    // k > n - W and 0 in between (one load and one product per element).
+#pragma unroll
+    for (int r = 0; r < C::R; ++r) {
+      const int k = j + r * C::TPR;
+      V w;
+      if constexpr (kProd) w = r == 0 ? wj : cmul(wj, root16<1, V>(r));
+      else w = cconj(__ldg(tw + tw_off(NX) + k));
+      V z = mk<V>(T(0), T(0));
+      if (k < W) z = cmul(stg[k], mk<V>(T(1) - w.y, w.x));                       // (1 + i w)
+      else if (k > C::n - W) z = cmul(cconj(stg[C::n - k]), mk<V>(T(1) + w.y, -w.x));  // (1 - i w)
+      x[r] = cconj(z);
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < C::R; ++r) {
     const int k = j + r * C::TPR;
@@ -196,13 +216,13 @@ __device__ __forceinline__ void c2r_input(cx<T> (&x)[RowCfg<NX>::R], const cx<T>
 // X[k] = 1/2 (Z[k] + Z*[n-k]) - i/2 e^{-2 pi i k / NX} (Z[k] - Z*[n-k]), k < W,
 // are written to the transposed mixed field dst.
 template <typename T, int NX>
-__device__ __forceinline__ void r2c_store(const cx<T>* fb_all, const BufRef& dst, const RowIO& io,
+__device__ __forceinline__ void r2c_store(const cx<T>* fb_all, int fbs, const BufRef& dst, const RowIO& io,
                                           const cx<T>* __restrict__ tw) {
   using V = cx<T>;
   using C = RowCfg<NX>;
   if (!io.ok) return;
   V* out = reinterpret_cast<V*>(dst.ptr);
-  const V* fb = fb_all + io.rl * C::FBUF;
+  const V* fb = fb_all + io.rl * fbs;
   for (int k = io.k0; k < io.W; k += io.kstep) {
     const V zk = fb[pad(k)];
     const V zc = cconj(fb[pad((C::n - k) & (C::n - 1))]);
@@ -227,12 +247,13 @@ k_row(const __grid_constant__ RowParams p) {
   constexpr int n = C::n, R = C::R, TPR = C::TPR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rpc = p.rpc;
-  const int sw = stage_stride(p.W);
+  const int sw = p.sws;                            // staging row stride
+  const int fbs = p.fbs;                           // FFT scratch row stride
   V* fb_all = reinterpret_cast<V*>(smem_raw);      // FFT scratch
-  V* slot_base = fb_all + rpc * C::FBUF;           // physical slots
+  V* slot_base = fb_all + rpc * fbs;               // physical slots
   V* stg_all = slot_base + p.nslots * rpc * n;     // staging rows
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
-  V* fb = fb_all + rloc * C::FBUF;
+  V* fb = fb_all + rloc * fbs;
   const int row0 = (int)blockIdx.x * rpc;
   const RowIO io(row0, rpc, p.rows_total, p.ny, p.W, p.active, p.member0);
   const int row = row0 + rloc;
@@ -368,7 +389,7 @@ k_row(const __grid_constant__ RowParams p) {
       continue;
     }
     __syncthreads();  // every row's spectrum ready
-    r2c_store<T, NX>(fb_all, p.buf[op.dst], io, tw);
+    r2c_store<T, NX>(fb_all, fbs, p.buf[op.dst], io, tw);
   }
 }
 
@@ -408,9 +429,23 @@ __device__ __forceinline__ FF ff_mul_f(FF x, float f) {
   e = fmaf(x.lo, f, e);
   return ff_fast_two_sum(p, e);
 }
+// product of two double-single values (the lo * lo term is below the result's
+// last bit and dropped)
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff_fast_two_sum(p, e);
+}
 
-// A pair of state values (elements 2m, 2m+1) in the storage of each path.
-template <typename T> struct StatePair;
+
+// A pair of state values (elements 2m, 2m+1) in one of the two storage
+// formats: FP64, or double-single float pairs.  The FP64 format serves the
+// FP64 path and, optionally, the FP32 path (its FP32 right-hand sides then
+// accumulate into FP64 state and sums).  Inputs f are the working-precision
+// stage values (float or double).
+template <typename S> struct StatePair;
 template <> struct StatePair<double> {
   double v[2];
   __device__ __forceinline__ static StatePair load(const void* base, int m) {
@@ -420,8 +455,16 @@ template <> struct StatePair<double> {
   __device__ __forceinline__ void store(void* base, int m) const {
     reinterpret_cast<double2*>(base)[m] = make_double2(v[0], v[1]);
   }
-  __device__ __forceinline__ void add(int h, double f) { v[h] += f; }
-  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, double s) { v[h] += s * a.v[h]; }
+  template <typename F> __device__ __forceinline__ void add(int h, F f) { v[h] += double(f); }
+  // v += s * a (the RK4 update y + dt/6 (k1 + 2 k2 + 2 k3 + k4))
+  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, const RkScalar& s) {
+    v[h] += s.d * a.v[h];
+  }
+  // the working copy of v + s f (a stage input) in the working precision T
+  template <typename T, typename F>
+  __device__ __forceinline__ T offset(int h, const RkScalar& s, F f) const {
+    return T(v[h] + s.d * double(f));
+  }
   __device__ __forceinline__ double value(int h) const { return v[h]; }
   __device__ __forceinline__ bool finite() const { return isfinite(v[0]) && isfinite(v[1]); }
   __device__ __forceinline__ static StatePair zero() { return StatePair{{0.0, 0.0}}; }
@@ -436,8 +479,13 @@ template <> struct StatePair<float> {
     reinterpret_cast<float4*>(base)[m] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
   }
   __device__ __forceinline__ void add(int h, float f) { v[h] = ff_add_f(v[h], f); }
-  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, float s) {
-    v[h] = ff_add(v[h], ff_mul_f(a.v[h], s));
+  __device__ __forceinline__ void add_scaled(int h, const StatePair& a, const RkScalar& s) {
+    v[h] = ff_add(v[h], ff_mul(a.v[h], FF{s.hi, s.lo}));
+  }
+  template <typename T>
+  __device__ __forceinline__ T offset(int h, const RkScalar& s, float f) const {
+    const FF r = ff_add(v[h], ff_mul_f(FF{s.hi, s.lo}, f));
+    return T(r.hi + r.lo);
   }
   __device__ __forceinline__ float value(int h) const { return v[h].hi + v[h].lo; }
   __device__ __forceinline__ bool finite() const { return isfinite(v[0].hi) && isfinite(v[1].hi); }
@@ -458,7 +506,9 @@ struct RkCfg {
   static constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 };
 
-template <typename T, int NX>
+// S: the state storage format (T itself, or double for the FP32 path with an
+// FP64 state)
+template <typename T, int NX, typename S>
 __global__ void __launch_bounds__(RkCfg<NX>::THREADS, RkCfg<NX>::template min_blocks<T>())
 k_rk(const __grid_constant__ RkParams p) {
   using V = cx<T>;
@@ -467,8 +517,9 @@ k_rk(const __grid_constant__ RkParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rpc = p.rpc;
   V* fb_all = reinterpret_cast<V*>(smem_raw);
+  const int fbs = p.fbs;                           // scratch row stride
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
-  V* fb = fb_all + rloc * C::FBUF;
+  V* fb = fb_all + rloc * fbs;
   const int row0 = (int)blockIdx.x * rpc;
   const RowIO io(row0, rpc, p.rows_total, p.ny, p.W, p.active, 0);
   const int row = row0 + rloc;
@@ -480,7 +531,7 @@ k_rk(const __grid_constant__ RkParams p) {
   const long long off = (long long)y * NX;
 
   // new state in the working precision (the FFT inputs of the tail)
-  using SP = StatePair<T>;
+  using SP = StatePair<S>;
   V xe[R], xp[R];
   const long long eoff = member * p.eta0.stride + off, poff = member * p.phi0.stride + off;
   char* E0 = reinterpret_cast<char*>(p.eta0.ptr) + eoff * 8;   // 8 bytes per value
@@ -499,7 +550,7 @@ k_rk(const __grid_constant__ RkParams p) {
   } else {
     V x[R];
     // first inverse: phi~_t (stage) or the eta correction
-    stage_mixed<T>(fb_all, C::FBUF, &p.phit, 1, io);
+    stage_mixed<T>(fb_all, fbs, &p.phit, 1, io);
     __syncthreads();
     c2r_input<T, NX>(x, fb, p.W, j, tw);
     row_group_sync<NX>();
@@ -518,7 +569,7 @@ k_rk(const __grid_constant__ RkParams p) {
         xe[r] = mk<V>(T(e.value(0)), T(e.value(1)));
       }
       __syncthreads();
-      stage_mixed<T>(fb_all, C::FBUF, &p.corr_phi, 1, io);
+      stage_mixed<T>(fb_all, fbs, &p.corr_phi, 1, io);
       __syncthreads();
       c2r_input<T, NX>(x, fb, p.W, j, tw);
       row_group_sync<NX>();
@@ -535,13 +586,15 @@ k_rk(const __grid_constant__ RkParams p) {
         xp[r] = mk<V>(T(q.value(0)), T(q.value(1)));
       }
     } else {
-      // classical RK4: sums b = (1/6, 1/3, 1/3, 1/6), next-stage offsets c = (1/2, 1/2, 1)
+      // classical RK4, y + dt/6 (k1 + 2 k2 + 2 k3 + k4): the sums take the
+      // exact weights 1, 2, 2, 1; next-stage offsets c dt with c = (1/2, 1/2, 1).
+      // dt/6 and c dt enter in the state's own format (double, or a
+      // double-single pair), so the update never rounds the step to a float.
       const V* Vr = act ? phys_row<T>(p.V, member, y, NX) : nullptr;
       char* AE = reinterpret_cast<char*>(p.acc_eta.ptr) + (member * p.acc_eta.stride + off) * 8;
       char* AP = reinterpret_cast<char*>(p.acc_phi.ptr) + (member * p.acc_phi.stride + off) * 8;
-      const T bw = T((p.stage == 1 || p.stage == 4) ? (1.0 / 6.0) : (1.0 / 3.0));
-      const T cdt = T((p.stage == 3 ? 1.0 : 0.5) * p.dt);
-      const T dt = T(p.dt);
+      const T bw = T((p.stage == 1 || p.stage == 4) ? 1 : 2);
+      const RkScalar cdt = p.cdt, dt6 = p.dt6;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
@@ -560,13 +613,13 @@ k_rk(const __grid_constant__ RkParams p) {
         if (p.stage < 4) {
           ae.store(AE, m);
           ap.store(AP, m);
-          xe[r] = mk<V>(T(e.value(0) + cdt * vv.x), T(e.value(1) + cdt * vv.y));
-          xp[r] = mk<V>(T(q.value(0) + cdt * ft.x), T(q.value(1) + cdt * ft.y));
+          xe[r] = mk<V>(e.template offset<T>(0, cdt, vv.x), e.template offset<T>(1, cdt, vv.y));
+          xp[r] = mk<V>(q.template offset<T>(0, cdt, ft.x), q.template offset<T>(1, cdt, ft.y));
         } else {
-          e.add_scaled(0, ae, dt);
-          e.add_scaled(1, ae, dt);
-          q.add_scaled(0, ap, dt);
-          q.add_scaled(1, ap, dt);
+          e.add_scaled(0, ae, dt6);
+          e.add_scaled(1, ae, dt6);
+          q.add_scaled(0, ap, dt6);
+          q.add_scaled(1, ap, dt6);
           e.store(E0, m);
           q.store(P0, m);
           bad |= !e.finite() || !q.finite();
@@ -588,11 +641,11 @@ k_rk(const __grid_constant__ RkParams p) {
   __syncthreads();
   fft_block<n, R, -1>(xe, fb, j, tw);
   __syncthreads();
-  r2c_store<T, NX>(fb_all, p.eta_hat, io, tw);
+  r2c_store<T, NX>(fb_all, fbs, p.eta_hat, io, tw);
   __syncthreads();
   fft_block<n, R, -1>(xp, fb, j, tw);
   __syncthreads();
-  r2c_store<T, NX>(fb_all, p.phi_hat, io, tw);
+  r2c_store<T, NX>(fb_all, fbs, p.phi_hat, io, tw);
 }
 
 // ===========================================================================
@@ -837,7 +890,9 @@ cudaError_t prepare_nx() {
   const int maxb = 227 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_row<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_rk<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+  e = cudaFuncSetAttribute(k_rk<T, NX, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+  if (e != cudaSuccess || sizeof(T) == 8) return e;
+  return cudaFuncSetAttribute(k_rk<T, NX, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
 }
 
 template <typename T, int NY>
@@ -851,7 +906,13 @@ cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
   if (p.rpc < 1 || p.rpc > C::RPC_MAX) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
-  k_row<T, NX><<<blocks, C::TPR * p.rpc, row_smem<T, NX>(p.rpc, p.W, p.nslots), st>>>(p);
+  RowParams q = p;
+  const bank::RowStrides rs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false);
+  q.fbs = rs.fbs;
+  q.sws = rs.sws;
+  const size_t smem = row_smem<T, NX>(q.rpc, q.fbs, q.sws, q.nslots);
+  if (smem > row_smem_bound<T, NX>(q.W, q.nslots) * (size_t)q.rpc) return cudaErrorInvalidValue;
+  k_row<T, NX><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
   return cudaGetLastError();
 }
 
@@ -860,7 +921,11 @@ cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
   if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
-  k_rk<T, NX><<<blocks, C::TPR * p.rpc, sizeof(cx<T>) * (size_t)p.rpc * C::FBUF, st>>>(p);
+  RkParams q = p;
+  q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true).fbs;
+  const size_t smem = sizeof(cx<T>) * (size_t)q.rpc * q.fbs;
+  if (q.state64 && sizeof(T) == 4) k_rk<T, NX, double><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
+  else k_rk<T, NX, T><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
   return cudaGetLastError();
 }
 
@@ -941,7 +1006,7 @@ int row_rpc_impl(int nx, int W, int nslots) {
 #define SBI_CASE(N)                                                         \
   case N:                                                                   \
     maxr = RowCfg<N>::RPC_MAX;                                              \
-    per = row_smem<T, N>(1, W, nslots);                                     \
+    per = row_smem_bound<T, N>(W, nslots);                                  \
     if (RowCfg<N>::template min_blocks<T>() == 2) budget = 113 * 1024;      \
     break;
     SBI_FOR_NX(SBI_CASE)

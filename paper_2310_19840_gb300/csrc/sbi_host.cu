@@ -178,6 +178,7 @@ struct sbi_ctx {
   sbi_options opt;
   double gravity = 9.81;
   bool fp64 = false;
+  bool state_ds = true;   // the state and RK sums are double-single pairs (FP32 path default)
   size_t real_size = 4;
   int nmembers = 0;
   cudaStream_t stream = nullptr;  // caller's stream
@@ -260,6 +261,15 @@ void* dalloc(sbi_ctx* c, size_t bytes) {
 // ---------------------------------------------------------------------------
 // Planner
 // ---------------------------------------------------------------------------
+// a step scalar as a double and as a double-single float pair
+RkScalar rk_scalar(double v) {
+  RkScalar r;
+  r.d = v;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
 struct Planner {
   sbi_ctx* c;
   Group& g;
@@ -839,6 +849,9 @@ struct Planner {
       p.rpc = std::max(1, kRkThreads / std::max(1, tpr));
     }
     p.dt = dt;
+    p.state64 = c->fp64 || !c->state_ds;
+    p.dt6 = rk_scalar(dt / 6.0);
+    p.cdt = rk_scalar((stage == 3 ? 1.0 : 0.5) * dt);
     p.eta0 = dref(g.eta0);
     p.phi0 = dref(g.phi0);
     p.acc_eta = dref(g.acc_eta);
@@ -1939,9 +1952,9 @@ __global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst,
 // Partial sums of eta and 1/2 (phi V + g eta^2) over fixed chunks of one
 // member, each chunk reduced by one block in a fixed tree order.
 // one state value as a double (hi + lo float pairs in the FP32 path)
-template <typename T>
+template <bool DS>
 __device__ __forceinline__ double state_value(const void* base, long long i) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (!DS) {
     return reinterpret_cast<const double*>(base)[i];
   } else {
     const float2 v = reinterpret_cast<const float2*>(base)[i];
@@ -1949,7 +1962,7 @@ __device__ __forceinline__ double state_value(const void* base, long long i) {
   }
 }
 
-template <typename T>
+template <typename T, bool DS>
 __global__ void k_invariant_partials(const void* __restrict__ eta, const void* __restrict__ phi,
                                      const T* __restrict__ V, long long n, double g, int chunk,
                                      double* __restrict__ out) {
@@ -1959,9 +1972,9 @@ __global__ void k_invariant_partials(const void* __restrict__ eta, const void* _
   for (int i = threadIdx.x; i < chunk; i += blockDim.x) {
     const long long q = base + i;
     if (q < n) {
-      const double h = state_value<T>(eta, q);
+      const double h = state_value<DS>(eta, q);
       m += h;
-      e += 0.5 * (state_value<T>(phi, q) * double(V[q]) + g * h * h);
+      e += 0.5 * (state_value<DS>(phi, q) * double(V[q]) + g * h * h);
     }
   }
   sm[0][threadIdx.x] = m;
@@ -2089,6 +2102,7 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
   c->opt = opt;
   c->gravity = gravity;
   c->fp64 = opt.precision == SBI_FP64;
+  c->state_ds = !c->fp64 && !opt.state_fp64;
   c->real_size = c->fp64 ? 8 : 4;
   c->nmembers = n;
   c->stream = (cudaStream_t)opt.cuda_stream;
@@ -2286,6 +2300,7 @@ void sbi_default_options(sbi_options* opt) {
   opt->alias_frac = 0.5;
   opt->h0 = NAN;
   opt->precision = SBI_FP32;
+  opt->state_fp64 = 0;
   opt->adapt_tol = 0.0;
   opt->filt_beta1 = 0.0;
   opt->filt_beta2 = 0.0;
@@ -2328,7 +2343,7 @@ int sbi_set_state(sbi_ctx* c, int member, const double* eta, const double* phi, 
       CK(cudaMemcpyAsync(g.out64, srcs[q], np * 8, cudaMemcpyHostToDevice, c->cap), "copy state");
       src = g.out64;
     }
-    cudaError_t e = c->fp64 ? state_convert<double>(src, dsts[q], np, false, c->cap)
+    cudaError_t e = !c->state_ds ? state_convert<double>(src, dsts[q], np, false, c->cap)
                             : state_convert<float>(src, dsts[q], np, false, c->cap);
     CK(e, "state conversion");
   }
@@ -2412,7 +2427,7 @@ int sbi_set_state_all(sbi_ctx* c, const double* eta, const double* phi, int on_d
           CK(cudaMemcpyAsync(g.stage64 + (size_t)li * np, srcs[q] + off[g.members[li]], np * 8 * run,
                              kind, c->cap), "copy state");
         void* to = reinterpret_cast<char*>(dsts[q]) + (size_t)li * np * 8;   // 8 bytes per stored value
-        cudaError_t e = c->fp64 ? state_convert<double>(from, to, (long long)(np * run), false, c->cap)
+        cudaError_t e = !c->state_ds ? state_convert<double>(from, to, (long long)(np * run), false, c->cap)
                                 : state_convert<float>(from, to, (long long)(np * run), false, c->cap);
         CK(e, "state conversion");
         li += run;
@@ -2450,7 +2465,7 @@ int sbi_get_state_all(sbi_ctx* c, double* eta, double* phi, int on_device) {
           int run = 1;
           while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
           const void* from = reinterpret_cast<const char*>(srcs[q]) + (size_t)li * np * 8;
-          cudaError_t e = c->fp64
+          cudaError_t e = !c->state_ds
               ? state_convert<double>(from, views[q] + off[g.members[li]], (long long)(np * run), true, c->stream)
               : state_convert<float>(from, views[q] + off[g.members[li]], (long long)(np * run), true, c->stream);
           CK(e, "state conversion");
@@ -2460,7 +2475,7 @@ int sbi_get_state_all(sbi_ctx* c, double* eta, double* phi, int on_device) {
       }
       int rc = ensure_stage(c, g);
       if (rc) return rc;
-      cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream)
+      cudaError_t e = !c->state_ds ? state_convert<double>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream)
                               : state_convert<float>(srcs[q], g.stage64, (long long)(np * g.n), true, c->stream);
       CK(e, "state conversion");
       for (int li = 0; li < g.n;) {   // one copy per run of consecutive members
@@ -2487,7 +2502,7 @@ int sbi_get_state(sbi_ctx* c, int member, double* eta, double* phi, int on_devic
   double* dsts[2] = {eta, phi};
   for (int q = 0; q < 2; ++q) {
     double* dst = on_device ? dsts[q] : g.out64;
-    cudaError_t e = c->fp64 ? state_convert<double>(srcs[q], dst, np, true, c->stream)
+    cudaError_t e = !c->state_ds ? state_convert<double>(srcs[q], dst, np, true, c->stream)
                             : state_convert<float>(srcs[q], dst, np, true, c->stream);
     CK(e, "state conversion");
     if (!on_device)
@@ -2547,7 +2562,7 @@ int sbi_crest(sbi_ctx* c, int member, double* x, double* y, double* height) {
     if (!g.d_crest) return fail(c, SBI_ENOMEM, "device allocation failed");
     CK(cudaStreamSynchronize(c->cap), "sync");
   }
-  cudaError_t e = c->fp64 ? state_convert<double>(g.eta0 + off, g.out64, (long long)np, true, c->stream)
+  cudaError_t e = !c->state_ds ? state_convert<double>(g.eta0 + off, g.out64, (long long)np, true, c->stream)
                           : state_convert<float>(g.eta0 + off, g.out64, (long long)np, true, c->stream);
   CK(e, "state conversion");
   k_crest<<<1, 256, 0, c->stream>>>(g.out64, g.nx, g.ny, g.Lx / g.nx, g.two_d ? g.Ly / g.ny : 0.0, g.d_crest);
@@ -2766,9 +2781,11 @@ int sbi_invariants(sbi_ctx* c, int member, double* mass, double* energy) {
     c->partial_cap = (size_t)nchunks * 2;
   }
   if (c->fp64)
-    k_invariant_partials<double><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const double*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
+    k_invariant_partials<double, false><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const double*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
+  else if (c->state_ds)
+    k_invariant_partials<float, true><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const float*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
   else
-    k_invariant_partials<float><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const float*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
+    k_invariant_partials<float, false><<<nchunks, 256, 0, c->stream>>>(g.eta0 + off, g.phi0 + off, (const float*)g.Vphys + off, np, c->gravity, chunk, c->d_partials);
   CK(cudaGetLastError(), "invariants");
   std::vector<double> part((size_t)nchunks * 2);
   CK(cudaMemcpyAsync(part.data(), c->d_partials, part.size() * 8, cudaMemcpyDeviceToHost, c->stream), "copy partials");

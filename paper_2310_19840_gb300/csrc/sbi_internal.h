@@ -71,6 +71,7 @@ struct RowParams {
   int ny;
   int W;
   int nslots;
+  int fbs, sws;         // row strides of the FFT scratch and staging rows (set by the launcher)
   int member0;          // first member of this launch within the group (for convergence flags)
   const int* active;    // per-member flag (nullptr: all active); inactive members skip the pass
   BufRef eta, delta, wgt;        // physical fields (ptr may be null)
@@ -138,16 +139,28 @@ struct TableSpec {
 // itself unchanged (the intermediate stages of the integrating-factor scheme)
 enum RkMode : int { RK_ENTRY = 0, RK_STAGE = 1, RK_CORRECT = 2, RK_OFFSET = 3 };
 
+// A step-size scalar of the RK stage update in both representations: the
+// double, and its double-single split (hi = nearest float, lo = nearest float
+// of the rest), formed on the host so that the state update never rounds the
+// step to a float.
+struct RkScalar {
+  double d;
+  float hi, lo;
+};
+
 struct RkParams {
   int rpc;              // rows per block
+  int fbs;              // row stride of the scratch rows (set by the launcher)
   const int* active;    // per-member flag (nullptr: all members)
   int mode;             // RkMode
   int stage;            // 1..4 for RK_STAGE
   int tail;             // 1: write the next stage's working copies (eta_w, mixed eta^, phi^)
   int rows_total, ny, W;
   double dt;
-  BufRef eta0, phi0;    // FP64 master state
-  BufRef acc_eta, acc_phi;      // FP64 RK4 sums
+  int state64;          // FP32 path only: the state and sums are FP64 (else double-single)
+  RkScalar dt6, cdt;    // RK_STAGE: dt/6 (stage 4 update) and the stage's offset c dt
+  BufRef eta0, phi0;    // master state (FP64, or double-single pairs)
+  BufRef acc_eta, acc_phi;      // RK4 sums k1 + 2 k2 + 2 k3 + k4 (state format)
   BufRef V;             // physical V of this stage (T)
   BufRef phit;          // mixed phi~_t of this stage (T complex) / RK_CORRECT, RK_OFFSET: eta correction
   BufRef corr_phi;      // RK_CORRECT, RK_OFFSET: phi correction (mixed)

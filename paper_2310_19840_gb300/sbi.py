@@ -43,7 +43,8 @@ class sbi_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("check_finite", C.c_int),
                 ("set_state_dealias", C.c_int),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("autotune", C.c_int), ("integrator", C.c_int), ("diagnostic", C.c_int)]
+                ("autotune", C.c_int), ("integrator", C.c_int), ("diagnostic", C.c_int),
+                ("state_fp64", C.c_int)]
 
 
 EXPORTS = {
@@ -140,13 +141,22 @@ def _ptr(a, dtype=np.float64):
 def invariants_noalloc(grid, gravity, eta, phi, V, stream=None):
     """Mass and energy from device arrays without any device allocation
     (sbi_invariants_noalloc); eta, phi, V are contiguous float64 CUDA tensors."""
+    import torch
     lib = load()
     g = sbi_grid(grid[0], grid[1], grid[2], grid[3] if len(grid) > 3 else 1.0)
+    npts = int(grid[0]) * int(grid[1])
     ptrs = []
     for a in (eta, phi, V):
+        # the kernel reads nx*ny doubles from each pointer on the current
+        # device: anything shorter, or elsewhere, is refused before the call
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise ValueError("sbi_invariants_noalloc takes CUDA tensors")
+        if a.numel() != npts:
+            raise ValueError(f"sbi_invariants_noalloc: a field holds {a.numel()} values, "
+                             f"the grid {npts}")
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError("sbi_invariants_noalloc: the fields must be on the current device")
         p, dev, keep = _ptr(a)
-        if not dev:
-            raise ValueError("sbi_invariants_noalloc takes device arrays")
         ptrs.append(p)
     m, e = C.c_double(), C.c_double()
     st = C.c_void_p(int(stream)) if stream is not None else None
@@ -163,7 +173,7 @@ class Context:
     def __init__(self, grids, gravity, depths=None, *, h0=math.nan, order=7, alias_frac=0.5,
                  precision=SBI_FP32, adapt_tol=0.0, filt_beta1=0.0, filt_beta2=0.0, k_ref=1.0,
                  sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1,
-                 autotune=1, integrator=SBI_RK4, diagnostic=SBI_DIAG_ESBI):
+                 autotune=1, integrator=SBI_RK4, diagnostic=SBI_DIAG_ESBI, state_fp64=0):
         self.lib = load()
         if isinstance(grids, tuple):
             grids = [grids]
@@ -173,7 +183,8 @@ class Context:
                               adapt_tol=adapt_tol, filt_beta1=filt_beta1, filt_beta2=filt_beta2,
                               k_ref=k_ref, sponge_nu=sponge_nu, check_finite=check_finite,
                               set_state_dealias=set_state_dealias, autotune=autotune,
-                              integrator=integrator, diagnostic=diagnostic)
+                              integrator=integrator, diagnostic=diagnostic,
+                              state_fp64=state_fp64)
         keep = []
         if sponge_w is not None:
             w = np.ascontiguousarray(sponge_w, dtype=np.float64).ravel()
