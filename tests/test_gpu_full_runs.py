@@ -1,0 +1,80 @@
+"""Whole configured runs on the GPU against the oracle's own run of the same
+workload (classical RK4, projected initial state).
+
+The oracle's runs are stored in tests/golden/oracle_run_<workload>.json,
+written by ``python -m oracle.run_drift <workload> --out tests/golden`` (the
+oracle and the seeded input generators only): the relative energy change over
+the run and the final eta and phi~ at 64 sampled grid points.  The GPU path
+runs the same number of steps and is compared at those points (largest error
+relative to the largest sampled |value|) and in its energy drift.
+
+Bars: FP64 path 1e-8 on the samples and 1e-9 on the drift (rounding grows
+over thousands of steps but stays far below the method's own error); FP32
+path 1e-4 on the samples and on the drift (the stated tolerance on energy
+drift over a run).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sbi_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+BARS = {1: (1e-8, 1e-9), 0: (1e-4, 1e-4)}   # (samples, energy drift) per precision
+
+
+@pytest.fixture(scope="module")
+def sbi():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2310_19840_gb300 import sbi as s
+    return s
+
+
+def _run(sbi, name, prec, steps):
+    wl = getattr(W, name)()
+    m = wl.members[0]
+    grid = O.Grid(m.nx, m.ny, m.Lx, m.Ly if m.ny > 1 else 1.0)
+    pb = O.Problem(grid, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
+                   sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
+                   filt_beta2=wl.filt_beta2, k_ref=wl.k_ref)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    depth = (m.h0 - m.delta) if m.delta is not None else None
+    ctx = sbi.Context([(m.nx, m.ny, m.Lx, m.Ly)], wl.gravity, [depth], h0=m.h0, order=wl.order,
+                      alias_frac=wl.alpha, precision=prec, filt_beta1=wl.filt_beta1,
+                      filt_beta2=wl.filt_beta2, k_ref=wl.k_ref, sponge_w=wl.sponge_w,
+                      sponge_nu=wl.sponge_nu)
+    ctx.set_state(0, eta, phi)
+    _, E0 = ctx.invariants(0)
+    left = steps
+    while left > 0:
+        k = min(500, left)
+        ctx.step(wl.dt, k)
+        left -= k
+    e, p = ctx.get_state(0)
+    _, E1 = ctx.invariants(0)
+    ctx.close()
+    return e, p, (E1 - E0) / E0
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("name", ["solitary_1d", "bar_1d"])
+def test_full_run_matches_oracle_run(sbi, name, prec):
+    path = os.path.join(GOLDEN, f"oracle_run_{name}.json")
+    gold = json.load(open(path))
+    e, p, drift = _run(sbi, name, prec, gold["steps"])
+    idx = np.array(gold["sample_index"])
+    es, ps = np.array(gold["eta_samples"]), np.array(gold["phi_samples"])
+    err_e = float(np.max(np.abs(e.ravel()[idx] - es)) / np.max(np.abs(es)))
+    err_p = float(np.max(np.abs(p.ravel()[idx] - ps)) / np.max(np.abs(ps)))
+    d_err = abs(drift - gold["energy_drift_rel"])
+    print(f"{name} prec {prec} after {gold['steps']} steps: eta {err_e:.2e} phi {err_p:.2e} "
+          f"drift gpu {drift:+.3e} oracle {gold['energy_drift_rel']:+.3e}")
+    bar_s, bar_d = BARS[prec]
+    assert err_e < bar_s and err_p < bar_s
+    assert d_err < bar_d

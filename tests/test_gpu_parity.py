@@ -33,6 +33,16 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+def maxrel(a, b):
+    """Largest pointwise error relative to the largest |b|."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# largest pointwise error of V relative to max|V| after one evaluation
+TOL_MAX = {0: 1e-5, 1: 1e-11}
+
+
 def _case(nx, ny, Lx, Ly, h0, variable, seed, amp_eta=0.04, amp_phi=0.3, amp_delta=0.1):
     grid = O.Grid(nx, ny, Lx, Ly if ny > 1 else 1.0)
     delta = W.random_field(nx, ny, seed, amplitude=amp_delta * h0) if variable else None
@@ -237,9 +247,12 @@ def test_invariants_match_oracle(sbi, prec):
 
 @pytest.mark.parametrize("nx,ny", [(4096, 1), (16, 2048), (4096, 8), (1024, 1024), (512, 512),
                                    (256, 256), (2048, 16), (4096, 2048)])
-def test_every_kernel_size_fp32_matches_fp64(sbi, nx, ny):
-    # Largest and extreme grids: each size instantiation launches in both
-    # precisions and the FP32 path agrees with the FP64 path (variable depth).
+def test_every_kernel_size_matches_oracle(sbi, nx, ny):
+    # Largest and extreme grids (variable depth): each size instantiation of
+    # the row and column kernels launches in both precisions and matches the
+    # FP64 oracle, in relative L2 and pointwise.  At 4096 x 2048 the FP32 path
+    # is compared with the FP64 path instead: the same instantiations meet the
+    # oracle on the 4096 x 2048 variable-depth sea (test_gpu_workloads.py).
     # The grid spacing is fixed (0.05 m) so k|delta| stays below ~1 at every
     # size: FP32 round-off is amplified by (k delta)^j / j! in the delta terms.
     # The spectra are spread over the band (as in the wave workloads): with all
@@ -251,12 +264,49 @@ def test_every_kernel_size_fp32_matches_fp64(sbi, nx, ny):
     phi = W.random_field(nx, ny, 5, amplitude=0.2, band=0.2, slope=0.5)
     out = {}
     for prec in (1, 0):
-        ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec)
+        ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - delta], h0=h0, precision=prec,
+                          set_state_dealias=0)
         ctx.set_state(0, eta, phi)
         out[prec] = ctx.vertical_velocity(0)
         ctx.close()
     assert np.all(np.isfinite(out[1]))
-    assert rel(out[0], out[1]) < TOL[0]
+    if nx * ny > 2 ** 22:
+        assert rel(out[0], out[1]) < TOL[0] and maxrel(out[0], out[1]) < TOL_MAX[0]
+        return
+    grid = O.Grid(nx, ny, Lx, Ly)
+    Vo = O.vertical_velocity(eta, phi, delta, h0, grid)
+    for prec in (1, 0):
+        print(f"{nx}x{ny} prec {prec}: rel {rel(out[prec], Vo):.2e} max {maxrel(out[prec], Vo):.2e}")
+        assert rel(out[prec], Vo) < TOL[prec] and maxrel(out[prec], Vo) < TOL_MAX[prec], prec
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("case", [(256, 1, 12.0, 1.0, 0.5, True), (64, 32, 6.0, 4.0, 0.8, True),
+                                  (128, 64, 8.0, 4.0, math.inf, False)])
+def test_eulerian_w_matches_oracle(sbi, prec, case):
+    # sbi_vertical_velocity(..., eulerian_w = 1): the Eulerian vertical
+    # velocity at the surface w = (V + grad eta . grad phi~) / (1 + |grad eta|^2)
+    # (Sec. 2.2, the definition of V through the normal derivative), built
+    # here from the oracle's V and the spectral gradients of the dealiased
+    # state.
+    nx, ny, Lx, Ly, h0, variable = case
+    grid, pb, eta, phi = _case(nx, ny, Lx, Ly, h0, variable, seed=300 + nx)
+    depth = (h0 - pb.delta) if variable else None
+    ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [depth], h0=h0, precision=prec)
+    ctx.set_state(0, eta, phi)
+    w = ctx.vertical_velocity(0, eulerian_w=True)
+    V = ctx.vertical_velocity(0)
+    Vo = O.vertical_velocity(eta, phi, pb.delta, h0, grid)
+    KX, KY, _ = O.wavenumbers(grid)
+    mask = O.dealias_mask(grid)
+    ge = O.gradient(mask * O.fft(eta), KX, KY, grid.dim)
+    gp = O.gradient(mask * O.fft(phi), KX, KY, grid.dim)
+    dot = sum(a * b for a, b in zip(ge, gp))
+    ge2 = sum(a * a for a in ge)
+    wo = (Vo + dot) / (1.0 + ge2)
+    assert not np.allclose(wo, Vo)          # the slope terms matter for this state
+    assert rel(w, wo) < TOL[prec] and maxrel(w, wo) < TOL_MAX[prec]
+    assert rel(V, Vo) < TOL[prec]             # the V output is unchanged by the w call
 
 
 def _ratios(eta, phi, delta, h0, grid):
@@ -637,20 +687,30 @@ def test_degenerate_states(sbi, prec, spec):
     assert abs(m1 - m0) <= 1e-12 * abs(m0) if prec == 1 else abs(m1 - m0) <= 1e-6 * abs(m0)
 
 
+# Fixed upper limits of the bar of the wide-mask cases.  The oracle's change
+# of V under input perturbations of one rounding of the path's precision is
+# 2e-6 at alpha = 1/2, 1.5e-5 at 0.75 and 1.6e-3 at 1 for FP32; the GPU path
+# rounds at every transform stage, not only at its input, and its FP32 error
+# on the steep wave was measured at up to 1.3e-4 (alpha = 0.75) and 2.0e-3
+# (alpha = 1), pointwise.  The caps sit about 2.5 times above those.
+MASK_BAR_CAP = {0: {1.0 / 3.0: 1e-5, 0.75: 3e-4, 1.0: 5e-3}, 1: {1.0 / 3.0: 1e-12, 0.75: 1e-12, 1.0: 1e-10}}
+
+
 @pytest.mark.parametrize("prec", [1, 0])
 @pytest.mark.parametrize("alpha", [1.0 / 3.0, 0.75, 1.0])
 def test_other_mask_widths_match_oracle(sbi, prec, alpha):
     # The dealiasing fraction alias_frac (R5) away from 1/2: the steep wave
     # (ESBI and HOS) and a 2-D variable bottom (ESBI) against the oracle.  A
-    # wide mask keeps modes whose order-7 terms amplify round-off: the bar is
-    # the usual one or 20 times the oracle's own change of V under an input
-    # perturbation at the path's rounding level, whichever is larger (at
-    # kH/2 = 0.3 and alpha = 1 an FP32-sized perturbation moves V by ~1e-3).
+    # wide mask keeps modes whose order-7 terms amplify round-off.  The bar is
+    # the usual one or 50 times the oracle's own change of V under input
+    # perturbations at the path's rounding level (the median over five
+    # perturbations; the GPU path rounds each value about 50 times in
+    # sequence, each rounding amplified like the input's), whichever is
+    # larger, but never above a fixed cap per width; the largest pointwise
+    # error is held to the same bar, so a single wrong mode cannot hide in the
+    # L2 norm.
     grid, eta, phi = _implicit_case(math.inf, 0.3)
     unit = 2.0 ** -24 if prec == 0 else 2.0 ** -53
-    r = np.random.default_rng(210)
-    de = eta * (1 + unit * r.standard_normal(eta.shape))
-    dp = phi * (1 + unit * r.standard_normal(phi.shape))
     for diag in (sbi.SBI_DIAG_ESBI, sbi.SBI_DIAG_HOS):
         ctx = sbi.Context([(grid.nx, 1, grid.Lx, 1.0)], 9.81, None, h0=math.inf, precision=prec,
                           alias_frac=alpha, diagnostic=diag, set_state_dealias=0)
@@ -661,14 +721,24 @@ def test_other_mask_widths_match_oracle(sbi, prec, alpha):
         else:
             f = lambda e, p: O.vertical_velocity(e, p, None, math.inf, grid, alpha=alpha)
         Vo = f(eta, phi)
-        cond = rel(f(de, dp), Vo)
-        assert rel(V, Vo) < max(TOL[prec], 20.0 * cond)
+        conds = []
+        for seed in range(210, 215):
+            r = np.random.default_rng(seed)
+            de = eta * (1 + unit * r.standard_normal(eta.shape))
+            dp = phi * (1 + unit * r.standard_normal(phi.shape))
+            conds.append(rel(f(de, dp), Vo))
+        bar = min(max(TOL[prec], 50.0 * float(np.median(conds))), MASK_BAR_CAP[prec][alpha])
+        print(f"alpha {alpha:.3f} diag {diag} prec {prec}: rel {rel(V, Vo):.2e} "
+              f"max {maxrel(V, Vo):.2e} bar {bar:.2e}")
+        assert rel(V, Vo) < bar and maxrel(V, Vo) < bar
     nx, ny, Lx, Ly, h0 = 64, 32, 6.0, 4.0, 0.8
     g2, pb, e2, p2 = _case(nx, ny, Lx, Ly, h0, True, seed=200)
     ctx = sbi.Context([(nx, ny, Lx, Ly)], 9.81, [h0 - pb.delta], h0=h0, precision=prec, alias_frac=alpha,
                       set_state_dealias=0)
     ctx.set_state(0, e2, p2)
-    assert rel(ctx.vertical_velocity(0), O.vertical_velocity(e2, p2, pb.delta, h0, g2, alpha=alpha)) < TOL[prec]
+    V2 = ctx.vertical_velocity(0)
+    Vo2 = O.vertical_velocity(e2, p2, pb.delta, h0, g2, alpha=alpha)
+    assert rel(V2, Vo2) < TOL[prec] and maxrel(V2, Vo2) < TOL_MAX[prec]
 
 
 def test_hos_option_validation(sbi):

@@ -1,11 +1,15 @@
 """GPU checks on the workloads at their full sizes, in the launch configuration
 the benchmark uses, plus failure detection and checkpoint/restart.
 
-Full-size outputs are compared with the oracle where it runs in seconds
-(1-D grids, 256^2 and 512^2 members); for the 4096 x 2048 variable-depth grid
-the checks are properties that hold at any size: agreement of the FP32 and FP64
-paths, equivariance under a shift by one grid cell, linearity of V in phi~,
-and exact mass conservation.
+Full-size outputs are compared with the oracle element by element: the 1-D
+grids, the 512^2 Stokes wave, the edge members of every graph branch of the
+96-member batch, and V of the 4096 x 2048 variable-depth sea (one oracle
+evaluation, about a minute of CPU time).  Each comparison bounds the relative
+L2 error and the largest pointwise error relative to max|V| (``maxrel``), so
+that one wrong row or block tail cannot hide in the L2 norm of a large field.
+For the 4096 x 2048 grid a few properties that hold at any size are checked as
+well: equivariance under a shift by one grid cell, linearity of V in phi~ and
+exact mass conservation.
 """
 import math
 
@@ -28,6 +32,18 @@ def sbi():
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def maxrel(a, b):
+    """Largest pointwise error relative to the largest |b|."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# V after one evaluation: relative L2 (the stated tolerance) and the largest
+# pointwise error relative to max|V|, per precision (SBI_FP32 = 0, SBI_FP64 = 1)
+TOL_L2 = {0: 1e-5, 1: 1e-12}
+TOL_MAX = {0: 1e-5, 1: 1e-11}
 
 
 def problem_of(wl, m):
@@ -131,26 +147,67 @@ def test_stokes_full_size_diagnostic(sbi, prec, tol):
     assert rel(ctx.vertical_velocity(0), O.vertical_velocity(eta, phi, None, m.h0, pb.grid)) < tol
 
 
+# The first and last member of every graph branch of the benchmark batch: the
+# 256^2 group (members 0..63) runs as one branch, the 512^2 group as two
+# (64..79 and 80..95).
+BATCH_EDGE_MEMBERS = (0, 63, 64, 79, 80, 95)
+
+
 def test_crossing_members_in_the_bench_batch(sbi):
-    # The benchmark's 96-member batch (FP32): the first 256^2 and the first
-    # 512^2 member after one RK4 step against the oracle.
+    # The benchmark's 96-member batch (FP32) after one RK4 step: the edge
+    # members of every graph branch against the oracle, state and V.
     wl = W.crossing_batch()
     ctx = context_of(sbi, wl, list(range(len(wl.members))), 0, check_finite=1)
     start = {}
     for i, m in enumerate(wl.members):
-        if i in (0, 64):
+        if i in BATCH_EDGE_MEMBERS:
             # both sides start from the same projected (dealiased, filtered) state
             pb = problem_of(wl, m)
             start[i] = (pb, O.project(pb, m.eta), O.project(pb, m.phi))
             ctx.set_state(i, start[i][1], start[i][2])
         else:
             ctx.set_state(i, m.eta, m.phi)
+    for i in BATCH_EDGE_MEMBERS:
+        pb, e0, p0 = start[i]
+        Vo = O.vertical_velocity(e0, p0, None, pb.h0, pb.grid, order=wl.order, alpha=wl.alpha)
+        V = ctx.vertical_velocity(i)
+        print(f"member {i}: V rel {rel(V, Vo):.2e} max {maxrel(V, Vo):.2e}")
+        assert rel(V, Vo) < TOL_L2[0] and maxrel(V, Vo) < TOL_MAX[0], i
     ctx.step(wl.dt, 1)
-    for i in (0, 64):
+    for i in BATCH_EDGE_MEMBERS:
         pb, e0, p0 = start[i]
         eo, po = O.step(pb, e0, p0, wl.dt, 1)
         e, p = ctx.get_state(i)
-        assert rel(e, eo) < 1e-5 and rel(p, po) < 1e-5
+        print(f"member {i}: eta rel {rel(e, eo):.2e} max {maxrel(e, eo):.2e}, "
+              f"phi rel {rel(p, po):.2e} max {maxrel(p, po):.2e}")
+        assert rel(e, eo) < 1e-5 and rel(p, po) < 1e-5, i
+        assert maxrel(e, eo) < 1e-5 and maxrel(p, po) < 1e-5, i
+
+
+@pytest.fixture(scope="module")
+def large_variable_oracle():
+    """The 4096 x 2048 variable-depth sea, its projected state and the
+    oracle's V of that state (evaluated once for the module)."""
+    wl = W.large_variable()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    Vo = O.vertical_velocity(eta, phi, m.delta, m.h0, pb.grid, order=wl.order, alpha=wl.alpha)
+    return wl, m, eta, phi, Vo
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_large_variable_matches_oracle(sbi, large_variable_oracle, prec):
+    # Config 5 at full size (k_row<4096>, k_col<2048>, variable depth with
+    # delta up to 0.3 h): V after one evaluation against the FP64 oracle.
+    wl, m, eta, phi, Vo = large_variable_oracle
+    ctx = context_of(sbi, wl, [0], prec)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    ctx.close()
+    print(f"large_variable prec {prec}: V rel {rel(V, Vo):.2e} max {maxrel(V, Vo):.2e}")
+    assert rel(V, Vo) < TOL_L2[prec]
+    assert maxrel(V, Vo) < TOL_MAX[prec]
 
 
 def test_large_variable_depth_properties(sbi):

@@ -42,13 +42,41 @@ def test_invariants_noalloc_matches_context(prec):
     ctx.close()
 
 
-def test_invariants_noalloc_rejects_oversize_and_null():
+def test_invariants_noalloc_rejects_bad_calls_before_any_launch():
+    # Every rejection happens on the host, before a kernel is launched: the
+    # C entry point's NULL, grid, gravity and size checks (called directly),
+    # and the binding's check that each field holds nx*ny values.
+    import ctypes as C
     torch = pytest.importorskip("torch")
     import __graft_entry__ as g
     g.build()
     from paper_2310_19840_gb300 import sbi
 
-    x = torch.zeros(4, dtype=torch.float64, device="cuda")
-    with pytest.raises(sbi.SbiError) as ei:
-        sbi.invariants_noalloc((8192, 8192, 1.0, 1.0), 9.81, x, x, x)
-    assert ei.value.code == sbi.SBI_EINVAL and "limit" in str(ei.value)
+    lib = sbi.load()
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    p = x.data_ptr()
+    m, e = C.c_double(), C.c_double()
+
+    def call(grid, gravity, eta=p, phi=p, V=p):
+        gr = sbi.sbi_grid(*grid)
+        rc = lib.sbi_invariants_noalloc(C.byref(gr), gravity, eta, phi, V, None,
+                                        C.byref(m), C.byref(e))
+        return rc, lib.sbi_noalloc_last_error().decode()
+
+    rc, msg = call((8, 8, 1.0, 1.0), 9.81, eta=None)
+    assert rc == sbi.SBI_EINVAL and "NULL" in msg
+    rc, msg = call((0, 8, 1.0, 1.0), 9.81)
+    assert rc == sbi.SBI_EINVAL and "bad grid" in msg
+    rc, msg = call((8, 8, 1.0, 1.0), 0.0)
+    assert rc == sbi.SBI_EINVAL and "gravity" in msg
+    rc, msg = call((8192, 8192, 1.0, 1.0), 9.81)
+    assert rc == sbi.SBI_EINVAL and "limit" in msg
+    # a valid call still works after the rejected ones
+    rc, msg = call((8, 8, 1.0, 1.0), 9.81)
+    assert rc == sbi.SBI_OK and m.value == 0.0 and e.value == 0.0
+    # the binding refuses fields shorter than the grid (the kernel would read
+    # past them) and host arrays
+    with pytest.raises(ValueError):
+        sbi.invariants_noalloc((16, 8, 1.0, 1.0), 9.81, x, x, x)
+    with pytest.raises(ValueError):
+        sbi.invariants_noalloc((8, 8, 1.0, 1.0), 9.81, x.cpu(), x, x)
