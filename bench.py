@@ -55,18 +55,44 @@ def parse():
     ap.add_argument("--members", default=None,
                     help="crossing_batch only: 'S,L' small (256^2) and large (512^2) members "
                          "instead of 64,32 (for profiling runs)")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "split"],
+                    help="N > 1: every rank advances its own batch of realisations "
+                         "(replicas, weak scaling), or the one batch is split over the ranks "
+                         "by cost (split, strong scaling)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="instead of timing: run the workload's configured number of steps "
+                         "in FP32 and in FP64 on the GPU and print their differences "
+                         "(eta, phi~, energy drift) as one JSON line")
+    ap.add_argument("--accuracy-steps", type=int, default=None,
+                    help="with --accuracy: steps instead of the workload's run length")
+    ap.add_argument("--state-fp64", action="store_true",
+                    help="FP32 path with the RK4 state and sums in FP64 instead of double-single")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU time of each oracle baseline sample (1 process and all cores)")
     return ap.parse_args()
 
 
-def make_workload(name, members=None, rank=0):
-    """The workload of one rank.  Ranks are independent replicas (weak
-    scaling): on the batched crossing seas rank r advances its own set of
-    realisations (random phases seeded from 1000 + 96 r), no data is exchanged."""
+def make_workload(name, members=None, rank=0, world=1, shard="replicas"):
+    """The workload of one rank.  With replicas (weak scaling) rank r advances
+    its own set of realisations of the batched crossing seas (random phases
+    seeded from 1000 + 96 r); with split (strong scaling) the one batch of
+    seed 1000 is divided over the ranks by cost (largest first into the
+    lightest rank) and rank r advances its share.  No data is exchanged."""
     import workloads as W
     if name == "crossing_batch":
         s, l = (64, 32)
         if members:
             s, l = (int(v) for v in members.split(","))
+        if shard == "split" and world > 1:
+            from paper_2310_19840_gb300 import shard as S
+            wl = W.crossing_batch(n_small=s, n_large=l, seed0=1000)
+            mine = S.partition([(m.nx, m.ny) for m in wl.members], world)[rank]
+            wl.notes["global_members"] = mine
+            wl.notes["global_count"] = len(wl.members)
+            wl.notes["global_points"] = wl.points
+            wl.notes["global_shapes"] = _shape_counts(wl.members)
+            wl.members = [wl.members[i] for i in mine]
+            return wl
         return W.crossing_batch(n_small=s, n_large=l, seed0=1000 + (s + l) * rank)
     return getattr(W, name)()
 
@@ -82,16 +108,44 @@ def reduce_max(value, world, device=None):
     return float(t.item())
 
 
-def workload_config(wl):
+def _shape_counts(members):
     shapes = {}
-    for m in wl.members:
+    for m in members:
         key = f"{m.nx}x{m.ny}"
         shapes[key] = shapes.get(key, 0) + 1
-    cfg = {"workload": wl.name, "members": shapes, "points": wl.points, "order": wl.order,
+    return shapes
+
+
+INTEGRATOR_NAMES = {"rk4": "classical RK4", "lawson": "lawson (integrating factor, RK4 stages)",
+                    "rk45": "integrating factor, Cash-Karp 5(4) pair, fixed step"}
+
+
+def arm_config(args, wl, world):
+    """The config dict of a JSON line; both arms print the same one."""
+    cfg = workload_config(wl)
+    cfg["integrator"] = INTEGRATOR_NAMES[args.integrator]
+    cfg["diagnostic"] = args.diagnostic
+    if args.state_fp64:
+        cfg["state"] = "FP64 (state_fp64)"
+    if world == 1:
+        cfg["parallelism"] = "single GPU"
+    elif args.shard == "split":
+        cfg["parallelism"] = f"batch split over {world} GPUs by cost"
+    else:
+        cfg["parallelism"] = f"replicas on {world} GPUs"
+    return cfg
+
+
+def workload_config(wl):
+    """The workload a line is measured on (for a batch split over ranks: the
+    whole batch)."""
+    shapes = wl.notes.get("global_shapes") or _shape_counts(wl.members)
+    points = wl.notes.get("global_points", wl.points)
+    cfg = {"workload": wl.name, "members": shapes, "points": points, "order": wl.order,
            "alias_frac": wl.alpha, "dt": wl.dt,
            "filter": bool(wl.filt_beta1 > 0), "sponge": wl.sponge_w is not None,
            "variable_depth": any(m.delta is not None for m in wl.members),
-           "l2": ("inputs larger than L2 (no flush needed)" if wl.points * 150 > 129e6 else
+           "l2": ("inputs larger than L2 (no flush needed)" if points * 150 > 129e6 else
                   "working set fits in L2 (about 150 B per point, not flushed): small-workload timing")}
     if wl.wavemaker:
         cfg["wavemaker"] = {"components": len(wl.wavemaker["amp"]), "x0": wl.wavemaker["x0"]}
@@ -276,69 +330,210 @@ def time_steps(ctx, torch, stream, dt, steps, warmup):
     return ev0.elapsed_time(ev1) / 1000.0
 
 
-def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4", diagnostic="esbi"):
-    """Time the FP64 oracle on a bounded sample: whole RK4 steps of members
-    drawn in workload order, until about target_s seconds of CPU work."""
-    from oracle import sbi_oracle as O
-    import numpy as np
-    t_tot, pts, steps_done = 0.0, 0, 0
-    members = []
-    # one member of each distinct shape, in workload proportion order
-    seen = set()
+def cpu_oracle_sample(wl, target_s=10.0, integrator="rk4", diagnostic="esbi", parallel=True):
+    """The FP64 oracle timed on the host on a bounded sample of the workload:
+    whole single-member RK4 steps cycling over the member shapes, about
+    target_s seconds of CPU time in one process (one thread) and, with
+    `parallel`, as much again in every host core at once (spawned processes,
+    one single-threaded oracle each).  The reported value is the all-core
+    aggregate when it was measured, the one-thread rate otherwise."""
+    jobs = _oracle_jobs(wl)
+    pts, steps_done, t_tot = _oracle_steps(jobs, target_s, integrator, diagnostic)
+    one = pts / t_tot
+    shapes = ",".join(f"{j['member'].nx}x{j['member'].ny}" for j in jobs)
+    out = {"value": one, "unit": UNIT, "cores": 1, "threads": 1, "kind": "oracle",
+           "sample": f"{steps_done} single-member RK4 steps cycling over member shapes [{shapes}]"
+                     f" ({t_tot:.1f} s of CPU time) in one process",
+           "one_thread_value": one}
+    out.update(host_info())
+    if parallel and (os.cpu_count() or 1) > 1:
+        par = cpu_oracle_parallel(wl, target_s, integrator, diagnostic)
+        out["value"] = par["value"]
+        out["cores"] = par["processes"]
+        out["threads"] = par["processes"]
+        out["all_cores_value"] = par["value"]
+        out["sample"] += (f"; then {par['processes']} single-threaded processes at once, "
+                          f"{par['steps']} steps ({par['cpu_seconds']:.1f} s of CPU time in all): "
+                          "value = sum of their rates")
+    return out
+
+
+def host_info():
+    """Host CPU model and logical core count (for the oracle baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def _oracle_jobs(wl):
+    """One member of each distinct shape, in workload order, with what a
+    worker process needs to step it."""
+    seen, jobs = set(), []
     for m in wl.members:
         key = (m.nx, m.ny)
-        if key not in seen:
-            seen.add(key)
-            members.append(m)
-    i = 0
-    while t_tot < target_s and i < 64:
-        m = members[i % len(members)]
+        if key in seen:
+            continue
+        seen.add(key)
+        jobs.append({"member": m, "gravity": wl.gravity, "order": wl.order, "alpha": wl.alpha,
+                     "sponge_w": wl.sponge_w, "sponge_nu": wl.sponge_nu,
+                     "filt_beta1": wl.filt_beta1, "filt_beta2": wl.filt_beta2, "k_ref": wl.k_ref,
+                     "wavemaker": wl.wavemaker, "dt": wl.dt})
+    return jobs
+
+
+def _oracle_steps(jobs, target_s, integrator, diagnostic, start=0):
+    """Whole single-member RK4 steps of the oracle, cycling over the jobs from
+    `start`, until about target_s seconds: (points, steps, seconds)."""
+    from oracle import sbi_oracle as O
+    import numpy as np
+    t_tot, pts, steps_done, i = 0.0, 0, 0, start
+    while t_tot < target_s and steps_done < 64:
+        j = jobs[i % len(jobs)]
+        m = j["member"]
+        wm = j["wavemaker"]
         g = O.Grid(m.nx, m.ny, m.Lx, m.Ly)
-        pb = O.Problem(g, wl.gravity, m.h0, delta=m.delta, order=wl.order, alpha=wl.alpha,
-                       sponge_w=wl.sponge_w, sponge_nu=wl.sponge_nu, filt_beta1=wl.filt_beta1,
-                       filt_beta2=wl.filt_beta2, k_ref=wl.k_ref,
-                       wavemaker=None if not wl.wavemaker else O.Wavemaker(
-                           np.array(wl.wavemaker["amp"]), np.array(wl.wavemaker["omega"]),
-                           np.array(wl.wavemaker["phase"]), wl.wavemaker["x0"]))
-        t0 = time.perf_counter()
+        pb = O.Problem(g, j["gravity"], m.h0, delta=m.delta, order=j["order"], alpha=j["alpha"],
+                       sponge_w=j["sponge_w"], sponge_nu=j["sponge_nu"], filt_beta1=j["filt_beta1"],
+                       filt_beta2=j["filt_beta2"], k_ref=j["k_ref"],
+                       wavemaker=None if not wm else O.Wavemaker(
+                           np.array(wm["amp"]), np.array(wm["omega"]), np.array(wm["phase"]), wm["x0"]))
         pb.integrator = integrator
         pb.diagnostic = diagnostic
-        O.step(pb, m.eta, m.phi, wl.dt, 1)
+        t0 = time.perf_counter()
+        O.step(pb, m.eta, m.phi, j["dt"], 1)
         t_tot += time.perf_counter() - t0
         pts += m.nx * m.ny
         steps_done += 1
         i += 1
-    shapes = ",".join(f"{m.nx}x{m.ny}" for m in members)
-    return {"value": pts / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps_done} single-member RK4 steps cycling over member shapes [{shapes}]"
-                      f" ({t_tot:.1f} s of CPU time)"}
+    return pts, steps_done, t_tot
+
+
+def _oracle_worker(payload):
+    jobs, target_s, integrator, diagnostic, start = payload
+    return _oracle_steps(jobs, target_s, integrator, diagnostic, start)
+
+
+def cpu_oracle_parallel(wl, target_s, integrator="rk4", diagnostic="esbi", processes=None):
+    """The oracle in `processes` spawned single-threaded processes at once (all
+    host cores by default), each stepping single members for about target_s
+    seconds: the aggregate rate is the sum of the processes' rates."""
+    import multiprocessing as mp
+    procs = processes or os.cpu_count() or 1
+    jobs = _oracle_jobs(wl)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(jobs, target_s, integrator, diagnostic, w) for w in range(procs)])
+    rate = sum(p / t for p, _, t in res if t > 0)
+    steps = sum(s for _, s, _ in res)
+    return {"value": rate, "processes": procs, "steps": steps,
+            "cpu_seconds": sum(t for _, _, t in res)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, on the same
+    workload, metric and config as the GB300 arm.  Each step is a bounded
+    sample: every host core steps single members of the workload's shapes
+    for about 2 s (spawned single-threaded processes); the value is the mean
+    aggregate rate over the timed steps."""
+    import multiprocessing as mp
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = make_workload(args.workload)
-    total_t, total_pts = 0.0, 0
-    samples = []
-    for k in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(wl, target_s=2.0, integrator=args.integrator, diagnostic=args.diagnostic)
-        if k >= args.warmup:
-            pts_s = r["value"]
-            samples.append(pts_s)
+    wl = make_workload(args.workload, args.members, 0, world, args.shard)
+    jobs = _oracle_jobs(wl)
+    procs = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    samples, cpu_s, nsteps = [], 0.0, 0
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for k in range(args.warmup + args.steps):
+            res = pool.map(_oracle_worker, [(jobs, 2.0, args.integrator, args.diagnostic, w + k)
+                                            for w in range(procs)])
+            if k >= args.warmup:
+                samples.append(sum(p / t for p, _, t in res if t > 0))
+                cpu_s += sum(t for _, _, t in res)
+                nsteps += sum(s for _, s, _ in res)
     value = sum(samples) / len(samples)
+    shapes = ",".join(f"{j['member'].nx}x{j['member'].ny}" for j in jobs)
+    cpu = {"value": value, "unit": UNIT, "cores": procs, "threads": procs, "kind": "oracle",
+           "sample": f"each step: {procs} single-threaded processes at once, each stepping single "
+                     f"members of shapes [{shapes}] for about 2 s; {nsteps} member steps "
+                     f"({cpu_s:.1f} s of CPU time) over the {args.steps} timed steps"}
+    cpu.update(host_info())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True,
+            "scaling": "strong" if (world > 1 and args.shard == "split") else "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(wl), integrator=args.integrator, diagnostic=args.diagnostic),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: single-member RK4 steps of the workload's "
-                                       "member shapes for about 2 s of CPU time"},
+            "config": arm_config(args, wl, world), "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def accuracy_run(args, sbi, torch, stream, wl, integ, diag):
+    """The workload's configured run (or --accuracy-steps) in FP64 and in FP32
+    on the GPU from the same initial state: per member the relative L2
+    difference of eta and phi~ at the end, each path's relative energy drift
+    (E_end - E_0) / E_0 and the difference of the two drifts; the JSON record
+    gives member 0 and the worst member."""
+    import numpy as np
+    steps = args.accuracy_steps or wl.steps
+    out = {}
+    t_run = {}
+    for prec in (sbi.SBI_FP64, sbi.SBI_FP32):
+        ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag)
+        for i, m in enumerate(wl.members):
+            ctx.set_state(i, m.eta, m.phi)
+        E0 = [ctx.invariants(i)[1] for i in range(len(wl.members))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        left = steps
+        while left > 0:
+            k = min(100, left)
+            ctx.step(wl.dt, k)
+            left -= k
+        torch.cuda.synchronize()
+        t_run[prec] = time.perf_counter() - t0
+        E1 = [ctx.invariants(i)[1] for i in range(len(wl.members))]
+        eta, phi = ctx.get_state_all()
+        out[prec] = (ctx.split(eta), ctx.split(phi), E0, E1)
+        ctx.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    per = []
+    for i in range(len(wl.members)):
+        e64, p64, E0_64, E1_64 = (out[sbi.SBI_FP64][0][i], out[sbi.SBI_FP64][1][i],
+                                  out[sbi.SBI_FP64][2][i], out[sbi.SBI_FP64][3][i])
+        e32, p32, E0_32, E1_32 = (out[sbi.SBI_FP32][0][i], out[sbi.SBI_FP32][1][i],
+                                  out[sbi.SBI_FP32][2][i], out[sbi.SBI_FP32][3][i])
+        d64 = (E1_64 - E0_64) / E0_64
+        d32 = (E1_32 - E0_32) / E0_32
+        per.append({"member": i, "eta_rel_l2": rel(e32, e64), "phi_rel_l2": rel(p32, p64),
+                    "energy_drift_fp64": d64, "energy_drift_fp32": d32,
+                    "drift_difference": abs(d32 - d64)})
+    worst = {k: max(p[k] for p in per) for k in ("eta_rel_l2", "phi_rel_l2", "drift_difference")}
+    return {"accuracy": True, "config": arm_config(args, wl, 1), "steps": steps, "dt": wl.dt,
+            "members": len(wl.members), "member0": per[0], "worst": worst,
+            "largest_fp64_drift": max(abs(p["energy_drift_fp64"]) for p in per),
+            "seconds": {"fp64": t_run[sbi.SBI_FP64], "fp32": t_run[sbi.SBI_FP32]},
+            "note": "FP32 path against the FP64 path of the same library over the run; the "
+                    "energy drifts include the filter's / sponge's dissipation where those are on"}
 
 
 def main():
@@ -358,12 +553,17 @@ def main():
     ge.build()
     from paper_2310_19840_gb300 import sbi
 
-    wl = make_workload(args.workload, args.members, rank)
+    wl = make_workload(args.workload, args.members, rank, world, args.shard)
     prec = sbi.SBI_FP64 if args.precision == "fp64" else sbi.SBI_FP32
     stream = torch.cuda.Stream()
     integ = {"rk4": sbi.SBI_RK4, "lawson": sbi.SBI_LAWSON_RK4, "rk45": sbi.SBI_IF_RK45}[args.integrator]
     diag = sbi.SBI_DIAG_HOS if args.diagnostic == "hos" else sbi.SBI_DIAG_ESBI
-    ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag)
+    if args.accuracy:
+        if rank == 0:
+            print(json.dumps(accuracy_run(args, sbi, torch, stream, wl, integ, diag)), flush=True)
+        return 0
+    ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag,
+                       state_fp64=int(args.state_fp64))
     for i, m in enumerate(wl.members):
         ctx.set_state(i, m.eta, m.phi)
     if args.compare_diagnostics:
@@ -386,7 +586,19 @@ def main():
     clk = clocks.stop()
     secs = reduce_max(secs, world, device="cuda")
     pts = wl.points
-    value = pts * args.steps * world / secs
+    split = world > 1 and args.shard == "split"
+    # whole-job rate: every rank's points (a split batch: the batch's points)
+    job_points = wl.notes["global_points"] if split else pts * world
+    value = job_points * args.steps / secs
+    gathered = None
+    if split:
+        # the invariants of every member of the batch, gathered by one
+        # all-reduce (outside the timed region)
+        from paper_2310_19840_gb300 import shard as S
+        local = {gi: ctx.invariants(li) for li, gi in enumerate(wl.notes["global_members"])}
+        table = S.gather_invariants(wl.notes["global_count"], local, world, device="cuda")
+        gathered = {"members": int(np.count_nonzero(table[:, 1])), "of": wl.notes["global_count"],
+                    "total_mass": float(table[:, 0].sum()), "total_energy": float(table[:, 1].sum())}
 
     # ---- per-kernel roofline: the same K steps with CUDA-event pairs per pass ----
     ctx.profile_enable(True)
@@ -477,30 +689,29 @@ def main():
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         nbytes = 2 * eta_h.numel() * 8
-        e2e = {"value": pts * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        te = reduce_max(te, world, device="cuda")
+        e2e = {"value": (job_points / pts) * pts * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ke,
                "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + sbi_get_state_all(pinned host)"}
         ctx_e.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(wl, target_s=10.0, integrator=args.integrator,
+        cpu = cpu_oracle_sample(wl, target_s=args.cpu_seconds, integrator=args.integrator,
                                 diagnostic=args.diagnostic)
 
-    cfg = workload_config(wl)
-    cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
-    cfg["integrator"] = {"rk4": "classical RK4", "lawson": "lawson (integrating factor, RK4 stages)",
-                         "rk45": "integrating factor, Cash-Karp 5(4) pair, fixed step"}[args.integrator]
-    cfg["diagnostic"] = args.diagnostic
-    cfg["transforms_per_point_step"] = ctx.step_transforms(-1) / wl.points
-    cfg["autotune"] = autotune_summary(ctx.autotune_report())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if split else "weak", "vs_baseline": None,
             "dtype": "f64" if prec == sbi.SBI_FP64 else "f32", "data": "synthetic",
-            "config": cfg, "clocks": clk, "gpu_launches": launches * args.steps,
+            "config": arm_config(args, wl, world), "clocks": clk,
+            "gpu_launches": launches * args.steps,
+            "transforms_per_point_step": ctx.step_transforms(-1) / wl.points,
+            "autotune": autotune_summary(ctx.autotune_report()),
             "model_step_GBps": step_model_gbps, "fused_step_GBps": step_gbps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_arm, "error": err}
+    if gathered:
+        line["invariants_gathered"] = gathered
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

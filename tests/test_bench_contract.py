@@ -27,8 +27,13 @@ def test_reference_arm_line():
     assert d["metric"] == "grid-point RK4 steps/s" and d["unit"] == "pt-steps/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
     assert d["config"]["workload"] == "solitary_1d"
+    # the config dict both arms print (same keys and values for the same flags)
+    assert {"parallelism", "integrator", "diagnostic", "points", "members"} <= d["config"].keys()
+    assert d["config"]["parallelism"] == "single GPU"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    # every host core, one single-threaded oracle process each, and the host named
+    assert cb["cores"] == cb["threads"] == os.cpu_count() == cb["nproc"] and cb["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
@@ -40,6 +45,8 @@ def test_gb300_arm_line():
     assert d["metric"] == "grid-point RK4 steps/s" and d["unit"] == "pt-steps/s" and d["value"] > 0
     assert d["n_gpus"] == 1 and d["steps"] == 5 and d["warmup"] == 3 and d["scaling"] == "weak"
     assert d["config"]["workload"] == "solitary_1d" and d["data"] == "synthetic"
+    ref = run(["--impl", "reference", "--workload", "solitary_1d", "--steps", "1", "--warmup", "1"], 600)
+    assert ref["config"] == d["config"]
     r = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= r.keys()
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
