@@ -162,11 +162,118 @@ __device__ __forceinline__ void group_sync() {
   else __syncthreads();
 }
 
+// Transforms of 128 and 256 points by 16 and 32 threads (radix 8, 8 and a
+// last radix-2 / radix-4 pass) can hand the data from the second pass to the
+// last one by warp shuffles instead of a shared-memory scatter and gather.
+constexpr bool kShuffleLastExchange = true;
+
+template <typename V>
+__device__ __forceinline__ V shfl_xor_cx(V v, int mask) {
+  V r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, mask);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, mask);
+  return r;
+}
+template <typename V>
+__device__ __forceinline__ V pick(bool c, V a, V b) { return c ? a : b; }
+
+// Last pass after the Ls = 8 pass, from registers: before it, thread j holds
+// x[r] = element 64 a + (j & 7) + 8 r with a = j >> 3 (the Stockham order of
+// the Ls = 8 pass); the last pass wants, for butterflies b = j + q T, the
+// elements b + 64 m.  Those sit in the lanes j' = 8 m + (j & 7) of the same
+// row, register (j >> 3) + (T / 8) q, so the exchange is a transpose between
+// the lane bits above 7 and the low register bits: one shuffle stage per lane
+// bit (xor 8, then xor 16), each lane keeping the half of its values that
+// stays and receiving the other half.
+template <int N, int SIGN, typename V>
+__device__ __forceinline__ void last_pass_by_shuffles(V (&x)[8], V* s, int j, const V* __restrict__ tw) {
+  constexpr int T = N / 8;          // 16 or 32 threads per transform
+  constexpr int Ls = 64, RP = N / Ls, Q = 8 / RP;
+  const int b0 = (j >> 3) & 1;
+  V v[Q][RP];
+  if constexpr (RP == 2) {
+    // N = 128: lanes j and j ^ 8 swap the registers of the other's parity
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const V keep = pick(b0, x[2 * q + 1], x[2 * q]);
+      const V recv = shfl_xor_cx(pick(b0, x[2 * q], x[2 * q + 1]), 8);
+      v[q][0] = pick(b0, recv, keep);
+      v[q][1] = pick(b0, keep, recv);
+    }
+  } else {
+    // N = 256: a 4 x 4 transpose per q between lane bits (3, 4) and register
+    // bits (0, 1); register c + 4 q of lane a holds row a, column c
+    const int b1 = (j >> 4) & 1;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      V t[2][2];   // [pair p: column 2 p + b0][row bit 0]
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const V keep = pick(b0, x[4 * q + 2 * p + 1], x[4 * q + 2 * p]);
+        const V recv = shfl_xor_cx(pick(b0, x[4 * q + 2 * p], x[4 * q + 2 * p + 1]), 8);
+        t[p][0] = pick(b0, recv, keep);
+        t[p][1] = pick(b0, keep, recv);
+      }
+      // keep the pair of column a = 2 b1 + b0, send the other one
+      V own[2], oth[2];
+#pragma unroll
+      for (int rb = 0; rb < 2; ++rb) {
+        own[rb] = pick(b1, t[1][rb], t[0][rb]);
+        oth[rb] = shfl_xor_cx(pick(b1, t[0][rb], t[1][rb]), 16);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const bool mine = ((m >> 1) & 1) == b1;
+        v[q][m] = pick(mine, own[m & 1], oth[m & 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = j + q * T;
+    if constexpr (RP == 4 && kProductTwiddles<V>) {
+      const V w1 = twiddle<SIGN>(tw, N, b), w2 = cmul(w1, w1);
+      v[q][1] = cmul(v[q][1], w1);
+      v[q][2] = cmul(v[q][2], w2);
+      v[q][3] = cmul(v[q][3], cmul(w1, w2));
+    } else {
+#pragma unroll
+      for (int m = 1; m < RP; ++m) v[q][m] = cmul(v[q][m], twiddle<SIGN>(tw, N, m * b));
+    }
+    Dft<RP, SIGN, V>::run(v[q]);
+#pragma unroll
+    for (int m = 0; m < RP; ++m) s[pad(j) + pad(q * T) + pad(m * Ls)] = v[q][m];
+  }
+  __syncwarp();
+}
+
 template <int N, int R, int Ls, int SIGN, typename V>
 struct StockhamPass {
   static constexpr bool WARP = (N / R) <= 32;
   __device__ __forceinline__ static void run(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
     constexpr int T = N / R;
+    if constexpr (kShuffleLastExchange && R == 8 && Ls == 8 && (N == 128 || N == 256)) {
+      // the Ls = 8 pass, then the last pass fed by shuffles
+      const int k = j & (Ls - 1);
+      const int base = k * (N / (Ls * R));
+      if constexpr (kProductTwiddles<V>) {
+        const V w1 = twiddle<SIGN>(tw, N, base), w4 = twiddle<SIGN>(tw, N, 4 * base);
+        const V w2 = cmul(w1, w1), w3 = cmul(w1, w2);
+        x[1] = cmul(x[1], w1);
+        x[2] = cmul(x[2], w2);
+        x[3] = cmul(x[3], w3);
+        x[4] = cmul(x[4], w4);
+        x[5] = cmul(x[5], cmul(w4, w1));
+        x[6] = cmul(x[6], cmul(w4, w2));
+        x[7] = cmul(x[7], cmul(w4, w3));
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, N, r * base));
+      }
+      Dft<R, SIGN, V>::run(x);
+      last_pass_by_shuffles<N, SIGN, V>(x, s, j, tw);
+      return;
+    }
     if constexpr (N / Ls >= R) {
       // full pass of radix R
       const int k = j & (Ls - 1);
