@@ -136,6 +136,24 @@ def test_submerged_bar_full_size_steps(sbi, prec, tol):
     assert rel(e, eo) < tol and rel(p, po) < tol
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["solitary_1d", "bar_1d", "stokes_2d"])
+def test_v_after_one_evaluation_per_workload(sbi, name, prec):
+    # V of the workload's (projected) initial state against the oracle, in
+    # the workload's own configuration: relative L2 and pointwise.
+    wl = getattr(W, name)()
+    m = wl.members[0]
+    pb = problem_of(wl, m)
+    eta, phi = O.project(pb, m.eta), O.project(pb, m.phi)
+    ctx = context_of(sbi, wl, [0], prec)
+    ctx.set_state(0, eta, phi)
+    V = ctx.vertical_velocity(0)
+    ctx.close()
+    Vo = O.vertical_velocity(eta, phi, m.delta, m.h0, pb.grid, order=wl.order, alpha=wl.alpha)
+    print(f"{name} prec {prec}: V rel {rel(V, Vo):.2e} max {maxrel(V, Vo):.2e}")
+    assert rel(V, Vo) < TOL_L2[prec] and maxrel(V, Vo) < TOL_MAX[prec]
+
+
 @pytest.mark.parametrize("prec,tol", [(1, 1e-11), (0, 1e-5)])
 def test_stokes_full_size_diagnostic(sbi, prec, tol):
     wl = W.stokes_2d()
