@@ -185,7 +185,10 @@ __device__ __forceinline__ V pick(bool c, V a, V b) { return c ? a : b; }
 // the lane bits above 7 and the low register bits: one shuffle stage per lane
 // bit (xor 8, then xor 16), each lane keeping the half of its values that
 // stays and receiving the other half.
-template <int N, int SIGN, typename V>
+// REGS: leave the result in registers instead of shared memory; thread j
+// then holds element j + r T in x[r] (the last pass computes exactly those:
+// b + 64 m = j + T (q + Q m)).
+template <int N, int SIGN, bool REGS, typename V>
 __device__ __forceinline__ void last_pass_by_shuffles(V (&x)[8], V* s, int j, const V* __restrict__ tw) {
   constexpr int T = N / 8;          // 16 or 32 threads per transform
   constexpr int Ls = 64, RP = N / Ls, Q = 8 / RP;
@@ -242,17 +245,24 @@ __device__ __forceinline__ void last_pass_by_shuffles(V (&x)[8], V* s, int j, co
     }
     Dft<RP, SIGN, V>::run(v[q]);
 #pragma unroll
-    for (int m = 0; m < RP; ++m) s[pad(j) + pad(q * T) + pad(m * Ls)] = v[q][m];
+    for (int m = 0; m < RP; ++m) {
+      if constexpr (REGS) x[q + Q * m] = v[q][m];
+      else s[pad(j) + pad(q * T) + pad(m * Ls)] = v[q][m];
+    }
   }
-  __syncwarp();
+  if constexpr (!REGS) __syncwarp();
 }
 
-template <int N, int R, int Ls, int SIGN, typename V>
+// transforms whose last pass is fed by shuffles (and can end in registers)
+template <int N, int R>
+inline constexpr bool kShuffleFft = kShuffleLastExchange && R == 8 && (N == 128 || N == 256);
+
+template <int N, int R, int Ls, int SIGN, typename V, bool REGS = false>
 struct StockhamPass {
   static constexpr bool WARP = (N / R) <= 32;
   __device__ __forceinline__ static void run(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
     constexpr int T = N / R;
-    if constexpr (kShuffleLastExchange && R == 8 && Ls == 8 && (N == 128 || N == 256)) {
+    if constexpr (kShuffleFft<N, R> && Ls == 8) {
       // the Ls = 8 pass, then the last pass fed by shuffles
       const int k = j & (Ls - 1);
       const int base = k * (N / (Ls * R));
@@ -271,7 +281,7 @@ struct StockhamPass {
         for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, N, r * base));
       }
       Dft<R, SIGN, V>::run(x);
-      last_pass_by_shuffles<N, SIGN, V>(x, s, j, tw);
+      last_pass_by_shuffles<N, SIGN, REGS, V>(x, s, j, tw);
       return;
     }
     if constexpr (N / Ls >= R) {
@@ -306,7 +316,7 @@ struct StockhamPass {
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = s[lb + pad(r * T)];
         group_sync<WARP>();
-        StockhamPass<N, R, Ls * R, SIGN, V>::run(x, s, j, tw);
+        StockhamPass<N, R, Ls * R, SIGN, V, REGS>::run(x, s, j, tw);
       }
     } else {
       // last pass, radix RP = N / Ls < R: butterflies b_q = j + q T (q < R/RP),
@@ -347,6 +357,22 @@ __device__ __forceinline__ void fft_block(V (&x)[R], V* s, int j, const V* __res
     __syncwarp();
   } else {
     StockhamPass<N, R, 1, SIGN, V>::run(x, s, j, tw);
+  }
+}
+
+// The same transform with the thread's own elements of the result in
+// registers on exit: x[r] = X[j + r N/R].  Where the last pass is fed by
+// shuffles it ends there (no final scatter and read-back); otherwise the
+// result is read back from s.  s has no live data on exit either way.
+template <int N, int R, int SIGN, typename V>
+__device__ __forceinline__ void fft_block_regs(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
+  if constexpr (kShuffleFft<N, R>) {
+    StockhamPass<N, R, 1, SIGN, V, true>::run(x, s, j, tw);
+  } else {
+    constexpr int T = N / R;
+    fft_block<N, R, SIGN>(x, s, j, tw);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = s[pad(j) + pad(r * T)];
   }
 }
 

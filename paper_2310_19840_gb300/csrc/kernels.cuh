@@ -371,23 +371,23 @@ k_row(const __grid_constant__ RowParams p) {
       }
       if (op.kind == ROP_WDOT) continue;
     }
-    // one transform call site for every op keeps the kernel's code small
-    const bool c2r = op.kind == ROP_C2R;
-    if (!c2r) __syncthreads();  // scratch free (previous cooperative store done)
-    fft_block<n, R, -1>(x, fb, j, tw);
-    if (c2r) {
-      // inverse transform: the row in physical space, packed as complex pairs
+    if (op.kind == ROP_C2R) {
+      // inverse transform: the row in physical space, packed as complex
+      // pairs; each thread's own elements m = j + r TPR come back in registers
+      fft_block_regs<n, R, -1>(x, fb, j, tw);
       V* slot = slot_base + (op.slot * rpc + rloc) * n;
       V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V z = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
+        const V z = cconj(x[r]);
         slot[m] = z;
         if (out) out[m] = z;
       }
       continue;
     }
+    __syncthreads();  // scratch free (previous cooperative store done)
+    fft_block<n, R, -1>(x, fb, j, tw);
     __syncthreads();  // every row's spectrum ready
     r2c_store<T, NX>(fb_all, fbs, p.buf[op.dst], io, tw);
   }
@@ -554,13 +554,13 @@ k_rk(const __grid_constant__ RkParams p) {
     __syncthreads();
     c2r_input<T, NX>(x, fb, p.W, j, tw);
     row_group_sync<NX>();
-    fft_block<n, R, -1>(x, fb, j, tw);
+    fft_block_regs<n, R, -1>(x, fb, j, tw);   // x[r]: element j + r TPR
     if (p.mode == RK_CORRECT || p.mode == RK_OFFSET) {
       const bool keep = p.mode == RK_CORRECT;   // RK_OFFSET leaves the state unchanged
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
+        const V c = cconj(x[r]);
         SP e = act ? SP::load(E0, m) : SP::zero();
         e.add(0, c.x);
         e.add(1, c.y);
@@ -573,11 +573,11 @@ k_rk(const __grid_constant__ RkParams p) {
       __syncthreads();
       c2r_input<T, NX>(x, fb, p.W, j, tw);
       row_group_sync<NX>();
-      fft_block<n, R, -1>(x, fb, j, tw);
+      fft_block_regs<n, R, -1>(x, fb, j, tw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V c = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
+        const V c = cconj(x[r]);
         SP q = act ? SP::load(P0, m) : SP::zero();
         q.add(0, c.x);
         q.add(1, c.y);
@@ -598,7 +598,7 @@ k_rk(const __grid_constant__ RkParams p) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
-        const V ft = cconj(fb[pad(j) + pad(r * TPR)]);   // fb[pad(m)]
+        const V ft = cconj(x[r]);
         xe[r] = mk<V>(T(0), T(0));
         xp[r] = mk<V>(T(0), T(0));
         if (!act) continue;
@@ -737,7 +737,7 @@ k_col(const __grid_constant__ ColParams p) {
     for (int r = 0; r < RC; ++r) x[r] = act ? src[j + r * TPC] : mk<V>(T(0), T(0));
     if constexpr (NY > 1) {
       group_sync<C::WARP>();  // scratch free
-      fft_block<NY, RC, -1>(x, sc, j, tw);
+      fft_block_regs<NY, RC, -1>(x, sc, j, tw);   // x[r]: mode j + r TPC
     }
     for (int q = p.term_begin[i]; q < p.term_begin[i + 1]; ++q) {
       const ColTerm t = p.terms[q];
@@ -747,7 +747,7 @@ k_col(const __grid_constant__ ColParams p) {
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
         const int ni = j + r * TPC;
-        const V v = (NY > 1) ? sc[pad(j) + pad(r * TPC)] : x[0];   // sc[pad(ni)]
+        const V v = x[r];
         acc[ni] = cadd(acc[ni], cmul_ipow(v, __ldg(tab + ni), ph));
       }
     }
@@ -766,9 +766,9 @@ k_col(const __grid_constant__ ColParams p) {
     }
     if constexpr (NY > 1) {
       group_sync<C::WARP>();
-      fft_block<NY, RC, -1>(x, sc, j, tw);
+      fft_block_regs<NY, RC, -1>(x, sc, j, tw);
 #pragma unroll
-      for (int r = 0; r < RC; ++r) x[r] = cconj(sc[pad(j) + pad(r * TPC)]);
+      for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
     } else {
       x[0] = cconj(x[0]);
     }
