@@ -39,8 +39,10 @@ struct Geometry {
 // Addresses (within one row) of every shared-memory instruction of a
 // Stockham transform of length N by N/R threads: each entry maps the thread
 // index j to an element index.  The last entry is the consumer's read of the
-// natural-order result.
-inline void stockham_pattern(int N, int R, std::vector<std::vector<int>>& ins) {
+// natural-order result.  shuffled: the transform hands its last pass the data
+// by warp shuffles and ends in registers (fft.cuh, kShuffleFft), so only the
+// first pass's scatter and gather touch shared memory.
+inline void stockham_pattern(int N, int R, std::vector<std::vector<int>>& ins, bool shuffled = false) {
   const int T = N / R;
   int Ls = 1;
   auto push = [&](auto f) {
@@ -49,6 +51,11 @@ inline void stockham_pattern(int N, int R, std::vector<std::vector<int>>& ins) {
     ins.push_back(a);
   };
   if (N == 1) return;
+  if (shuffled) {
+    for (int r = 0; r < R; ++r) push([&](int j) { return pad16(j * R) + pad16(r); });
+    for (int r = 0; r < R; ++r) push([&](int j) { return pad16(j) + pad16(r * T); });
+    return;
+  }
   while (true) {
     if (N / Ls >= R) {
       for (int r = 0; r < R; ++r)
@@ -76,10 +83,19 @@ inline int wavefronts(const std::vector<int>& addr, int E) {
   return mx;
 }
 
-// Wavefronts of the per-row (FFT) instructions over all warps of a block.
-inline long long fft_cost(const Geometry& g, int S) {
+// Wavefronts of the per-row (FFT) instructions over all warps of a block;
+// shuffled: see stockham_pattern, plus the writes of the kept modes to the
+// row (element k = j + r TPR < W, r2c_regs in kernels.cuh).
+inline long long fft_cost(const Geometry& g, int S, bool shuffled = false) {
   std::vector<std::vector<int>> ins;
-  stockham_pattern(g.n, g.R, ins);
+  stockham_pattern(g.n, g.R, ins, shuffled);
+  if (shuffled) {
+    for (int r = 0; r < g.R && r * g.TPR < g.W; ++r) {
+      std::vector<int> a(g.TPR);
+      for (int j = 0; j < g.TPR; ++j) a[j] = j + r * g.TPR < g.W ? j + r * g.TPR : -1;
+      ins.push_back(a);
+    }
+  }
   const int threads = g.rpc * g.TPR;
   long long tot = 0;
   for (int w = 0; w * 32 < threads; ++w) {
@@ -87,9 +103,9 @@ inline long long fft_cost(const Geometry& g, int S) {
       std::vector<int> addr;
       for (int t = 32 * w; t < std::min(threads, 32 * w + 32); ++t) {
         const int row = t / g.TPR, j = t % g.TPR;
-        addr.push_back(row * S + f[j]);
+        if (f[j] >= 0) addr.push_back(row * S + f[j]);
       }
-      tot += wavefronts(addr, g.E);
+      if (!addr.empty()) tot += wavefronts(addr, g.E);
     }
   }
   return tot;
@@ -157,10 +173,13 @@ struct RowStrides {
   int fbs, sws;
 };
 
-inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, bool rk) {
+// shuffled: the row transforms end in registers (kShuffleFft); the forward
+// outputs are then written per row and read back by the cooperative store
+// one element each (no Z[k], Z[n-k] pair).
+inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, bool rk, bool shuffled) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int, int, int, bool>, RowStrides> cache;
-  const auto key = std::make_tuple(n, R, TPR, rpc, W, elem_bytes, rk);
+  static std::map<std::tuple<int, int, int, int, int, int, bool, bool>, RowStrides> cache;
+  const auto key = std::make_tuple(n, R, TPR, rpc, W, elem_bytes, rk, shuffled);
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
@@ -169,6 +188,7 @@ inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, 
   const Geometry g{n, R, TPR, rpc, W, 128 / elem_bytes};
   const int fb_len = n + (n >> 4) + 1;
   auto io_reads = [&](int S) {
+    if (shuffled) return coop_cost(g, [&](int rl, int k) { return rl * S + k; });
     return coop_cost(g, [&](int rl, int k) { return rl * S + pad16(k); }) +
            coop_cost(g, [&](int rl, int k) { return rl * S + pad16((n - k) & (n - 1)); });
   };
@@ -177,10 +197,11 @@ inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, 
   };
   RowStrides out{};
   if (rk) {
-    out.fbs = best_stride(fb_len, g.E, [&](int S) { return fft_cost(g, S) + io_reads(S) + staging(S); });
+    out.fbs = best_stride(fb_len, g.E,
+                          [&](int S) { return fft_cost(g, S, shuffled) + io_reads(S) + staging(S); });
     out.sws = 0;
   } else {
-    out.fbs = best_stride(fb_len, g.E, [&](int S) { return fft_cost(g, S) + io_reads(S); });
+    out.fbs = best_stride(fb_len, g.E, [&](int S) { return fft_cost(g, S, shuffled) + io_reads(S); });
     out.sws = best_stride(std::max(W, 1), g.E, staging);
   }
   std::lock_guard<std::mutex> lock(mu);

@@ -232,6 +232,53 @@ __device__ __forceinline__ void r2c_store(const cx<T>* fb_all, int fbs, const Bu
   }
 }
 
+// Packed forward real FFT, output side, for rows whose transform ends in
+// registers (kShuffleFft): thread j holds Z[j + r TPR] in x[r] and forms
+// X[k] = 1/2 (Z[k] + Z*[n-k]) - i/2 e^{-2 pi i k / NX} (Z[k] - Z*[n-k]) for its
+// own k = j + r TPR < W, writing it to the row's buffer xrow[k].  Z[n-k] sits
+// in lane (TPR - j) mod TPR of the row, register R-1-r (thread 0: its own
+// register (R - r) mod R), so one shuffle per kept register fetches it.  The
+// twiddle is e^{-2 pi i j / NX} times e^{-2 pi i r / 16} (TPR / NX = 1/16)
+// in FP32, the table entry in FP64.
+template <typename T, int NX>
+__device__ __forceinline__ void r2c_regs(const cx<T> (&x)[RowCfg<NX>::R], cx<T>* xrow, int W, int j,
+                                         const cx<T>* __restrict__ tw) {
+  using V = cx<T>;
+  using C = RowCfg<NX>;
+  constexpr int R = C::R, TPR = C::TPR;
+  static_assert(R == 8 && 2 * R * TPR == NX, "rows of the shuffle-fed transforms only");
+  constexpr bool kProd = kProductTwiddles<V>;     // FP64: every twiddle from the table
+  const V wj = __ldg(tw + tw_off(NX) + j);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (r * TPR >= W) break;                       // no thread keeps a mode here
+    V zc;
+    zc.x = __shfl_sync(0xffffffffu, x[R - 1 - r].x, (TPR - j) & (TPR - 1), TPR);
+    zc.y = __shfl_sync(0xffffffffu, x[R - 1 - r].y, (TPR - j) & (TPR - 1), TPR);
+    if (j == 0) zc = x[(R - r) & (R - 1)];
+    zc = cconj(zc);
+    const V zk = x[r];
+    const int k = j + r * TPR;
+    V w;
+    if constexpr (kProd) w = r == 0 ? wj : cmul(wj, root16<-1, V>(r));
+    else w = __ldg(tw + tw_off(NX) + k);
+    const V sum = cadd(zk, zc);
+    const V d = cmul(csub(zk, zc), w);
+    if (k < W) xrow[k] = cscale(csub(sum, rot<1>(d)), T(0.5));
+  }
+}
+
+// Block-cooperative store of the rows' kept modes xrow[k] (row stride fbs) to
+// the transposed mixed field dst.
+template <typename T>
+__device__ __forceinline__ void store_modes(const cx<T>* x_all, int fbs, const BufRef& dst, const RowIO& io) {
+  using V = cx<T>;
+  if (!io.ok) return;
+  V* out = reinterpret_cast<V*>(dst.ptr);
+  const V* xr = x_all + io.rl * fbs;
+  for (int k = io.k0; k < io.W; k += io.kstep) out[io.at(dst, k)] = xr[k];
+}
+
 template <typename T>
 __device__ __forceinline__ T ipow(T v, int p) {
   T r = T(1);
@@ -387,9 +434,17 @@ k_row(const __grid_constant__ RowParams p) {
       continue;
     }
     __syncthreads();  // scratch free (previous cooperative store done)
-    fft_block<n, R, -1>(x, fb, j, tw);
-    __syncthreads();  // every row's spectrum ready
-    r2c_store<T, NX>(fb_all, fbs, p.buf[op.dst], io, tw);
+    if constexpr (kShuffleFft<n, R>) {
+      // spectrum in registers, kept modes formed in the row's own threads
+      fft_block_regs<n, R, -1>(x, fb, j, tw);
+      r2c_regs<T, NX>(x, fb, p.W, j, tw);
+      __syncthreads();  // every row's kept modes ready
+      store_modes<T>(fb_all, fbs, p.buf[op.dst], io);
+    } else {
+      fft_block<n, R, -1>(x, fb, j, tw);
+      __syncthreads();  // every row's spectrum ready
+      r2c_store<T, NX>(fb_all, fbs, p.buf[op.dst], io, tw);
+    }
   }
 }
 
@@ -907,7 +962,8 @@ cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
   if (p.rpc < 1 || p.rpc > C::RPC_MAX) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
   RowParams q = p;
-  const bank::RowStrides rs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false);
+  const bank::RowStrides rs =
+      bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false, kShuffleFft<C::n, C::R>);
   q.fbs = rs.fbs;
   q.sws = rs.sws;
   const size_t smem = row_smem<T, NX>(q.rpc, q.fbs, q.sws, q.nslots);
@@ -922,7 +978,7 @@ cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
   if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
   RkParams q = p;
-  q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true).fbs;
+  q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true, false).fbs;
   const size_t smem = sizeof(cx<T>) * (size_t)q.rpc * q.fbs;
   if (q.state64 && sizeof(T) == 4) k_rk<T, NX, double><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
   else k_rk<T, NX, T><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
