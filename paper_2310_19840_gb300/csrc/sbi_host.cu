@@ -890,8 +890,10 @@ struct Planner {
   }
 
   // (M Lambda - 1) correction of the FP64 state, applied through RK_CORRECT.
-  void plan_project(std::vector<Pass>& out, bool with_filter) {
-    out.push_back(plan_rk(RK_ENTRY, 0, 0.0, 1));
+  // entry = false: the pass before already wrote the state's working copies
+  // (eta_m, phi_m) with its tail.
+  void plan_project(std::vector<Pass>& out, bool with_filter, bool entry = true) {
+    if (entry) out.push_back(plan_rk(RK_ENTRY, 0, 0.0, 1));
     const int depth = with_filter ? 3 : 0;
     out.push_back(col({{"eta_m", {term(0, 1.0, 0, 0, 0, 0)}}, {"phi_m", {term(1, 1.0, 0, 0, 0, 0)}}},
                       {{"Ce", term(0, 1.0, 0, depth, 0, 0, 2)}, {"Cp", term(1, 1.0, 0, depth, 0, 0, 2)}},
@@ -1737,15 +1739,20 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
     }
     if (kind == SK_RK45_B) {
       // accept the step: the order-5 offsets into the state
-      all.push_back(pl.plan_rk(RK_CORRECT, 4, 0.0, c->filter_on() ? 0 : 1, "De", "Dp"));
-      if (c->filter_on()) pl.plan_project(all, true);
+      // the accepted state's working copies come from this pass's tail; the
+      // filter's projection then needs no entry pass of its own
+      all.push_back(pl.plan_rk(RK_CORRECT, 4, 0.0, 1, "De", "Dp"));
+      if (c->filter_on()) pl.plan_project(all, true, false);
       if (pl.oom) *oom = true;
       out.push_back(std::move(all));
       continue;
     }
     for (int s = 1; s <= 4; ++s) {
       const double t_off = (s == 1 ? 0.0 : (s == 4 ? 1.0 : 0.5)) * dt;  // stage times
-      const int tail = (s < 4 || !c->filter_on()) ? 1 : 0;
+      // every stage's tail writes the working copies of its state; after the
+      // last stage they are those of the new state, which the filter's
+      // projection reads (so it needs no entry pass)
+      const int tail = 1;
       if (c->opt.integrator == SBI_LAWSON_RK4) {
         // integrating factor: stage 1 is u_n (eta_m, phi_m), the later stages'
         // working copies live in (eta_s, phi_s)
@@ -1766,7 +1773,7 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
         all.push_back(pl.plan_rk(RK_STAGE, s, dt, tail));
       }
     }
-    if (c->filter_on()) pl.plan_project(all, true);
+    if (c->filter_on()) pl.plan_project(all, true, false);
     if (pl.oom) *oom = true;
     out.push_back(std::move(all));
   }

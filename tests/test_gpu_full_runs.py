@@ -10,8 +10,10 @@ relative to the largest sampled |value|) and in its energy drift.
 
 Bars: FP64 path 1e-8 on the samples and 1e-9 on the drift (rounding grows
 over thousands of steps but stays far below the method's own error); FP32
-path 1e-4 on the samples and on the drift (the stated tolerance on energy
-drift over a run).
+path 1e-4 on the drift (the stated tolerance on energy drift over a run) and
+on the samples, except for the 512^2 Stokes wave: over its 31 periods at
+H/d = 0.5 the FP32 path's phase drifts from the FP64 path's (eta 6e-4
+relative L2 after 2000 steps), so its samples are held to 3e-3.
 """
 import json
 import os
@@ -26,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 BARS = {1: (1e-8, 1e-9), 0: (1e-4, 1e-4)}   # (samples, energy drift) per precision
+FP32_SAMPLE_BAR = {"stokes_2d": 3e-3}
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +66,7 @@ def _run(sbi, name, prec, steps):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-@pytest.mark.parametrize("name", ["solitary_1d", "bar_1d"])
+@pytest.mark.parametrize("name", ["solitary_1d", "bar_1d", "stokes_2d"])
 def test_full_run_matches_oracle_run(sbi, name, prec):
     path = os.path.join(GOLDEN, f"oracle_run_{name}.json")
     gold = json.load(open(path))
@@ -76,5 +79,7 @@ def test_full_run_matches_oracle_run(sbi, name, prec):
     print(f"{name} prec {prec} after {gold['steps']} steps: eta {err_e:.2e} phi {err_p:.2e} "
           f"drift gpu {drift:+.3e} oracle {gold['energy_drift_rel']:+.3e}")
     bar_s, bar_d = BARS[prec]
+    if prec == 0:
+        bar_s = FP32_SAMPLE_BAR.get(name, bar_s)
     assert err_e < bar_s and err_p < bar_s
     assert d_err < bar_d
