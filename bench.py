@@ -690,7 +690,7 @@ def main():
         te = time.perf_counter() - t0
         nbytes = 2 * eta_h.numel() * 8
         te = reduce_max(te, world, device="cuda")
-        e2e = {"value": (job_points / pts) * pts * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": job_points * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ke,
                "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + sbi_get_state_all(pinned host)"}
         ctx_e.close()
