@@ -715,6 +715,9 @@ k_rk(const __grid_constant__ RkParams p) {
 // Column-pass geometry: 8 elements per thread (one warp per column at 256,
 // two at 512, ...).  In FP32 columns of at least a warp are compiled for four
 // resident blocks per SM (64 registers).
+// 512-point columns by the even/odd split (col_fft_eo)
+constexpr bool kColEvenOdd = true;
+
 template <typename T, int NY>
 struct ColCfg {
   static constexpr int RC = NY == 1 ? 1 : cmin(8, NY);
@@ -723,9 +726,45 @@ struct ColCfg {
   // 8-byte elements: 256 threads per block; 16-byte elements: half the columns
   static constexpr int CPB = NY == 1 ? 256 : cmax(1, 256 / TPC / (int)(sizeof(T) / 4));
   static constexpr int THREADS = TPC * CPB;
-  static constexpr int SCR = NY == 1 ? 0 : padded_len(NY);
+  // 512-point columns as two 256-point halves (even and odd samples), one
+  // per warp, combined by one radix-2 step (col_fft_eo)
+  static constexpr bool EO = kColEvenOdd && NY == 512 && RC == 8;
+  static constexpr int SCR = NY == 1 ? 0 : (EO ? 2 * padded_len(256) : padded_len(NY));
   static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && RC == 8 && TPC >= 32) ? 4 : 0;  // 0: no minimum
 };
+
+// A 512-point transform by 64 threads as two 256-point ones: warp w (lane l)
+// holds the samples a[2 (l + 32 r) + w] in x[r] and transforms them in the
+// warp (fft_block_regs, its own half sc + w P of the scratch); then
+// X[k] = E[k] + w^k O[k] and X[k + 256] = E[k] - w^k O[k] for k = l + 32 r,
+// the odd half's twiddled values and the even half's exchanged through the
+// scratch.  On exit warp 0 holds X[l + 32 r], warp 1 X[256 + l + 32 r].
+template <int SIGN, typename V>
+__device__ __forceinline__ void col_fft_eo(V (&x)[8], V* sc, int j, const V* __restrict__ tw) {
+  constexpr int P = padded_len(256);
+  const int w = j >> 5, l = j & 31;
+  fft_block_regs<256, 8, SIGN>(x, sc + w * P, l, tw);
+  if (w == 1) {
+    if constexpr (kProductTwiddles<V>) {
+      const V wl = twiddle<SIGN>(tw, 512, l);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], r == 0 ? wl : cmul(wl, root16<SIGN, V>(r)));
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, 512, l + 32 * r));
+    }
+  }
+  V* mine = sc + w * P;
+  const V* other = sc + (1 - w) * P;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) mine[pad(l) + pad(32 * r)] = x[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const V o = other[pad(l) + pad(32 * r)];
+    x[r] = w == 0 ? cadd(x[r], o) : csub(o, x[r]);
+  }
+}
 
 template <typename T, int NY>
 __host__ __device__ constexpr size_t col_smem(int nacc, int cpb) {
@@ -779,18 +818,26 @@ k_col(const __grid_constant__ ColParams p) {
   const V* tw = reinterpret_cast<const V*>(p.tw);
   const long long col_off = (long long)kx * NY;
 
+  // mode held in slot r after a transform, and the input element of slot r
+  // (the even/odd split of 512-point columns changes both)
+  constexpr bool EO = C::EO;
+  auto own_mode = [&](int r) { return EO ? 256 * (j >> 5) + (j & 31) + 32 * r : j + r * TPC; };
+  auto in_elem = [&](int r) { return EO ? 2 * ((j & 31) + 32 * r) + (j >> 5) : j + r * TPC; };
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
-    acc0[j + r * TPC] = mk<V>(T(0), T(0));
-    acc1[j + r * TPC] = mk<V>(T(0), T(0));
+    acc0[own_mode(r)] = mk<V>(T(0), T(0));
+    acc1[own_mode(r)] = mk<V>(T(0), T(0));
   }
 
   for (int i = 0; i < p.nin; ++i) {
     const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
     V x[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) x[r] = act ? src[j + r * TPC] : mk<V>(T(0), T(0));
-    if constexpr (NY > 1) {
+    for (int r = 0; r < RC; ++r) x[r] = act ? src[in_elem(r)] : mk<V>(T(0), T(0));
+    if constexpr (EO) {
+      group_sync<C::WARP>();  // scratch free
+      col_fft_eo<-1>(x, sc, j, tw);                // x[r]: mode own_mode(r)
+    } else if constexpr (NY > 1) {
       group_sync<C::WARP>();  // scratch free
       fft_block_regs<NY, RC, -1>(x, sc, j, tw);   // x[r]: mode j + r TPC
     }
@@ -801,12 +848,15 @@ k_col(const __grid_constant__ ColParams p) {
       V* acc = (t.acc == 0) ? acc0 : acc1;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
-        const int ni = j + r * TPC;
+        const int ni = own_mode(r);
         const V v = x[r];
         acc[ni] = cadd(acc[ni], cmul_ipow(v, __ldg(tab + ni), ph));
       }
     }
   }
+  // with the even/odd split the outputs read the accumulators in input
+  // order, which other threads of the column wrote
+  if constexpr (EO) group_sync<C::WARP>();
   for (int o = 0; o < p.nouts; ++o) {
     const ColTerm t = p.outs[o];
     const T* tab = reinterpret_cast<const T*>(t.tab) + col_off;
@@ -816,10 +866,15 @@ k_col(const __grid_constant__ ColParams p) {
     // conjugated input: the forward FFT of conj(X) is the conjugate of F^{-1}(X)
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
-      const int ni = j + r * TPC;
+      const int ni = in_elem(r);
       x[r] = cconj(cmul_ipow(acc[ni], __ldg(tab + ni), ph));
     }
-    if constexpr (NY > 1) {
+    if constexpr (EO) {
+      group_sync<C::WARP>();
+      col_fft_eo<-1>(x, sc, j, tw);
+#pragma unroll
+      for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
+    } else if constexpr (NY > 1) {
       group_sync<C::WARP>();
       fft_block_regs<NY, RC, -1>(x, sc, j, tw);
 #pragma unroll
@@ -831,13 +886,13 @@ k_col(const __grid_constant__ ColParams p) {
       for (int q = 0; q < p.npass; ++q) {
         const V* ps = reinterpret_cast<const V*>(p.pass[q].ptr) + member * p.pass[q].stride + col_off;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[j + r * TPC]);
+        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[own_mode(r)]);
       }
     }
     if (act) {
       V* dst = reinterpret_cast<V*>(p.buf[t.in].ptr) + member * p.buf[t.in].stride + col_off;
 #pragma unroll
-      for (int r = 0; r < RC; ++r) dst[j + r * TPC] = x[r];
+      for (int r = 0; r < RC; ++r) dst[own_mode(r)] = x[r];
     }
   }
 }
