@@ -675,24 +675,33 @@ def main():
         eta_o = torch.empty_like(eta_h).pin_memory()
         phi_o = torch.empty_like(phi_h).pin_memory()
 
-        def e2e_step():
+        def e2e_streamed():
+            ctx_e.step_streamed(eta_h, phi_h, wl.dt, 1, eta_o, phi_o)
+
+        def e2e_calls():
             ctx_e.set_state_all(eta_h, phi_h)
             ctx_e.step(wl.dt, 1)
             ctx_e.get_state_all(eta_o, phi_o)
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 10))
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            e2e_step()
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+
+        def e2e_time(fn):
+            for _ in range(max(1, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            ke = max(1, min(args.steps, 10))
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                fn()
+            torch.cuda.synchronize()
+            return ke, reduce_max(time.perf_counter() - t0, world, device="cuda")
         nbytes = 2 * eta_h.numel() * 8
-        te = reduce_max(te, world, device="cuda")
+        ke, te = e2e_time(e2e_streamed)
+        kc, tc = e2e_time(e2e_calls)
         e2e = {"value": job_points * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ke,
-               "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + sbi_get_state_all(pinned host)"}
+               "api": "sbi_step_streamed(pinned host in, dt, 1, pinned host out)",
+               "three_calls": {"value": job_points * kc / tc, "steps": kc,
+                               "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + "
+                                      "sbi_get_state_all(pinned host)"}}
         ctx_e.close()
 
     cpu = None

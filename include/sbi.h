@@ -212,6 +212,33 @@ int sbi_vertical_velocity_implicit(sbi_ctx* ctx, int member, int iterations, dou
  * low-pass filtered.  The step is replayed from a CUDA graph. */
 int sbi_step(sbi_ctx* ctx, double dt, int n);
 
+/* The state of every member streamed through the device for n steps: the
+ * same result, bit for bit, as
+ *   sbi_set_state_all(ctx, eta_in, phi_in, 0); sbi_step(ctx, dt, n);
+ *   sbi_get_state_all(ctx, eta_out, phi_out, 0);
+ * (Sec. 2.2 steps between the copies), with the copies of one member group
+ * overlapping the steps of the others.  Each group runs on a stream of its
+ * own: copy of its eta and phi~ in (copy engine, into a device staging
+ * buffer), conversion, the entry pass of sbi_set_state_all, n replays of the
+ * group's step graph, conversion out and copy out; the first group's stream
+ * has the highest priority, so the groups finish one after another and the
+ * last copies out overlap the remaining steps.  The paper has no counterpart
+ * (it holds one problem's state on one device).
+ *   eta_in, phi_in    sum over members of nx*ny doubles each, member order as
+ *                     in sbi_set_state_all; host (pinned memory for the
+ *                     overlap; pageable memory works but its copies block) or
+ *                     device memory.
+ *   eta_out, phi_out  the same sizes, written after the n steps; they may be
+ *                     eta_in, phi_in themselves.
+ *   dt, n             as in sbi_step; n = 0 copies the entry state out.
+ * Contexts with one member group, the adaptive pair (SBI_IF_RK45), a
+ * wavemaker or profiling on run the three calls one after another.  Two
+ * device staging buffers per group (the group's points x 8 bytes each) are
+ * allocated on first use and kept.  Synchronizes the stream.  SBI_EINVAL for
+ * a NULL buffer, dt <= 0 or n < 0; SBI_ENONFINITE as sbi_step. */
+int sbi_step_streamed(sbi_ctx* ctx, const double* eta_in, const double* phi_in, double dt, int n,
+                      double* eta_out, double* phi_out);
+
 /* Mass int eta dA and total energy 1/2 int (V phi~ + g eta^2) dA (Eq. energy,
  * dimensional, unit density) of one member, reduced in FP64 in a fixed order.
  * Synchronizes the stream. */

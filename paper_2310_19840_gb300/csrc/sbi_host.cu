@@ -135,6 +135,7 @@ struct Group {
   void* eta_ws = nullptr;    // physical working eta of the adaptive scheme's later stages (lazy)
   double* out64 = nullptr;   // conversion buffer for one member's field
   double* stage64 = nullptr; // conversion buffer for every member's field (batch calls; lazy)
+  double* stage64b = nullptr; // the second field's buffer (streamed step; lazy)
   int* d_active = nullptr;   // per-member flags for single-member passes
   int* d_conv = nullptr;     // adaptive order: 1 while a member still iterates
   int* d_orders = nullptr;   // adaptive order: orders used by the last diagnostic
@@ -158,6 +159,7 @@ struct GraphEntry {
   double dt;
   bool prof;
   int kind = 0;                      // StepKind
+  int group = -1;                    // -1: every group as concurrent branches; else that group alone
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
@@ -185,6 +187,8 @@ struct sbi_ctx {
   cudaStream_t cap = nullptr;     // internal stream for graph capture
   std::vector<cudaStream_t> gstreams;  // one capture branch per member group
   std::vector<cudaEvent_t> gevents;    // fork / join events of the branches
+  std::vector<cudaStream_t> pstreams;  // streamed step: one stream per group, by falling priority
+  std::vector<cudaEvent_t> pevents;    // streamed step: start, then one per group
   std::vector<Group> groups;
   std::vector<std::pair<int, int>> where;  // member -> (group, local index)
   std::vector<void*> allocs;
@@ -1827,12 +1831,16 @@ void free_graphs(sbi_ctx* c) {
   c->graphs.clear();
 }
 
-int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP) {
+int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, int group = -1) {
   for (auto& ge : c->graphs)
-    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind) { *out = &ge; return SBI_OK; }
+    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind && ge.group == group) { *out = &ge; return SBI_OK; }
   bool oom = false;
   std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, &oom, kind);
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
+  if (group >= 0) {   // one group's passes alone (the streamed step)
+    std::vector<Pass> one = gps.at((size_t)group);
+    gps.assign(1, one);
+  }
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
   CK(cudaStreamSynchronize(c->stream), "sync before capture");
   // block shapes are tuned (or taken from earlier tuning) before capture
@@ -1847,6 +1855,7 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP) 
   ge.dt = dt;
   ge.prof = c->prof;
   ge.kind = kind;
+  ge.group = group;
   if (c->prof) {   // the profiled graph owns one event pair per pass
     for (size_t gi = 0; gi < gps.size(); ++gi)
       for (size_t i = 0; i < gps[gi].size(); ++i) {
@@ -1891,7 +1900,7 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP) 
     }
   }
   // the simulation time of the next step (read by the wavemaker passes)
-  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP) {
+  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP && group < 0) {
     k_advance_time<<<1, 32, 0, c->cap>>>(c->d_time, dt);
     const cudaError_t el = cudaGetLastError();
     if (el != cudaSuccess) rc = cuda_fail(c, el, "kernel launch");
@@ -2694,6 +2703,120 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
   return SBI_OK;
 }
 
+// Upload, n steps and download of every member's state, pipelined per member
+// group: each group runs on its own stream (priority falling with the group
+// index), so the copies of one group overlap the steps of the others.  Every
+// launch and its arguments are those of sbi_set_state_all + sbi_step +
+// sbi_get_state_all (same passes, same block shapes), so the result is the
+// same bits.
+int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, double dt, int n,
+                      double* eta_out, double* phi_out) {
+  if (!c) return SBI_EINVAL;
+  if (!eta_in || !phi_in || !eta_out || !phi_out) return fail(c, SBI_EINVAL, "state buffers must not be NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
+  if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
+  const size_t G = c->groups.size();
+  // one group, the adaptive pair (host-side tables per step), the wavemaker
+  // (one clock for every group) and profiling keep the three calls in order
+  if (G < 2 || c->opt.integrator == SBI_IF_RK45 || c->wm_n > 0 || c->prof) {
+    int rc = sbi_set_state_all(c, eta_in, phi_in, 0);
+    if (!rc) rc = sbi_step(c, dt, n);
+    if (!rc) rc = sbi_get_state_all(c, eta_out, phi_out, 0);
+    return rc;
+  }
+  const std::vector<size_t> off = member_offsets(c);
+  // everything that allocates, plans, tunes or synchronizes comes first
+  std::vector<GraphEntry*> ges(G, nullptr);
+  std::vector<std::vector<Pass>> entry(G);
+  for (size_t gi = 0; gi < G; ++gi) {
+    Group& g = c->groups[gi];
+    if (n > 0) {
+      const int rc = get_step_graph(c, dt, &ges[gi], SK_STEP, (int)gi);
+      if (rc) return rc;
+    }
+    int rc = ensure_stage(c, g);
+    if (rc) return rc;
+    if (!g.stage64b) g.stage64b = (double*)dalloc(c, g.phys_elems() * g.n * 8);
+    if (!g.stage64b) return fail(c, SBI_ENOMEM, "device allocation failed");
+    Planner pl{c, g};
+    if (c->opt.set_state_dealias) pl.plan_project(entry[gi], false);
+    else entry[gi].push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
+    if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  }
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+  while (c->pstreams.size() < G) {
+    cudaStream_t s2;
+    const int prio = std::min(least, greatest + (int)c->pstreams.size());
+    CK(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio), "stream");
+    c->pstreams.push_back(s2);
+  }
+  while (c->pevents.size() < G + 1) {
+    cudaEvent_t e2;
+    CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "event");
+    c->pevents.push_back(e2);
+  }
+  CK(cudaEventRecord(c->pevents[0], c->stream), "event");   // after the caller's earlier work
+  const double* in[2] = {eta_in, phi_in};
+  double* outp[2] = {eta_out, phi_out};
+  for (size_t gi = 0; gi < G; ++gi) {
+    Group& g = c->groups[gi];
+    cudaStream_t st = c->pstreams[gi];
+    const size_t np = g.phys_elems();
+    double* stage[2] = {g.stage64, g.stage64b};
+    double* state[2] = {g.eta0, g.phi0};
+    CK(cudaStreamWaitEvent(st, c->pevents[0], 0), "wait");
+    for (int q = 0; q < 2; ++q) {
+      for (int li = 0; li < g.n;) {   // one copy per run of consecutive members
+        int run = 1;
+        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+        CK(cudaMemcpyAsync(stage[q] + (size_t)li * np, in[q] + off[g.members[li]], np * 8 * run,
+                           cudaMemcpyDefault, st), "copy state");
+        li += run;
+      }
+      const cudaError_t e = !c->state_ds ? state_convert<double>(stage[q], state[q], (long long)(np * g.n), false, st)
+                                         : state_convert<float>(stage[q], state[q], (long long)(np * g.n), false, st);
+      CK(e, "state conversion");
+    }
+    int rc = run_passes(c, entry[gi], st);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(ges[gi]->exec, st), "graph launch");
+    for (int q = 0; q < 2; ++q) {
+      const cudaError_t e = !c->state_ds ? state_convert<double>(state[q], stage[q], (long long)(np * g.n), true, st)
+                                         : state_convert<float>(state[q], stage[q], (long long)(np * g.n), true, st);
+      CK(e, "state conversion");
+    }
+  }
+  // the downloads are queued after every group's work: a copy into pageable
+  // memory returns only when it is done and would hold back the next group
+  for (size_t gi = 0; gi < G; ++gi) {
+    Group& g = c->groups[gi];
+    cudaStream_t st = c->pstreams[gi];
+    const size_t np = g.phys_elems();
+    double* stage[2] = {g.stage64, g.stage64b};
+    for (int q = 0; q < 2; ++q) {
+      for (int li = 0; li < g.n;) {
+        int run = 1;
+        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+        CK(cudaMemcpyAsync(outp[q] + off[g.members[li]], stage[q] + (size_t)li * np, np * 8 * run,
+                           cudaMemcpyDefault, st), "copy state");
+        li += run;
+      }
+    }
+    CK(cudaEventRecord(c->pevents[gi + 1], st), "event");
+    CK(cudaStreamWaitEvent(c->stream, c->pevents[gi + 1], 0), "wait");
+  }
+  for (int i = 0; i < n; ++i) c->t_host += dt;
+  CK(cudaStreamSynchronize(c->stream), "step_streamed");
+  if (c->opt.check_finite && n > 0) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+    CK(cudaStreamSynchronize(c->stream), "step_streamed");
+    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
+  }
+  return SBI_OK;
+}
+
 // The step after an error err at step h (the controller of the adaptive
 // integrating factor).
 double next_step_size(double h, double err, double tol) {
@@ -2997,6 +3120,7 @@ void sbi_destroy(sbi_ctx* c) {
   if (!c) return;
   if (c->cap) cudaStreamSynchronize(c->cap);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto s2 : c->pstreams) cudaStreamSynchronize(s2);
   free_graphs(c);
   for (void* p : c->allocs) {
     if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
@@ -3005,6 +3129,8 @@ void sbi_destroy(sbi_ctx* c) {
   c->allocs.clear();
   for (auto s2 : c->gstreams) cudaStreamDestroy(s2);
   for (auto e2 : c->gevents) cudaEventDestroy(e2);
+  for (auto s2 : c->pstreams) cudaStreamDestroy(s2);
+  for (auto e2 : c->pevents) cudaEventDestroy(e2);
   for (auto e2 : c->tune_ev)
     if (e2) cudaEventDestroy(e2);
   if (c->cap) cudaStreamDestroy(c->cap);

@@ -65,6 +65,8 @@ EXPORTS = {
     "sbi_crest": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)]),
     "sbi_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "sbi_step_streamed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                    C.c_void_p, C.c_void_p]),
     "sbi_invariants": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sbi_set_time": (C.c_int, [C.c_void_p, C.c_double]),
     "sbi_get_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -312,6 +314,28 @@ class Context:
 
     def step(self, dt, n=1):
         self._check(self.lib.sbi_step(self.ctx, float(dt), int(n)))
+
+    def step_streamed(self, eta_in, phi_in, dt, n=1, eta_out=None, phi_out=None):
+        """sbi_step_streamed: every member's state in (concatenated in member
+        order), n steps, the state out.  The outputs are new numpy arrays unless
+        given (contiguous float64 numpy arrays or torch tensors, host or
+        device; they may be the inputs)."""
+        if eta_out is None:
+            eta_out = np.empty(self.total_points())
+        if phi_out is None:
+            phi_out = np.empty(self.total_points())
+        ptrs, keeps = [], []   # keeps: converted inputs stay alive over the call
+        for a, is_out in ((eta_in, False), (phi_in, False), (eta_out, True), (phi_out, True)):
+            p, _, keep = _ptr(a)
+            if is_out and keep is not a:
+                raise ValueError("eta_out and phi_out must be contiguous float64 arrays or tensors")
+            if int(np.prod(keep.shape)) != self.total_points():
+                raise ValueError("every buffer must hold every member's points")
+            ptrs.append(p)
+            keeps.append(keep)
+        self._check(self.lib.sbi_step_streamed(self.ctx, ptrs[0], ptrs[1], float(dt), int(n),
+                                               ptrs[2], ptrs[3]))
+        return eta_out, phi_out
 
     def step_adaptive(self, t_end, tol, h):
         """sbi_step_adaptive: returns (proposed next step, accepted, rejected)."""
