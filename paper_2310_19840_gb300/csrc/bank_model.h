@@ -175,18 +175,23 @@ struct RowStrides {
 
 // shuffled: the row transforms end in registers (kShuffleFft); the forward
 // outputs are then written per row and read back by the cooperative store
-// one element each (no Z[k], Z[n-k] pair).
-inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, bool rk, bool shuffled) {
+// one element each (no Z[k], Z[n-k] pair).  fb_min: the least FFT scratch
+// row (the split transforms of fft.cuh need a little more than the padded
+// length).  Rows of 32 threads or more never share a warp, so for them the
+// transform's own accesses cost the same at every stride and only the
+// cooperative copies decide.
+inline RowStrides choose(int n, int R, int TPR, int rpc, int W, int elem_bytes, bool rk, bool shuffled,
+                         int fb_min = 0) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int, int, int, bool, bool>, RowStrides> cache;
-  const auto key = std::make_tuple(n, R, TPR, rpc, W, elem_bytes, rk, shuffled);
+  static std::map<std::tuple<int, int, int, int, int, int, bool, bool, int>, RowStrides> cache;
+  const auto key = std::make_tuple(n, R, TPR, rpc, W, elem_bytes, rk, shuffled, fb_min);
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
   const Geometry g{n, R, TPR, rpc, W, 128 / elem_bytes};
-  const int fb_len = n + (n >> 4) + 1;
+  const int fb_len = std::max(n + (n >> 4) + 1, fb_min);
   auto io_reads = [&](int S) {
     if (shuffled) return coop_cost(g, [&](int rl, int k) { return rl * S + k; });
     return coop_cost(g, [&](int rl, int k) { return rl * S + pad16(k); }) +

@@ -376,4 +376,152 @@ __device__ __forceinline__ void fft_block_regs(V (&x)[R], V* s, int j, const V* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split transforms of N = S * 256 points (S = 2, 4, 8) by S warps: T = N / 8
+// threads, thread j = 32 q + l (warp q, lane l).  In place of log_8 N
+// block-synchronised Stockham passes: one radix-S step across the warps in
+// registers, one exchange through shared memory (the only block barrier) and
+// one 256-point transform inside each warp (shuffle-fed, warp-synchronous).
+//   DIF (decimation in frequency), natural order in: thread j holds a[j + T r]
+//   in x[r].  With e = m + 256 w (m < 256, w < S),
+//     b_q[m] = w_N^{m q} sum_w a[m + 256 w] w_S^{w q},
+//     X[S k + q] = sum_m b_q[m] w_256^{m k}:
+//   thread j owns the radix-S columns m = j + T p (p < P = 8 / S, registers
+//   x[p + P w]); warp q then transforms b_q.  On exit thread j holds
+//   X[S (l + 32 r) + q] in x[r].
+//   DIT (decimation in time), the same read backwards: thread j holds
+//   c_q[l + 32 r] = a[S (l + 32 r) + q] in x[r]; warp q transforms c_q into
+//   Y_q, and X[k + 256 w] = sum_q w_S^{q w} (w_N^{q k} Y_q[k]); on exit thread
+//   j holds X[j + T r] in x[r].
+// Scratch: S rows of padded_len(256) elements, row q holding warp q's part of
+// the exchange and then its 256-point scratch.  Every thread of the block
+// calls these (block barrier); the caller makes sure nobody still reads s.
+// ---------------------------------------------------------------------------
+constexpr bool kSplitTransforms = true;
+template <int N, int R>
+inline constexpr bool kSplitFft = kSplitTransforms && R == 8 && (N == 512 || N == 1024 || N == 2048);
+
+// shared-memory elements a transform of N points by radix R needs
+template <int N, int R>
+__host__ __device__ constexpr int fft_scratch_len() {
+  return kSplitFft<N, R> ? (N / 256) * padded_len(256) : padded_len(N);
+}
+
+// v[k] *= w_N^{k m} for k = 1 .. S - 1 (FP32: powers by products, at most
+// three roundings each; FP64: every power from the table)
+template <int S, int SIGN, typename V>
+__device__ __forceinline__ void twiddle_run(V (&v)[S], const V* __restrict__ tw, int N, int m) {
+  if constexpr (S == 1) {
+    return;
+  } else if constexpr (kProductTwiddles<V>) {
+    const V w1 = twiddle<SIGN>(tw, N, m);
+    const V w2 = cmul(w1, w1);
+    v[1] = cmul(v[1], w1);
+    if constexpr (S >= 4) {
+      const V w3 = cmul(w1, w2);
+      v[2] = cmul(v[2], w2);
+      v[3] = cmul(v[3], w3);
+      if constexpr (S == 8) {
+        const V w4 = twiddle<SIGN>(tw, N, 4 * m);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w4, w1));
+        v[6] = cmul(v[6], cmul(w4, w2));
+        v[7] = cmul(v[7], cmul(w4, w3));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < S; ++k) v[k] = cmul(v[k], twiddle<SIGN>(tw, N, k * m));
+  }
+}
+
+template <int N, int SIGN, typename V>
+__device__ __forceinline__ void fft_split_dif(V (&x)[8], V* s, int j, const V* __restrict__ tw) {
+  constexpr int S = N / 256, P = 8 / S, T = N / 8, PP = padded_len(256);
+  const int q = j >> 5, l = j & 31;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int m = j + T * p;
+    V v[S];
+#pragma unroll
+    for (int w = 0; w < S; ++w) v[w] = x[p + P * w];
+    Dft<S, SIGN, V>::run(v);
+    twiddle_run<S, SIGN>(v, tw, N, m);
+#pragma unroll
+    for (int k = 0; k < S; ++k) s[k * PP + pad(m)] = v[k];
+  }
+  __syncthreads();
+  V* row = s + q * PP;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) x[r] = row[pad(l) + pad(32 * r)];
+  __syncwarp();   // row q is read only by warp q: free for its transform
+  fft_block_regs<256, 8, SIGN>(x, row, l, tw);
+}
+
+template <int N, int SIGN, typename V>
+__device__ __forceinline__ void fft_split_dit(V (&x)[8], V* s, int j, const V* __restrict__ tw) {
+  constexpr int S = N / 256, P = 8 / S, T = N / 8, PP = padded_len(256);
+  const int q = j >> 5, l = j & 31;
+  V* row = s + q * PP;
+  fft_block_regs<256, 8, SIGN>(x, row, l, tw);   // x[r] = Y_q[l + 32 r]; row free again
+  if (q > 0) {
+    // w_N^{q (l + 32 r)} = w_N^{q l} w_N^{32 q r}
+    if constexpr (kProductTwiddles<V>) {
+      const V wl = twiddle<SIGN>(tw, N, q * l);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], r == 0 ? wl : cmul(wl, twiddle<SIGN>(tw, N, 32 * q * r)));
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, N, q * (l + 32 * r)));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) row[pad(l) + pad(32 * r)] = x[r];
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int m = j + T * p;
+    V v[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) v[k] = s[k * PP + pad(m)];
+    Dft<S, SIGN, V>::run(v);
+#pragma unroll
+    for (int w = 0; w < S; ++w) x[p + P * w] = v[w];
+  }
+}
+
+// Thread j's inputs to fft_regs_in_order are the elements jin + T r with
+// jin = fft_in_index(j): the decimated order of the split form, else j.
+template <int N, int R>
+__device__ __forceinline__ int fft_in_index(int j) {
+  if constexpr (kSplitFft<N, R>) return (N / 256) * (j & 31) + (j >> 5);
+  else return j;
+}
+
+// Transform with the inputs in fft_in_index order and the thread's own
+// elements of the result in registers on exit, x[r] = X[j + r N/R].
+// s has no live data on exit.
+template <int N, int R, int SIGN, typename V>
+__device__ __forceinline__ void fft_regs_in_order(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
+  if constexpr (kSplitFft<N, R>) fft_split_dit<N, SIGN>(x, s, j, tw);
+  else fft_block_regs<N, R, SIGN>(x, s, j, tw);
+}
+
+// Transform of natural-order inputs (x[r] = a[j + r N/R]) that leaves the
+// result in natural order in s[pad(k)]: readers in other threads need a
+// block barrier (or a warp barrier where the transform fits one warp) first.
+template <int N, int R, int SIGN, typename V>
+__device__ __forceinline__ void fft_to_smem(V (&x)[R], V* s, int j, const V* __restrict__ tw) {
+  if constexpr (kSplitFft<N, R>) {
+    constexpr int T = N / R;
+    fft_split_dif<N, SIGN>(x, s, j, tw);
+    __syncthreads();   // every warp done with its rows of s
+    const int jo = (N / 256) * (j & 31) + (j >> 5);
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[pad(jo + r * T)] = x[r];
+  } else {
+    fft_block<N, R, SIGN>(x, s, j, tw);
+  }
+}
+
 }  // namespace sbi

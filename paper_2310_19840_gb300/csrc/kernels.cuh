@@ -37,7 +37,7 @@ struct RowCfg {
   static constexpr bool WARP = TPR <= 32;
   static constexpr int RPC_MAX = cmin(256, WARP ? cmax(16, 512 / TPR) : cmax(1, 512 / TPR));
   static constexpr int MAX_THREADS = TPR * RPC_MAX;
-  static constexpr int FBUF = padded_len(n);
+  static constexpr int FBUF = fft_scratch_len<n, R>();    // FFT scratch per row
   template <typename T>
   // 0: no minimum, the register count is left to the compiler
   static constexpr int min_blocks() { return sizeof(T) == 4 ? 2 : 0; }
@@ -329,7 +329,7 @@ k_row(const __grid_constant__ RowParams p) {
         stage_mixed<T>(stg_all, sw, p.buf + op.a, op.b, io);
         __syncthreads();
       }
-      c2r_input<T, NX>(x, stg_all + rloc * sw, p.W, j, tw);
+      c2r_input<T, NX>(x, stg_all + rloc * sw, p.W, fft_in_index<n, R>(j), tw);
       __syncthreads();  // every row has read its staging row; scratch free
       // the next single-buffer input lands while this one is transformed
       pending = next_async_c2r(p, o + 1);
@@ -421,7 +421,7 @@ k_row(const __grid_constant__ RowParams p) {
     if (op.kind == ROP_C2R) {
       // inverse transform: the row in physical space, packed as complex
       // pairs; each thread's own elements m = j + r TPR come back in registers
-      fft_block_regs<n, R, -1>(x, fb, j, tw);
+      fft_regs_in_order<n, R, -1>(x, fb, j, tw);
       V* slot = slot_base + (op.slot * rpc + rloc) * n;
       V* out = (act && op.dst != kNone) ? phys_row_w<T>(p.buf[op.dst], member, y, NX) : nullptr;
 #pragma unroll
@@ -441,7 +441,7 @@ k_row(const __grid_constant__ RowParams p) {
       __syncthreads();  // every row's kept modes ready
       store_modes<T>(fb_all, fbs, p.buf[op.dst], io);
     } else {
-      fft_block<n, R, -1>(x, fb, j, tw);
+      fft_to_smem<n, R, -1>(x, fb, j, tw);
       __syncthreads();  // every row's spectrum ready
       r2c_store<T, NX>(fb_all, fbs, p.buf[op.dst], io, tw);
     }
@@ -607,9 +607,9 @@ k_rk(const __grid_constant__ RkParams p) {
     // first inverse: phi~_t (stage) or the eta correction
     stage_mixed<T>(fb_all, fbs, &p.phit, 1, io);
     __syncthreads();
-    c2r_input<T, NX>(x, fb, p.W, j, tw);
+    c2r_input<T, NX>(x, fb, p.W, fft_in_index<n, R>(j), tw);
     row_group_sync<NX>();
-    fft_block_regs<n, R, -1>(x, fb, j, tw);   // x[r]: element j + r TPR
+    fft_regs_in_order<n, R, -1>(x, fb, j, tw);   // x[r]: element j + r TPR
     if (p.mode == RK_CORRECT || p.mode == RK_OFFSET) {
       const bool keep = p.mode == RK_CORRECT;   // RK_OFFSET leaves the state unchanged
 #pragma unroll
@@ -626,9 +626,9 @@ k_rk(const __grid_constant__ RkParams p) {
       __syncthreads();
       stage_mixed<T>(fb_all, fbs, &p.corr_phi, 1, io);
       __syncthreads();
-      c2r_input<T, NX>(x, fb, p.W, j, tw);
+      c2r_input<T, NX>(x, fb, p.W, fft_in_index<n, R>(j), tw);
       row_group_sync<NX>();
-      fft_block_regs<n, R, -1>(x, fb, j, tw);
+      fft_regs_in_order<n, R, -1>(x, fb, j, tw);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * TPR;
@@ -694,11 +694,11 @@ k_rk(const __grid_constant__ RkParams p) {
     for (int r = 0; r < R; ++r) ew[j + r * TPR] = xe[r];
   }
   __syncthreads();
-  fft_block<n, R, -1>(xe, fb, j, tw);
+  fft_to_smem<n, R, -1>(xe, fb, j, tw);
   __syncthreads();
   r2c_store<T, NX>(fb_all, fbs, p.eta_hat, io, tw);
   __syncthreads();
-  fft_block<n, R, -1>(xp, fb, j, tw);
+  fft_to_smem<n, R, -1>(xp, fb, j, tw);
   __syncthreads();
   r2c_store<T, NX>(fb_all, fbs, p.phi_hat, io, tw);
 }
@@ -729,7 +729,14 @@ struct ColCfg {
   // 512-point columns as two 256-point halves (even and odd samples), one
   // per warp, combined by one radix-2 step (col_fft_eo)
   static constexpr bool EO = kColEvenOdd && NY == 512 && RC == 8;
-  static constexpr int SCR = NY == 1 ? 0 : (EO ? 2 * padded_len(256) : padded_len(NY));
+  // 1024- and 2048-point columns by the split transforms of fft.cuh: forward
+  // by decimation in frequency (natural loads, spectrum in decimated order),
+  // inverse by decimation in time (decimated spectrum in, natural stores)
+  static constexpr bool SPLIT = kSplitFft<NY, RC> && NY >= 1024;
+  static constexpr int SCR = NY == 1 ? 0 : (EO ? 2 * padded_len(256) : fft_scratch_len<NY, RC>());
+  // accumulator length per column (padded where the modes are held with
+  // stride NY / 256, so that those accesses spread over the banks)
+  static constexpr int ACC = SPLIT ? padded_len(NY) : NY;
   static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && RC == 8 && TPC >= 32) ? 4 : 0;  // 0: no minimum
 };
 
@@ -769,7 +776,7 @@ __device__ __forceinline__ void col_fft_eo(V (&x)[8], V* sc, int j, const V* __r
 template <typename T, int NY>
 __host__ __device__ constexpr size_t col_smem(int nacc, int cpb) {
   using C = ColCfg<T, NY>;
-  return sizeof(cx<T>) * (size_t)cpb * ((size_t)C::SCR + (size_t)NY * nacc);
+  return sizeof(cx<T>) * (size_t)cpb * ((size_t)C::SCR + (size_t)C::ACC * nacc);
 }
 
 // columns per block of a launch: the size's default CPB, or a smaller count
@@ -808,8 +815,8 @@ k_col(const __grid_constant__ ColParams p) {
   const int c = threadIdx.x / TPC, j = threadIdx.x % TPC;
   V* base = reinterpret_cast<V*>(smem_raw);
   V* sc = base + c * SCR;                                   // FFT scratch
-  V* acc0 = base + cpb * SCR + c * NY * p.nacc;             // accumulators
-  V* acc1 = acc0 + (p.nacc > 1 ? NY : 0);
+  V* acc0 = base + cpb * SCR + c * C::ACC * p.nacc;         // accumulators
+  V* acc1 = acc0 + (p.nacc > 1 ? C::ACC : 0);
   const int gc = blockIdx.x * cpb + c;
   const bool valid = gc < p.cols_total;
   const int member = valid ? gc / p.W : 0;
@@ -818,25 +825,43 @@ k_col(const __grid_constant__ ColParams p) {
   const V* tw = reinterpret_cast<const V*>(p.tw);
   const long long col_off = (long long)kx * NY;
 
-  // mode held in slot r after a transform, and the input element of slot r
-  // (the even/odd split of 512-point columns changes both)
-  constexpr bool EO = C::EO;
-  auto own_mode = [&](int r) { return EO ? 256 * (j >> 5) + (j & 31) + 32 * r : j + r * TPC; };
-  auto in_elem = [&](int r) { return EO ? 2 * ((j & 31) + 32 * r) + (j >> 5) : j + r * TPC; };
+  // Element orders of slot r.  ld: the input element loaded; fwd: the mode
+  // held after the forward transform (accumulated); inv: the mode read as
+  // input of an inverse transform; st: the element it leaves (stored).  Plain
+  // transforms keep the natural order j + r TPC throughout; the even/odd
+  // split of 512-point columns loads decimated elements and holds each
+  // warp's half of the modes; the split form of longer columns loads and
+  // stores in natural order and holds decimated modes.  acc_at: position of
+  // a mode in the accumulators.
+  constexpr bool EO = C::EO, SPLIT = C::SPLIT;
+  const int jd = (NY / 256) * (j & 31) + (j >> 5);       // split: decimated lane order
+  auto nat = [&](int r) { return j + r * TPC; };
+  auto ld = [&](int r) { return EO ? 2 * ((j & 31) + 32 * r) + (j >> 5) : nat(r); };
+  auto fwd = [&](int r) {
+    return EO ? 256 * (j >> 5) + (j & 31) + 32 * r : (SPLIT ? jd + r * TPC : nat(r));
+  };
+  auto inv = [&](int r) { return EO ? ld(r) : fwd(r); };
+  auto st = [&](int r) { return EO ? fwd(r) : nat(r); };
+  auto acc_at = [&](int m) { return SPLIT ? pad(m) : m; };
+  // table position of slot r's mode m (split: the table's decimated order)
+  auto tab_at = [&](int r, int m) { return SPLIT ? 256 * (j >> 5) + (j & 31) + 32 * r : m; };
 #pragma unroll
   for (int r = 0; r < RC; ++r) {
-    acc0[own_mode(r)] = mk<V>(T(0), T(0));
-    acc1[own_mode(r)] = mk<V>(T(0), T(0));
+    acc0[acc_at(fwd(r))] = mk<V>(T(0), T(0));
+    acc1[acc_at(fwd(r))] = mk<V>(T(0), T(0));
   }
 
   for (int i = 0; i < p.nin; ++i) {
     const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
     V x[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) x[r] = act ? src[in_elem(r)] : mk<V>(T(0), T(0));
+    for (int r = 0; r < RC; ++r) x[r] = act ? src[ld(r)] : mk<V>(T(0), T(0));
     if constexpr (EO) {
       group_sync<C::WARP>();  // scratch free
-      col_fft_eo<-1>(x, sc, j, tw);                // x[r]: mode own_mode(r)
+      col_fft_eo<-1>(x, sc, j, tw);                // x[r]: mode fwd(r)
+    } else if constexpr (SPLIT) {
+      __syncthreads();        // scratch free
+      fft_split_dif<NY, -1>(x, sc, j, tw);         // x[r]: mode fwd(r)
     } else if constexpr (NY > 1) {
       group_sync<C::WARP>();  // scratch free
       fft_block_regs<NY, RC, -1>(x, sc, j, tw);   // x[r]: mode j + r TPC
@@ -848,14 +873,15 @@ k_col(const __grid_constant__ ColParams p) {
       V* acc = (t.acc == 0) ? acc0 : acc1;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
-        const int ni = own_mode(r);
+        const int ni = fwd(r);
         const V v = x[r];
-        acc[ni] = cadd(acc[ni], cmul_ipow(v, __ldg(tab + ni), ph));
+        acc[acc_at(ni)] = cadd(acc[acc_at(ni)], cmul_ipow(v, __ldg(tab + tab_at(r, ni)), ph));
       }
     }
   }
   // with the even/odd split the outputs read the accumulators in input
-  // order, which other threads of the column wrote
+  // order, which other threads of the column wrote (the split form reads
+  // back the thread's own modes)
   if constexpr (EO) group_sync<C::WARP>();
   for (int o = 0; o < p.nouts; ++o) {
     const ColTerm t = p.outs[o];
@@ -866,12 +892,17 @@ k_col(const __grid_constant__ ColParams p) {
     // conjugated input: the forward FFT of conj(X) is the conjugate of F^{-1}(X)
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
-      const int ni = in_elem(r);
-      x[r] = cconj(cmul_ipow(acc[ni], __ldg(tab + ni), ph));
+      const int ni = inv(r);
+      x[r] = cconj(cmul_ipow(acc[acc_at(ni)], __ldg(tab + tab_at(r, ni)), ph));
     }
     if constexpr (EO) {
       group_sync<C::WARP>();
       col_fft_eo<-1>(x, sc, j, tw);
+#pragma unroll
+      for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
+    } else if constexpr (SPLIT) {
+      __syncthreads();
+      fft_split_dit<NY, -1>(x, sc, j, tw);         // x[r]: element st(r)
 #pragma unroll
       for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
     } else if constexpr (NY > 1) {
@@ -886,13 +917,13 @@ k_col(const __grid_constant__ ColParams p) {
       for (int q = 0; q < p.npass; ++q) {
         const V* ps = reinterpret_cast<const V*>(p.pass[q].ptr) + member * p.pass[q].stride + col_off;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[own_mode(r)]);
+        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[st(r)]);
       }
     }
     if (act) {
       V* dst = reinterpret_cast<V*>(p.buf[t.in].ptr) + member * p.buf[t.in].stride + col_off;
 #pragma unroll
-      for (int r = 0; r < RC; ++r) dst[own_mode(r)] = x[r];
+      for (int r = 0; r < RC; ++r) dst[st(r)] = x[r];
     }
   }
 }
@@ -901,11 +932,16 @@ k_col(const __grid_constant__ ColParams p) {
 // Multiplier tables: the real factor of a ColTerm for every stored mode
 // (kx < W, all ny), evaluated in FP64 and rounded to the working precision.
 // ---------------------------------------------------------------------------
+// perm > 1: the column pass holds the modes of a column in the decimated
+// order of the split transforms (mode n = perm (l + 32 r) + q read by lane l,
+// warp q), so mode n is stored at (n mod perm) 256 + n / perm and the reads
+// of a warp are contiguous.
 template <typename T>
-__global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
+__global__ void k_coef_table(T* __restrict__ out, const TableSpec s, int perm) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)s.W * s.ny) return;
   const int kx = (int)(idx / s.ny), n = (int)(idx % s.ny);
+  const long long at = (long long)kx * s.ny + (perm > 1 ? (n % perm) * 256 + n / perm : n);
   const int ns = (s.ny == 1) ? 0 : (n < s.ny / 2 ? n : n - s.ny);
   const double kxv = kx * s.two_pi_over_Lx, kyv = ns * s.two_pi_over_Ly;
   const double k = sqrt(kxv * kxv + kyv * kyv);
@@ -950,13 +986,23 @@ __global__ void k_coef_table(T* __restrict__ out, const TableSpec s) {
   const bool keep = kx < s.kx_keep && (ns < 0 ? -ns : ns) < s.ky_keep;
   if (s.mask == 2) f *= (keep ? d : 0.0) - 1.0;
   else f *= d * ((s.mask == 1 && !keep) ? 0.0 : 1.0);
-  out[idx] = T(f);
+  out[at] = T(f);
+}
+
+// order of the modes of a column in the multiplier tables (k_coef_table)
+template <typename T>
+int col_table_perm(int ny) {
+  if (ny == 512 && ColCfg<T, 512>::SPLIT) return 2;
+  if (ny == 1024 && ColCfg<T, 1024>::SPLIT) return 4;
+  if (ny == 2048 && ColCfg<T, 2048>::SPLIT) return 8;
+  return 1;
 }
 
 template <typename T>
 cudaError_t launch_coef_table_impl(void* out, const TableSpec& s, cudaStream_t st) {
   const long long n = (long long)s.W * s.ny;
-  k_coef_table<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<T*>(out), s);
+  k_coef_table<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<T*>(out), s,
+                                                                 col_table_perm<T>(s.ny));
   return cudaGetLastError();
 }
 
@@ -1018,7 +1064,7 @@ cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
   RowParams q = p;
   const bank::RowStrides rs =
-      bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false, kShuffleFft<C::n, C::R>);
+      bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false, kShuffleFft<C::n, C::R>, C::FBUF);
   q.fbs = rs.fbs;
   q.sws = rs.sws;
   const size_t smem = row_smem<T, NX>(q.rpc, q.fbs, q.sws, q.nslots);
@@ -1033,7 +1079,7 @@ cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
   if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC) return cudaErrorInvalidValue;
   const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
   RkParams q = p;
-  q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true, false).fbs;
+  q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true, false, C::FBUF).fbs;
   const size_t smem = sizeof(cx<T>) * (size_t)q.rpc * q.fbs;
   if (q.state64 && sizeof(T) == 4) k_rk<T, NX, double><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
   else k_rk<T, NX, T><<<blocks, C::TPR * q.rpc, smem, st>>>(q);
