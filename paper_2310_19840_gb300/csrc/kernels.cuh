@@ -715,8 +715,6 @@ k_rk(const __grid_constant__ RkParams p) {
 // Column-pass geometry: 8 elements per thread (one warp per column at 256,
 // two at 512, ...).  In FP32 columns of at least a warp are compiled for four
 // resident blocks per SM (64 registers).
-// 512-point columns by the even/odd split (col_fft_eo)
-constexpr bool kColEvenOdd = true;
 
 template <typename T, int NY>
 struct ColCfg {
@@ -726,52 +724,16 @@ struct ColCfg {
   // 8-byte elements: 256 threads per block; 16-byte elements: half the columns
   static constexpr int CPB = NY == 1 ? 256 : cmax(1, 256 / TPC / (int)(sizeof(T) / 4));
   static constexpr int THREADS = TPC * CPB;
-  // 512-point columns as two 256-point halves (even and odd samples), one
-  // per warp, combined by one radix-2 step (col_fft_eo)
-  static constexpr bool EO = kColEvenOdd && NY == 512 && RC == 8;
-  // 1024- and 2048-point columns by the split transforms of fft.cuh: forward
+  // 512- to 2048-point columns by the split transforms of fft.cuh: forward
   // by decimation in frequency (natural loads, spectrum in decimated order),
   // inverse by decimation in time (decimated spectrum in, natural stores)
-  static constexpr bool SPLIT = kSplitFft<NY, RC> && NY >= 1024;
-  static constexpr int SCR = NY == 1 ? 0 : (EO ? 2 * padded_len(256) : fft_scratch_len<NY, RC>());
+  static constexpr bool SPLIT = kSplitFft<NY, RC>;
+  static constexpr int SCR = NY == 1 ? 0 : fft_scratch_len<NY, RC>();
   // accumulator length per column (padded where the modes are held with
   // stride NY / 256, so that those accesses spread over the banks)
   static constexpr int ACC = SPLIT ? padded_len(NY) : NY;
   static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && RC == 8 && TPC >= 32) ? 4 : 0;  // 0: no minimum
 };
-
-// A 512-point transform by 64 threads as two 256-point ones: warp w (lane l)
-// holds the samples a[2 (l + 32 r) + w] in x[r] and transforms them in the
-// warp (fft_block_regs, its own half sc + w P of the scratch); then
-// X[k] = E[k] + w^k O[k] and X[k + 256] = E[k] - w^k O[k] for k = l + 32 r,
-// the odd half's twiddled values and the even half's exchanged through the
-// scratch.  On exit warp 0 holds X[l + 32 r], warp 1 X[256 + l + 32 r].
-template <int SIGN, typename V>
-__device__ __forceinline__ void col_fft_eo(V (&x)[8], V* sc, int j, const V* __restrict__ tw) {
-  constexpr int P = padded_len(256);
-  const int w = j >> 5, l = j & 31;
-  fft_block_regs<256, 8, SIGN>(x, sc + w * P, l, tw);
-  if (w == 1) {
-    if constexpr (kProductTwiddles<V>) {
-      const V wl = twiddle<SIGN>(tw, 512, l);
-#pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], r == 0 ? wl : cmul(wl, root16<SIGN, V>(r)));
-    } else {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = cmul(x[r], twiddle<SIGN>(tw, 512, l + 32 * r));
-    }
-  }
-  V* mine = sc + w * P;
-  const V* other = sc + (1 - w) * P;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) mine[pad(l) + pad(32 * r)] = x[r];
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const V o = other[pad(l) + pad(32 * r)];
-    x[r] = w == 0 ? cadd(x[r], o) : csub(o, x[r]);
-  }
-}
 
 template <typename T, int NY>
 __host__ __device__ constexpr size_t col_smem(int nacc, int cpb) {
@@ -825,23 +787,14 @@ k_col(const __grid_constant__ ColParams p) {
   const V* tw = reinterpret_cast<const V*>(p.tw);
   const long long col_off = (long long)kx * NY;
 
-  // Element orders of slot r.  ld: the input element loaded; fwd: the mode
-  // held after the forward transform (accumulated); inv: the mode read as
-  // input of an inverse transform; st: the element it leaves (stored).  Plain
-  // transforms keep the natural order j + r TPC throughout; the even/odd
-  // split of 512-point columns loads decimated elements and holds each
-  // warp's half of the modes; the split form of longer columns loads and
-  // stores in natural order and holds decimated modes.  acc_at: position of
-  // a mode in the accumulators.
-  constexpr bool EO = C::EO, SPLIT = C::SPLIT;
+  // Slot r holds element nat(r) = j + r TPC of a column on input and on
+  // output, and mode fwd(r) of its spectrum in between: the same for plain
+  // transforms, the decimated order jd + r TPC for the split form.  acc_at:
+  // position of a mode in the accumulators.
+  constexpr bool SPLIT = C::SPLIT;
   const int jd = (NY / 256) * (j & 31) + (j >> 5);       // split: decimated lane order
   auto nat = [&](int r) { return j + r * TPC; };
-  auto ld = [&](int r) { return EO ? 2 * ((j & 31) + 32 * r) + (j >> 5) : nat(r); };
-  auto fwd = [&](int r) {
-    return EO ? 256 * (j >> 5) + (j & 31) + 32 * r : (SPLIT ? jd + r * TPC : nat(r));
-  };
-  auto inv = [&](int r) { return EO ? ld(r) : fwd(r); };
-  auto st = [&](int r) { return EO ? fwd(r) : nat(r); };
+  auto fwd = [&](int r) { return SPLIT ? jd + r * TPC : nat(r); };
   auto acc_at = [&](int m) { return SPLIT ? pad(m) : m; };
   // table position of slot r's mode m (split: the table's decimated order)
   auto tab_at = [&](int r, int m) { return SPLIT ? 256 * (j >> 5) + (j & 31) + 32 * r : m; };
@@ -855,11 +808,8 @@ k_col(const __grid_constant__ ColParams p) {
     const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
     V x[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) x[r] = act ? src[ld(r)] : mk<V>(T(0), T(0));
-    if constexpr (EO) {
-      group_sync<C::WARP>();  // scratch free
-      col_fft_eo<-1>(x, sc, j, tw);                // x[r]: mode fwd(r)
-    } else if constexpr (SPLIT) {
+    for (int r = 0; r < RC; ++r) x[r] = act ? src[nat(r)] : mk<V>(T(0), T(0));
+    if constexpr (SPLIT) {
       __syncthreads();        // scratch free
       fft_split_dif<NY, -1>(x, sc, j, tw);         // x[r]: mode fwd(r)
     } else if constexpr (NY > 1) {
@@ -879,10 +829,7 @@ k_col(const __grid_constant__ ColParams p) {
       }
     }
   }
-  // with the even/odd split the outputs read the accumulators in input
-  // order, which other threads of the column wrote (the split form reads
-  // back the thread's own modes)
-  if constexpr (EO) group_sync<C::WARP>();
+  // each thread reads back the modes it accumulated: no barrier
   for (int o = 0; o < p.nouts; ++o) {
     const ColTerm t = p.outs[o];
     const T* tab = reinterpret_cast<const T*>(t.tab) + col_off;
@@ -892,17 +839,12 @@ k_col(const __grid_constant__ ColParams p) {
     // conjugated input: the forward FFT of conj(X) is the conjugate of F^{-1}(X)
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
-      const int ni = inv(r);
+      const int ni = fwd(r);
       x[r] = cconj(cmul_ipow(acc[acc_at(ni)], __ldg(tab + tab_at(r, ni)), ph));
     }
-    if constexpr (EO) {
-      group_sync<C::WARP>();
-      col_fft_eo<-1>(x, sc, j, tw);
-#pragma unroll
-      for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
-    } else if constexpr (SPLIT) {
+    if constexpr (SPLIT) {
       __syncthreads();
-      fft_split_dit<NY, -1>(x, sc, j, tw);         // x[r]: element st(r)
+      fft_split_dit<NY, -1>(x, sc, j, tw);         // x[r]: element nat(r)
 #pragma unroll
       for (int r = 0; r < RC; ++r) x[r] = cconj(x[r]);
     } else if constexpr (NY > 1) {
@@ -917,13 +859,13 @@ k_col(const __grid_constant__ ColParams p) {
       for (int q = 0; q < p.npass; ++q) {
         const V* ps = reinterpret_cast<const V*>(p.pass[q].ptr) + member * p.pass[q].stride + col_off;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[st(r)]);
+        for (int r = 0; r < RC; ++r) x[r] = cadd(x[r], ps[nat(r)]);
       }
     }
     if (act) {
       V* dst = reinterpret_cast<V*>(p.buf[t.in].ptr) + member * p.buf[t.in].stride + col_off;
 #pragma unroll
-      for (int r = 0; r < RC; ++r) dst[st(r)] = x[r];
+      for (int r = 0; r < RC; ++r) dst[nat(r)] = x[r];
     }
   }
 }
