@@ -271,6 +271,29 @@ def autotune_summary(report):
     return out
 
 
+def schedule_summary(report):
+    """The step schedules the library timed (sbi_schedule_report): per
+    candidate its role, ms per step (None if not timed), name, mode and
+    units, and the name of the one in use."""
+    out = {"candidates": []}
+    for ln in report.splitlines():
+        if " units:" not in ln:
+            continue
+        role, rest = ln.split(" ", 1)
+        ms = None
+        if " ms per step: " in rest:
+            t, rest = rest.split(" ms per step: ", 1)
+            ms = float(t)
+        head, units = rest.split(" units:", 1)
+        name, _, mode = head.partition(" [")
+        out["candidates"].append({"role": role, "ms_per_step": ms, "schedule": name,
+                                  "mode": mode.split("]")[0], "units": units.split()})
+    picked = [c for c in out["candidates"] if c["role"] in ("chosen", "forced")] or \
+        [c for c in out["candidates"] if c["role"] == "default"]
+    out["chosen"] = picked[0]["schedule"] if picked else None
+    return out
+
+
 def make_context(sbi, wl, precision, stream, **extra):
     grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in wl.members]
     depths = [(m.h0 - m.delta) if m.delta is not None else None for m in wl.members]
@@ -570,9 +593,6 @@ def main():
         if rank == 0:
             print(json.dumps(compare_diagnostics(ctx, wl, torch, args)))
         return
-    launches = ctx.step_launches()
-    bytes_step = ctx.step_bytes(-1)
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
@@ -585,6 +605,9 @@ def main():
     secs = time_steps(ctx, torch, stream, wl.dt, args.steps, args.warmup)
     clk = clocks.stop()
     secs = reduce_max(secs, world, device="cuda")
+    # launches and bytes of a step under the schedule the first step chose
+    launches = ctx.step_launches()
+    bytes_step = ctx.step_bytes(-1)
     pts = wl.points
     split = world > 1 and args.shard == "split"
     # whole-job rate: every rank's points (a split batch: the batch's points)
@@ -717,6 +740,7 @@ def main():
             "gpu_launches": launches * args.steps,
             "transforms_per_point_step": ctx.step_transforms(-1) / wl.points,
             "autotune": autotune_summary(ctx.autotune_report()),
+            "schedule": schedule_summary(ctx.schedule_report()),
             "model_step_GBps": step_model_gbps, "fused_step_GBps": step_gbps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_arm, "error": err}
     if gathered:

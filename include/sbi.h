@@ -49,8 +49,9 @@ extern "C" {
 #define SBI_ECUDA          3   /* a CUDA runtime call failed */
 #define SBI_ENONFINITE     4   /* NaN or Inf appeared in the state */
 #define SBI_ENOTCONVERGED  5   /* adaptive order reached M without meeting adapt_tol */
-#define SBI_ETIMEOUT       6   /* a bounded device-side wait expired (reserved: no kernel of
-                                    * this library waits on another, so none is returned) */
+#define SBI_ETIMEOUT       6   /* a bounded device-side wait expired: a column pass whose inputs
+                                    * arrive by bulk copies gave up waiting for one (reported by
+                                    * sbi_step / sbi_step_streamed with check_finite = 1) */
 
 #define SBI_FP32 0             /* FFTs, multipliers, products in FP32; FP64 state, RK4 sums, invariants */
 #define SBI_FP64 1             /* everything in FP64 (the plain path) */
@@ -121,6 +122,18 @@ typedef struct {
                             in FP64 (the transforms, multipliers and products stay FP32).
                             Both use 8 bytes per value; results differ only in the last bits
                             of the state.  Ignored by SBI_FP64, whose state is FP64. */
+    int    schedule;     /* how a step's launches are split into graph branches (see
+                            sbi_schedule_report); the results are the same bits for every
+                            value.  0 (default): chosen by timing on the first step when
+                            autotune = 1, else B = 3.  B > 0: units of at most total/B
+                            points (member ranges of one group), run as concurrent
+                            branches; 1 gives one branch per group.  -1: one branch per
+                            group, the branches one after another. */
+    int    col_staging;  /* inputs of the column passes: 0 (default): direct loads, or bulk
+                            copies (TMA) into shared memory where the autotuner times that form
+                            faster; 1: bulk copies wherever a column holds at least 32 points
+                            (the autotuner then times block shapes of that form only); -1:
+                            direct loads only.  The arithmetic is the same either way. */
 } sbi_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -331,12 +344,33 @@ int sbi_step_launches(const sbi_ctx* ctx, int* launches);
 /* Choices of the autotuner (opt.autotune), one line per distinct pass shape:
  *   "<pass shape>: rpc|cpb <chosen>/<default> <ms per launch> ms", e.g.
  *   "row nx=512 rows=16384 slots=1 ops=21 CPPPPPPCPPPPPPCPPPPPP: rpc 8/16 0.0910 ms"
+ * A column choice with the suffix "s" (e.g. "cpb 4s/8") is the staged form:
+ * each column's inputs arrive in shared memory by bulk copies (TMA,
+ * cp.async.bulk), the next input in flight while the current one is
+ * transformed; the arithmetic is the same.
  * (ms is -1 for a shape that was not timed: one candidate only, or a pass
  * that is not re-run because its outputs alias its inputs).
  * Writes at most cap bytes (NUL-terminated) into buf and the full length
  * (without the NUL) into *needed; buf may be NULL when cap is 0.  The paper
  * has no counterpart. */
 int sbi_autotune_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* needed);
+
+/* The step schedule: how the members are split into the branches of a step
+ * graph.  A branch (unit) is a range of members of one group (members on the
+ * same grid); the units run as concurrent graph branches, or one after another
+ * ("serial").  Any split gives the same results bit for bit, since every
+ * member's arithmetic is the same; only how the launches fill the GPU changes.
+ * With opt.autotune = 1 the first step of the classical RK4 or Lawson scheme
+ * captures and times each candidate (one branch per group, the serial order,
+ * and splits into member ranges of at most total/B points for B = 2, 3, 4, 6)
+ * on the real buffers, the state saved before and restored exactly after, and
+ * keeps the fastest (the default, B = 3, unless another is 3 % faster).
+ * Report lines:
+ *   "chosen|default|tried <ms> ms per step: <name> [serial|concurrent] <U> units: <nx>x<ny>[m0:m1] ..."
+ * ("default ..." alone, without a time, when nothing was timed).  Empty before
+ * the first step.  Buffer conventions as sbi_autotune_report.  The paper has
+ * no counterpart (its runs are one problem at a time). */
+int sbi_schedule_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 /* Mass and energy of one state without any device allocation.  (This entry
  * point has no counterpart in the paper; it serves callers that may not

@@ -7,6 +7,7 @@ template <> cudaError_t launch_col<double>(int ny, const ColParams& p, cudaStrea
 }
 template <> cudaError_t prepare_col_kernels<double>(int ny) { return prepare_col_impl<double>(ny); }
 template <> int col_geometry<double>(int ny, int* tpc) { return col_geometry_impl<double>(ny, tpc); }
+template <> bool col_stageable<double>(int ny) { return col_stageable_impl<double>(ny); }
 template <> cudaError_t launch_coef_table<double>(void* out, const TableSpec& s, cudaStream_t st) {
   return launch_coef_table_impl<double>(out, s, st);
 }

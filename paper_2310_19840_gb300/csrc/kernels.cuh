@@ -138,6 +138,67 @@ __device__ __forceinline__ void cp_async_elem(V* dst_smem, const V* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk copies global -> shared by the tensor memory accelerator (TMA):
+// cp.async.bulk moves a contiguous run (16-byte aligned ends, a multiple of 16
+// bytes) and signals its completion on an mbarrier in shared memory as
+// transaction bytes.  The barrier is armed with the expected byte count by
+// mbarrier.arrive.expect_tx; a waiter polls mbarrier.try_wait.parity on the
+// phase it expects, with an iteration limit after which it records a timeout
+// in *flag and goes on (the host reports it; no kernel waits forever).
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// A wait gives up after one second of polling, or as soon as another thread
+// has given up (the flag is read every 256 polls); it then records the
+// timeout and waits once more, again for at most a second, for its copy.
+// Returns false when it gave up: the caller issues and waits for nothing more.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, int* flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  for (int round = 0; round < 2; ++round) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+      if (mbar_try_wait(bar, parity)) return round == 0;
+      if ((it & 255u) == 0) {
+        if (global_ns() - t0 > kWaitLimitNs) break;
+        if (round == 0 && flag && *(volatile int*)flag) break;
+      }
+    }
+    if (round == 0 && flag) atomicExch(flag, 1);
+  }
+  return false;
+}
+
 // Block-cooperative asynchronous load of one mixed buffer's rows into the
 // staging rows stg[rl * sw + k], k < W; rows that are absent or inactive are
 // zero-filled with plain stores.
@@ -301,7 +362,7 @@ k_row(const __grid_constant__ RowParams p) {
   V* stg_all = slot_base + p.nslots * rpc * n;     // staging rows
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
   V* fb = fb_all + rloc * fbs;
-  const int row0 = (int)blockIdx.x * rpc;
+  const int row0 = p.row_begin + (int)blockIdx.x * rpc;
   const RowIO io(row0, rpc, p.rows_total, p.ny, p.W, p.active, p.member0);
   const int row = row0 + rloc;
   const bool valid = row < p.rows_total;
@@ -575,7 +636,7 @@ k_rk(const __grid_constant__ RkParams p) {
   const int fbs = p.fbs;                           // scratch row stride
   const int rloc = threadIdx.x / TPR, j = threadIdx.x % TPR;
   V* fb = fb_all + rloc * fbs;
-  const int row0 = (int)blockIdx.x * rpc;
+  const int row0 = p.row_begin + (int)blockIdx.x * rpc;
   const RowIO io(row0, rpc, p.rows_total, p.ny, p.W, p.active, 0);
   const int row = row0 + rloc;
   const bool valid = row < p.rows_total;
@@ -740,6 +801,19 @@ __host__ __device__ constexpr size_t col_smem(int nacc, int cpb) {
   using C = ColCfg<T, NY>;
   return sizeof(cx<T>) * (size_t)cpb * ((size_t)C::SCR + (size_t)C::ACC * nacc);
 }
+// the staged form adds, 128-byte aligned, one input column per column of the
+// block (filled by a bulk copy) and one mbarrier per column
+template <typename T, int NY>
+__host__ __device__ constexpr size_t col_stage_offset(int nacc, int cpb) {
+  return (col_smem<T, NY>(nacc, cpb) + 127) / 128 * 128;
+}
+template <typename T, int NY>
+__host__ __device__ constexpr size_t col_smem_staged(int nacc, int cpb) {
+  return col_stage_offset<T, NY>(nacc, cpb) + sizeof(cx<T>) * (size_t)cpb * NY + 8 * (size_t)cpb;
+}
+// columns long enough for bulk copies (whole 16-byte units, at least 256 bytes)
+template <typename T, int NY>
+inline constexpr bool kColStageable = NY >= 32;
 
 // columns per block of a launch: the size's default CPB, or a smaller count
 // that still makes whole warps (the column FFTs synchronise whole warps)
@@ -766,20 +840,26 @@ __device__ __forceinline__ V cmul_ipow(V x, S f, int q) {   // x f i^q
   return mk<V>(r2, i2);
 }
 
-template <typename T, int NY>
+// STAGED: each column's inputs arrive by bulk copies (TMA) into a staging
+// column in shared memory, the next input in flight while the current one is
+// transformed and accumulated; the arithmetic is that of the direct form.
+template <typename T, int NY, bool STAGED>
 __global__ void __launch_bounds__(ColCfg<T, NY>::THREADS, ColCfg<T, NY>::MIN_BLOCKS)
 k_col(const __grid_constant__ ColParams p) {
   using V = cx<T>;
   using C = ColCfg<T, NY>;
   constexpr int RC = C::RC, TPC = C::TPC, SCR = C::SCR;
   const int cpb = col_cpb<T, NY>(p.cpb);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // staged form: the timeout flag, read first so that its latency overlaps
+  // the set-up below
+  const int gave_up = (STAGED && p.err_flag) ? *(volatile int*)p.err_flag : 0;
   const int c = threadIdx.x / TPC, j = threadIdx.x % TPC;
   V* base = reinterpret_cast<V*>(smem_raw);
   V* sc = base + c * SCR;                                   // FFT scratch
   V* acc0 = base + cpb * SCR + c * C::ACC * p.nacc;         // accumulators
   V* acc1 = acc0 + (p.nacc > 1 ? C::ACC : 0);
-  const int gc = blockIdx.x * cpb + c;
+  const int gc = p.col_begin + (int)blockIdx.x * cpb + c;
   const bool valid = gc < p.cols_total;
   const int member = valid ? gc / p.W : 0;
   const int kx = valid ? gc % p.W : 0;
@@ -803,17 +883,60 @@ k_col(const __grid_constant__ ColParams p) {
     acc0[acc_at(fwd(r))] = mk<V>(T(0), T(0));
     acc1[acc_at(fwd(r))] = mk<V>(T(0), T(0));
   }
+  // staged form: the column's staging run and barrier; thread j = 0 of the
+  // column arms the barrier and issues the copy of input i (16-byte aligned:
+  // a column starts at a multiple of NY elements of its buffer)
+  V* stg = nullptr;
+  unsigned long long* bar = nullptr;
+  constexpr unsigned kColBytes = (unsigned)(sizeof(V) * NY);
+  auto issue = [&](int i) {
+    const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
+    // the column's earlier reads of the staging run (generic proxy) come
+    // before the copy that overwrites it (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, kColBytes);
+    bulk_copy_g2s(stg, src, kColBytes, bar);
+  };
+  // live: the column's copies are issued and waited for; a launch that finds
+  // the timeout flag already set (an earlier wait gave up) moves no data,
+  // and a thread whose wait gave up issues and waits for nothing more
+  bool live = act;
+  if constexpr (STAGED) {
+    unsigned char* st0 = smem_raw + col_stage_offset<T, NY>(p.nacc, cpb);
+    stg = reinterpret_cast<V*>(st0) + c * NY;
+    bar = reinterpret_cast<unsigned long long*>(st0 + sizeof(V) * (size_t)cpb * NY) + c;
+    if (gave_up) live = false;
+    if (j == 0) {
+      mbar_init(bar, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();   // barriers initialised before any thread waits on them
+    if (j == 0 && live && p.nin > 0) issue(0);
+  }
 
   for (int i = 0; i < p.nin; ++i) {
-    const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
     V x[RC];
+    if constexpr (STAGED) {
+      if (live) live = mbar_wait_bounded(bar, (unsigned)(i & 1), p.err_flag);
 #pragma unroll
-    for (int r = 0; r < RC; ++r) x[r] = act ? src[nat(r)] : mk<V>(T(0), T(0));
+      for (int r = 0; r < RC; ++r) x[r] = live ? stg[nat(r)] : mk<V>(T(0), T(0));
+    } else {
+      const V* src = reinterpret_cast<const V*>(p.buf[i].ptr) + member * p.buf[i].stride + col_off;
+#pragma unroll
+      for (int r = 0; r < RC; ++r) x[r] = act ? src[nat(r)] : mk<V>(T(0), T(0));
+    }
     if constexpr (SPLIT) {
-      __syncthreads();        // scratch free
+      __syncthreads();        // scratch free (and, staged: the staging column read)
+      if constexpr (STAGED) {
+        if (j == 0 && live && i + 1 < p.nin) issue(i + 1);
+      }
       fft_split_dif<NY, -1>(x, sc, j, tw);         // x[r]: mode fwd(r)
     } else if constexpr (NY > 1) {
-      group_sync<C::WARP>();  // scratch free
+      group_sync<C::WARP>();  // scratch free (and, staged: the staging column read)
+      if constexpr (STAGED) {
+        static_assert(C::WARP, "staged columns of the plain form fit one warp");
+        if (j == 0 && live && i + 1 < p.nin) issue(i + 1);
+      }
       fft_block_regs<NY, RC, -1>(x, sc, j, tw);   // x[r]: mode j + r TPC
     }
     for (int q = p.term_begin[i]; q < p.term_begin[i + 1]; ++q) {
@@ -995,15 +1118,19 @@ cudaError_t prepare_nx() {
 
 template <typename T, int NY>
 cudaError_t prepare_ny() {
-  return cudaFuncSetAttribute(k_col<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem<T, NY>(kMaxColAcc, ColCfg<T, NY>::CPB));
+  cudaError_t e = cudaFuncSetAttribute(k_col<T, NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)col_smem<T, NY>(kMaxColAcc, ColCfg<T, NY>::CPB));
+  if (e != cudaSuccess || !kColStageable<T, NY>) return e;
+  return cudaFuncSetAttribute(k_col<T, NY, kColStageable<T, NY>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)col_smem_staged<T, NY>(kMaxColAcc, ColCfg<T, NY>::CPB));
 }
 
 template <typename T, int NX>
 cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
-  if (p.rpc < 1 || p.rpc > C::RPC_MAX) return cudaErrorInvalidValue;
-  const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
+  if (p.rpc < 1 || p.rpc > C::RPC_MAX || p.row_begin < 0 || p.row_begin >= p.rows_total)
+    return cudaErrorInvalidValue;
+  const int blocks = (p.rows_total - p.row_begin + p.rpc - 1) / p.rpc;
   RowParams q = p;
   const bank::RowStrides rs =
       bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), false, kShuffleFft<C::n, C::R>, C::FBUF);
@@ -1018,8 +1145,9 @@ cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
 template <typename T, int NX>
 cudaError_t launch_rk_n(const RkParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
-  if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC) return cudaErrorInvalidValue;
-  const int blocks = (p.rows_total + p.rpc - 1) / p.rpc;
+  if (p.rpc < 1 || p.rpc > RkCfg<NX>::RPC || p.row_begin < 0 || p.row_begin >= p.rows_total)
+    return cudaErrorInvalidValue;
+  const int blocks = (p.rows_total - p.row_begin + p.rpc - 1) / p.rpc;
   RkParams q = p;
   q.fbs = bank::choose(C::n, C::R, C::TPR, p.rpc, p.W, (int)sizeof(cx<T>), true, false, C::FBUF).fbs;
   const size_t smem = sizeof(cx<T>) * (size_t)q.rpc * q.fbs;
@@ -1033,9 +1161,16 @@ cudaError_t launch_col_n(const ColParams& p, cudaStream_t st) {
   using C = ColCfg<T, NY>;
   if (p.nacc < 1 || p.nacc > kMaxColAcc) return cudaErrorInvalidValue;
   const int cpb = col_cpb<T, NY>(p.cpb);
-  if (!col_cpb_ok<T, NY>(cpb)) return cudaErrorInvalidValue;
-  const int blocks = (p.cols_total + cpb - 1) / cpb;
-  k_col<T, NY><<<blocks, C::TPC * cpb, col_smem<T, NY>(p.nacc, cpb), st>>>(p);
+  if (!col_cpb_ok<T, NY>(cpb) || p.col_begin < 0 || p.col_begin >= p.cols_total) return cudaErrorInvalidValue;
+  const int blocks = (p.cols_total - p.col_begin + cpb - 1) / cpb;
+  if (p.staged) {
+    if constexpr (kColStageable<T, NY>)
+      k_col<T, NY, true><<<blocks, C::TPC * cpb, col_smem_staged<T, NY>(p.nacc, cpb), st>>>(p);
+    else
+      return cudaErrorInvalidValue;
+  } else {
+    k_col<T, NY, false><<<blocks, C::TPC * cpb, col_smem<T, NY>(p.nacc, cpb), st>>>(p);
+  }
   return cudaGetLastError();
 }
 
@@ -1133,6 +1268,16 @@ int row_tpr_impl(int nx) {
     SBI_FOR_NX(SBI_CASE)
 #undef SBI_CASE
     default: return 0;
+  }
+}
+
+template <typename T>
+bool col_stageable_impl(int ny) {
+  switch (ny) {
+#define SBI_CASE(N) case N: return kColStageable<T, N>;
+    SBI_FOR_NY(SBI_CASE)
+#undef SBI_CASE
+    default: return false;
   }
 }
 

@@ -155,11 +155,20 @@ struct Group {
   size_t mixed_elems() const { return (size_t)ny * W; }
 };
 
+// One branch of a step schedule: the members [m0, m1) (local indices) of one
+// group.  Every pass of a step covers whole rows and columns of each member, so
+// a group's passes restricted to a member range are the same launches over
+// fewer rows or columns, with the same arithmetic per member.
+struct Unit {
+  int group, m0, m1;
+  bool operator==(const Unit& o) const { return group == o.group && m0 == o.m0 && m1 == o.m1; }
+};
+
 struct GraphEntry {
   double dt;
   bool prof;
   int kind = 0;                      // StepKind
-  int group = -1;                    // -1: every group as concurrent branches; else that group alone
+  int group = -1;                    // -1: every unit of the schedule; else that unit alone
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
@@ -191,10 +200,16 @@ struct sbi_ctx {
   std::vector<cudaEvent_t> pevents;    // streamed step: start, then one per group
   std::vector<Group> groups;
   std::vector<std::pair<int, int>> where;  // member -> (group, local index)
+  // step schedule: the branches of a step graph (concurrent, or one after
+  // another when serial), chosen by timing on the first step (choose_schedule)
+  std::vector<Unit> units;
+  bool serial = false;
+  bool sched_done = false;
+  std::string sched_report;
   std::vector<void*> allocs;
   void* tw = nullptr;
   void* wgt = nullptr;  // shared sponge weight (working precision) or null
-  int* d_flags = nullptr;  // [0]: non-finite state
+  int* d_flags = nullptr;  // [0]: non-finite state; [1]: a bounded wait gave up
   double* d_partials = nullptr;
   size_t partial_cap = 0;
   std::list<GraphEntry> graphs;   // stable addresses: two graphs may be held at once
@@ -511,6 +526,9 @@ struct Planner {
     p.filt_beta2 = c->opt.filt_beta2;
     p.nacc = nacc;
     p.tw = c->tw;
+    p.err_flag = c->d_flags + 1;
+    p.staged = (c->opt.col_staging == 1 &&
+                (c->fp64 ? col_stageable<double>(g.ny) : col_stageable<float>(g.ny))) ? 1 : 0;
     const double scale = 1.0 / ((double)g.nx * g.ny);
     size_t total_terms = 0;
     for (auto& in : ins) total_terms += in.terms.size();
@@ -1634,20 +1652,28 @@ std::string pass_signature(const Pass& p) {
   if (p.kind == PK_ROW) {
     std::string ops;
     for (int o = 0; o < p.row.nops; ++o) ops += "CPNWV"[p.row.ops[o].kind < 5 ? p.row.ops[o].kind : 0];
-    snprintf(b, sizeof(b), "row nx=%d rows=%d slots=%d ops=%d ", p.nsize, p.row.rows_total, p.row.nslots,
-             p.row.nops);
+    snprintf(b, sizeof(b), "row nx=%d rows=%d slots=%d ops=%d ", p.nsize, p.row.rows_total - p.row.row_begin,
+             p.row.nslots, p.row.nops);
     return b + ops;
   }
   snprintf(b, sizeof(b), "col ny=%d cols=%d in=%d terms=%d out=%d acc=%d pass=%d", p.nsize,
-           p.col.cols_total, p.col.nin, p.col.nterms, p.col.nouts, p.col.nacc, p.col.npass);
+           p.col.cols_total - p.col.col_begin, p.col.nin, p.col.nterms, p.col.nouts, p.col.nacc, p.col.npass);
   return b;
 }
 
+constexpr int kStagedTag = 1 << 16;
+
 int tune_pass(sbi_ctx* c, Pass& p, cudaStream_t st) {
   if (!c->opt.autotune || (p.kind != PK_ROW && p.kind != PK_COL)) return SBI_OK;
+  // a column choice packs the columns per block and the staged form (bulk
+  // copies of the inputs into shared memory) as cpb + kStagedTag * staged
   auto apply = [&](Pass& q, int v) {
-    if (q.kind == PK_ROW) q.row.rpc = v;
-    else q.col.cpb = v;
+    if (q.kind == PK_ROW) {
+      q.row.rpc = v;
+    } else {
+      q.col.cpb = v % kStagedTag;
+      q.col.staged = v / kStagedTag;
+    }
   };
   const std::string key = pass_signature(p);
   auto it = c->tuned.find(key);
@@ -1665,9 +1691,19 @@ int tune_pass(sbi_ctx* c, Pass& p, cudaStream_t st) {
   } else {
     int tpc = 0;
     const int cpb = c->fp64 ? col_geometry<double>(p.nsize, &tpc) : col_geometry<float>(p.nsize, &tpc);
-    deflt = p.col.cpb > 0 ? p.col.cpb : cpb;
-    for (int v = deflt; v >= 1 && cand.size() < 4; v /= 2)
-      if (tpc > 0 && (v * tpc) % 32 == 0) cand.push_back(v);
+    const int base = p.col.cpb > 0 ? p.col.cpb : cpb;
+    deflt = base + kStagedTag * p.col.staged;
+    // the staged form is a candidate where the option leaves the choice open
+    const bool stg = c->opt.col_staging == 0 &&
+                     (c->fp64 ? col_stageable<double>(p.nsize) : col_stageable<float>(p.nsize));
+    for (int staged = p.col.staged; staged <= (stg ? 1 : p.col.staged); ++staged) {
+      int k = 0;
+      for (int v = base; v >= 1 && k < 3; v /= 2)
+        if (tpc > 0 && (v * tpc) % 32 == 0) {
+          cand.push_back(v + kStagedTag * staged);
+          ++k;
+        }
+    }
   }
   int best = deflt;
   double best_ms = -1.0, deflt_ms = -1.0;
@@ -1784,14 +1820,144 @@ std::vector<std::vector<Pass>> plan_step_groups(sbi_ctx* c, double dt, bool* oom
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// Step schedule.  The members of a group are independent problems, so the
+// passes of a step can run over any partition of the batch into units (member
+// ranges of one group), as concurrent graph branches or one unit after
+// another: the arithmetic of every member is the same in every case, and so
+// are the results, bit for bit.  What changes is how the launches fill the
+// GPU (launch sizes, the tails of their last waves, overlap between branches).
+// The candidates are the serial order, one branch per group, and splits of the
+// groups into nearly equal member ranges of at most total/B points for
+// B = 2, 3, 4, 6; B = 3 is the default.  On the first step of the classical
+// RK4 or Lawson scheme, with autotuning on, every candidate's step graph is
+// captured and timed on the real buffers (one warm-up and three timed replays,
+// the state saved before and restored after), and the fastest is kept; the
+// default stays unless another candidate is at least 3 % faster.
+// ---------------------------------------------------------------------------
+bool pass_sliceable(const Pass& p) { return p.kind == PK_ROW || p.kind == PK_COL || p.kind == PK_RK; }
+
+// a group's pass restricted to its members [m0, m1)
+Pass slice_pass(const Pass& p, const Group& g, int m0, int m1) {
+  Pass q = p;
+  if (m0 == 0 && m1 == g.n) return q;
+  if (p.kind == PK_ROW) {
+    q.row.row_begin = m0 * g.ny;
+    q.row.rows_total = m1 * g.ny;
+  } else if (p.kind == PK_COL) {
+    q.col.col_begin = m0 * g.W;
+    q.col.cols_total = m1 * g.W;
+  } else {
+    q.rk.row_begin = m0 * g.ny;
+    q.rk.rows_total = m1 * g.ny;
+  }
+  const double f = (double)(m1 - m0) / (double)g.n;
+  q.bytes *= f;
+  q.xforms *= f;
+  return q;
+}
+
+struct Sched {
+  std::vector<Unit> units;
+  bool serial;
+  std::string name;
+};
+
+// Units with at most cap points each (cap 0: one unit per group); only
+// groups whose passes can all be sliced are split.
+std::vector<Unit> units_for_cap(const sbi_ctx* c, size_t cap, const std::vector<bool>& sliceable) {
+  std::vector<Unit> u;
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    const Group& g = c->groups[gi];
+    const size_t pts = g.phys_elems() * (size_t)g.n;
+    int k = 1;
+    if (sliceable[gi] && cap > 0) k = (int)std::min<size_t>((size_t)g.n, (pts + cap - 1) / cap);
+    for (int q = 0; q < k; ++q)
+      u.push_back(Unit{(int)gi, (int)((long long)q * g.n / k), (int)((long long)(q + 1) * g.n / k)});
+  }
+  return u;
+}
+
+// which groups' step passes can all be restricted to member ranges
+std::vector<bool> groups_sliceable(sbi_ctx* c, bool* oom) {
+  std::vector<bool> ok(c->groups.size(), true);
+  std::vector<int> kinds = {SK_STEP};
+  if (c->opt.integrator == SBI_IF_RK45) kinds = {SK_RK45_A, SK_RK45_B};
+  for (int kind : kinds) {
+    const std::vector<std::vector<Pass>> gps = plan_step_groups(c, 1.0, oom, kind);
+    for (size_t gi = 0; gi < gps.size(); ++gi)
+      for (const Pass& p : gps[gi])
+        if (!pass_sliceable(p)) ok[gi] = false;
+  }
+  return ok;
+}
+
+// the candidate schedules, the default first
+std::vector<Sched> sched_candidates(sbi_ctx* c, bool* oom) {
+  const std::vector<bool> sl = groups_sliceable(c, oom);
+  size_t total = 0, biggest = 0;
+  for (const auto& g : c->groups) {
+    total += g.phys_elems() * (size_t)g.n;
+    biggest = std::max(biggest, g.phys_elems());
+  }
+  std::vector<Sched> out;
+  auto add = [&](std::vector<Unit> u, bool serial, const std::string& name) {
+    if (u.size() < 2) serial = false;   // one unit: the same graph either way
+    for (const auto& s2 : out)
+      if (s2.units == u && s2.serial == serial) return;
+    out.push_back(Sched{std::move(u), serial, name});
+  };
+  auto cap_of = [&](size_t B) { return std::max(biggest, (total + B - 1) / B); };
+  add(units_for_cap(c, cap_of(3), sl), false, "split total/3");
+  add(units_for_cap(c, 0, sl), true, "serial groups");
+  add(units_for_cap(c, 0, sl), false, "one branch per group");
+  for (size_t B : {2, 4, 6}) add(units_for_cap(c, cap_of(B), sl), false, "split total/" + std::to_string(B));
+  return out;
+}
+
+// the schedule opt.schedule names (-1: serial groups; B > 0: split total/B)
+Sched forced_sched(sbi_ctx* c, bool* oom) {
+  const std::vector<bool> sl = groups_sliceable(c, oom);
+  size_t total = 0, biggest = 0;
+  for (const auto& g : c->groups) {
+    total += g.phys_elems() * (size_t)g.n;
+    biggest = std::max(biggest, g.phys_elems());
+  }
+  const int B = c->opt.schedule;
+  Sched s{B < 0 ? units_for_cap(c, 0, sl)
+                : units_for_cap(c, std::max(biggest, (total + (size_t)B - 1) / (size_t)B), sl),
+          B < 0, B < 0 ? "serial groups" : "split total/" + std::to_string(B)};
+  if (s.units.size() < 2) s.serial = false;
+  return s;
+}
+
+// The passes of one step per unit of the current schedule (before the
+// schedule is chosen: the named one, else the default).
+std::vector<std::vector<Pass>> plan_step_units(sbi_ctx* c, double dt, bool* oom, int kind = SK_STEP) {
+  if (c->units.empty()) {
+    const Sched s = c->opt.schedule != 0 ? forced_sched(c, oom) : sched_candidates(c, oom)[0];
+    c->units = s.units;
+    c->serial = s.serial;
+  }
+  const std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, oom, kind);
+  std::vector<std::vector<Pass>> out;
+  for (const Unit& u : c->units) {
+    const Group& g = c->groups[u.group];
+    std::vector<Pass> v;
+    for (const Pass& p : gps[u.group]) v.push_back(slice_pass(p, g, u.m0, u.m1));
+    out.push_back(std::move(v));
+  }
+  return out;
+}
+
 std::vector<Pass> plan_step(sbi_ctx* c, double dt, bool* oom) {
   std::vector<Pass> all;
   if (c->opt.integrator == SBI_IF_RK45) {
     for (int kind : {SK_RK45_A, SK_RK45_B})
-      for (auto& v : plan_step_groups(c, dt, oom, kind)) all.insert(all.end(), v.begin(), v.end());
+      for (auto& v : plan_step_units(c, dt, oom, kind)) all.insert(all.end(), v.begin(), v.end());
     return all;
   }
-  for (auto& v : plan_step_groups(c, dt, oom)) all.insert(all.end(), v.begin(), v.end());
+  for (auto& v : plan_step_units(c, dt, oom)) all.insert(all.end(), v.begin(), v.end());
   return all;
 }
 
@@ -1831,14 +1997,14 @@ void free_graphs(sbi_ctx* c) {
   c->graphs.clear();
 }
 
-int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, int group = -1) {
-  for (auto& ge : c->graphs)
-    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind && ge.group == group) { *out = &ge; return SBI_OK; }
+// Capture the step graph of the current schedule (unit < 0: every unit; else
+// that unit alone, for the streamed step).
+int build_step_graph(sbi_ctx* c, double dt, int kind, int unit, GraphEntry& ge) {
   bool oom = false;
-  std::vector<std::vector<Pass>> gps = plan_step_groups(c, dt, &oom, kind);
+  std::vector<std::vector<Pass>> gps = plan_step_units(c, dt, &oom, kind);
   if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
-  if (group >= 0) {   // one group's passes alone (the streamed step)
-    std::vector<Pass> one = gps.at((size_t)group);
+  if (unit >= 0) {   // one unit's passes alone (the streamed step)
+    std::vector<Pass> one = gps.at((size_t)unit);
     gps.assign(1, one);
   }
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
@@ -1851,11 +2017,10 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, 
     }
   size_t npasses = 0;
   for (auto& v : gps) npasses += v.size();
-  GraphEntry ge;
   ge.dt = dt;
   ge.prof = c->prof;
   ge.kind = kind;
-  ge.group = group;
+  ge.group = unit;
   if (c->prof) {   // the profiled graph owns one event pair per pass
     for (size_t gi = 0; gi < gps.size(); ++gi)
       for (size_t i = 0; i < gps[gi].size(); ++i) {
@@ -1867,7 +2032,7 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, 
         ge.ev_family.push_back(family_of(gps[gi][i]));
       }
   }
-  // one branch per group: fork from the capture stream, join back
+  // one branch per unit: fork from the capture stream, join back
   while (c->gstreams.size() < gps.size()) {
     cudaStream_t s2;
     CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "stream");
@@ -1880,9 +2045,10 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, 
   }
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   int rc = SBI_OK;
-  // the groups run as concurrent branches; a profiled replay runs them one
-  // after the other, so that each launch's event pair times that launch alone
-  const bool branch = gps.size() > 1 && !c->prof;
+  // the units run as concurrent branches unless the schedule is serial; a
+  // profiled replay runs them one after the other, so that each launch's
+  // event pair times that launch alone
+  const bool branch = gps.size() > 1 && !c->prof && !c->serial;
   if (branch) cudaEventRecord(c->gevents[0], c->cap);
   size_t evi = 0;
   for (size_t gi = 0; gi < gps.size() && rc == SBI_OK; ++gi) {
@@ -1900,30 +2066,207 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, 
     }
   }
   // the simulation time of the next step (read by the wavemaker passes)
-  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP && group < 0) {
+  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP && unit < 0) {
     k_advance_time<<<1, 32, 0, c->cap>>>(c->d_time, dt);
     const cudaError_t el = cudaGetLastError();
     if (el != cudaSuccess) rc = cuda_fail(c, el, "kernel launch");
     else ++npasses;
   }
   cudaError_t e = cudaStreamEndCapture(c->cap, &ge.graph);
-  auto drop_events = [&]() {
+  auto drop = [&]() {
     for (auto ev : ge.ev) cudaEventDestroy(ev);
+    ge.ev.clear();
+    if (ge.graph) cudaGraphDestroy(ge.graph);
+    ge.graph = nullptr;
   };
   if (rc) {
-    drop_events();
+    drop();
     return rc;
   }
   if (e != cudaSuccess) {
-    drop_events();
+    drop();
     return cuda_fail(c, e, "end capture");
   }
   e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
   if (e != cudaSuccess) {
-    drop_events();
+    drop();
     return cuda_fail(c, e, "graph instantiate");
   }
   ge.launches = (int)npasses;
+  return SBI_OK;
+}
+
+void destroy_graph(GraphEntry& ge) {
+  if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  if (ge.graph) cudaGraphDestroy(ge.graph);
+  for (auto e : ge.ev) cudaEventDestroy(e);
+  ge.exec = nullptr;
+  ge.graph = nullptr;
+  ge.ev.clear();
+}
+
+// Device buffers a step reads before it writes them: the state, the working
+// copies of the state (physical eta, mixed eta^ and phi^), the simulation
+// time and the non-finite flag.  A copy of them lets the schedule candidates
+// be timed on real steps and the state be put back exactly afterwards.
+struct Snapshot {
+  std::vector<std::pair<void*, size_t>> bufs;
+  void* scratch = nullptr;
+  size_t total = 0;
+};
+
+void snapshot_free(sbi_ctx* c, Snapshot& s) {
+  if (!s.scratch) return;
+  cudaStreamSynchronize(c->cap);
+  if (c->opt.dev_free) c->opt.dev_free(s.scratch, c->opt.alloc_user);
+  else cudaFree(s.scratch);
+  s.scratch = nullptr;
+}
+
+// 1: taken; 0: not enough device memory (nothing to undo); < 0: CUDA error
+int snapshot_take(sbi_ctx* c, Snapshot& s) {
+  auto add = [&](void* p, size_t bytes) {
+    if (p && bytes) s.bufs.push_back({p, bytes});
+  };
+  for (auto& g : c->groups) {
+    const size_t np = g.phys_elems() * (size_t)g.n;
+    const size_t nm = g.mixed_elems() * (size_t)g.n * 2 * c->real_size;
+    add(g.eta0, np * 8);
+    add(g.phi0, np * 8);
+    add(g.eta_w, np * c->real_size);
+    for (const char* name : {"eta_m", "phi_m"}) {
+      auto it = g.mixed.find(name);
+      if (it != g.mixed.end()) add(it->second, nm);
+    }
+  }
+  add(c->d_time, c->d_time ? sizeof(double) : 0);
+  add(c->d_flags, 64);
+  for (auto& b : s.bufs) s.total += (b.second + 255) / 256 * 256;
+  void* p = nullptr;
+  if (c->opt.dev_alloc) p = c->opt.dev_alloc(s.total, c->opt.alloc_user);
+  else if (cudaMalloc(&p, s.total) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) return 0;
+  s.scratch = p;
+  size_t off = 0;
+  for (auto& b : s.bufs) {
+    if (cudaMemcpyAsync((char*)p + off, b.first, b.second, cudaMemcpyDeviceToDevice, c->cap) != cudaSuccess)
+      return -1;
+    off += (b.second + 255) / 256 * 256;
+  }
+  return 1;
+}
+
+int snapshot_restore(sbi_ctx* c, const Snapshot& s) {
+  size_t off = 0;
+  for (auto& b : s.bufs) {
+    CK(cudaMemcpyAsync(b.first, (char*)s.scratch + off, b.second, cudaMemcpyDeviceToDevice, c->cap), "restore");
+    off += (b.second + 255) / 256 * 256;
+  }
+  CK(cudaStreamSynchronize(c->cap), "restore");
+  return SBI_OK;
+}
+
+std::string sched_desc(const sbi_ctx* c, const Sched& s) {
+  std::string d = s.name + (s.serial ? " [serial]" : " [concurrent]") + " " + std::to_string(s.units.size()) + " units:";
+  for (const Unit& u : s.units) {
+    const Group& g = c->groups[u.group];
+    d += " " + std::to_string(g.nx) + "x" + std::to_string(g.ny) + "[" + std::to_string(u.m0) + ":" +
+         std::to_string(u.m1) + "]";
+  }
+  return d;
+}
+
+// Choose the step schedule (see the comment above pass_sliceable).
+int choose_schedule(sbi_ctx* c, double dt, int kind) {
+  if (c->sched_done) return SBI_OK;
+  bool oom = false;
+  std::vector<Sched> cands = sched_candidates(c, &oom);
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
+  if (c->opt.schedule != 0) {
+    // a schedule named by the caller: nothing is timed
+    const Sched s = forced_sched(c, &oom);
+    if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
+    c->units = s.units;
+    c->serial = s.serial;
+    c->sched_done = true;
+    c->sched_report = "forced " + sched_desc(c, s) + "\n";
+    return SBI_OK;
+  }
+  c->units = cands[0].units;
+  c->serial = cands[0].serial;
+  if (c->prof) return SBI_OK;   // a profiled replay keeps the default until a plain step chooses
+  c->sched_done = true;
+  c->sched_report = "default " + sched_desc(c, cands[0]) + "\n";
+  if (!c->opt.autotune || kind != SK_STEP || cands.size() < 2) return SBI_OK;
+  Snapshot snap;
+  const int taken = snapshot_take(c, snap);
+  if (taken < 0) {
+    snapshot_free(c, snap);
+    return cuda_fail(c, cudaGetLastError(), "state copy");
+  }
+  if (taken == 0) {
+    c->sched_report += "not timed: no device memory for a copy of the state\n";
+    return SBI_OK;
+  }
+  if (!c->tune_ev[0]) {
+    CK(cudaEventCreate(&c->tune_ev[0]), "event");
+    CK(cudaEventCreate(&c->tune_ev[1]), "event");
+  }
+  std::vector<double> ms(cands.size(), -1.0);
+  int rc = SBI_OK;
+  for (size_t i = 0; i < cands.size() && rc == SBI_OK; ++i) {
+    c->units = cands[i].units;
+    c->serial = cands[i].serial;
+    GraphEntry ge;
+    rc = build_step_graph(c, dt, kind, -1, ge);
+    if (rc) break;
+    auto replay = [&]() { return cudaGraphLaunch(ge.exec, c->cap); };
+    cudaError_t e = replay();   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(c->tune_ev[0], c->cap);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = replay();
+    if (e == cudaSuccess) e = cudaEventRecord(c->tune_ev[1], c->cap);
+    if (e == cudaSuccess) e = cudaEventSynchronize(c->tune_ev[1]);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, c->tune_ev[0], c->tune_ev[1]);
+    destroy_graph(ge);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "schedule timing");
+    else ms[i] = t / 3.0;
+    if (rc == SBI_OK) rc = snapshot_restore(c, snap);
+  }
+  snapshot_free(c, snap);
+  if (rc) return rc;
+  size_t best = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (ms[i] < ms[best]) best = i;
+  if (best != 0 && !(ms[best] < 0.97 * ms[0])) best = 0;
+  c->units = cands[best].units;
+  c->serial = cands[best].serial;
+  c->sched_report.clear();
+  for (size_t i = 0; i < cands.size(); ++i) {
+    char t[64];
+    snprintf(t, sizeof(t), "%.4f ms per step: ", ms[i]);
+    c->sched_report += std::string(i == best ? "chosen " : (i == 0 ? "default " : "tried ")) + t +
+                       sched_desc(c, cands[i]) + "\n";
+  }
+  if (best != 0) c->sched_report += "default " + sched_desc(c, cands[0]) + "\n";
+  return SBI_OK;
+}
+
+int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, int unit = -1) {
+  if (!c->sched_done) {
+    const int rc = choose_schedule(c, dt, kind);
+    if (rc) return rc;
+    // graphs captured under an earlier (default) schedule are dropped
+    if (c->sched_done) free_graphs(c);
+  }
+  for (auto& ge : c->graphs)
+    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind && ge.group == unit) { *out = &ge; return SBI_OK; }
+  GraphEntry ge;
+  const int rc = build_step_graph(c, dt, kind, unit, ge);
+  if (rc) return rc;
   c->graphs.push_back(ge);
   *out = &c->graphs.back();
   return SBI_OK;
@@ -2068,10 +2411,6 @@ int upload_real(sbi_ctx* c, void* dst, const std::vector<double>& v, size_t offs
   return SBI_OK;
 }
 
-// a member group (one concurrent branch of the step graph) holds at most
-// 1/kBranchShare of the batch's points unless one member is larger
-constexpr size_t kBranchShare = 3;
-
 int create_impl(int n, const sbi_grid* grids, double gravity, const double* const* h,
                 const sbi_options* opt_in, sbi_ctx** out) {
   if (!out) return fail(nullptr, SBI_EINVAL, "out is NULL");
@@ -2097,6 +2436,8 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
     return fail(nullptr, SBI_EINVAL, "the HOS diagnostic is not combined with adapt_tol > 0");
   if (opt.integrator != SBI_RK4 && opt.adapt_tol > 0.0)
     return fail(nullptr, SBI_EINVAL, "the integrating factor (integrator) is not combined with adapt_tol > 0");
+  if (opt.schedule < -1) return fail(nullptr, SBI_EINVAL, "schedule must be -1, 0 or a positive B");
+  if (opt.col_staging < -1 || opt.col_staging > 1) return fail(nullptr, SBI_EINVAL, "col_staging must be -1, 0 or 1");
   if ((opt.dev_alloc == nullptr) != (opt.dev_free == nullptr))
     return fail(nullptr, SBI_EINVAL, "dev_alloc and dev_free must be given together");
   for (int i = 0; i < n; ++i) {
@@ -2174,48 +2515,18 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
     return bail(SBI_ECUDA);
   }
 
-  // group members with identical grids and depth settings.  The groups run
-  // as concurrent graph branches, so a grid that holds more than a third of
-  // the batch's points is split into consecutive chunks of nearly equal size
-  // (one group each): the branches then carry similar work.
+  // group members with identical grids and depth settings: every pass of a
+  // group is one launch over its members (or over a member range of it, see
+  // the step schedule)
   c->where.resize(n);
-  std::vector<int> sig(n, -1), rank(n, 0);
-  std::vector<int> sig_count;
-  std::vector<size_t> sig_pts;
-  size_t total_pts = 0, max_member = 0;
+  std::vector<int> sig(n, -1);
   for (int i = 0; i < n; ++i) {
-    const size_t pts = (size_t)grids[i].nx * grids[i].ny;
-    total_pts += pts;
-    max_member = std::max(max_member, pts);
     for (int j = 0; j < i && sig[i] < 0; ++j)
       if (grids[j].nx == grids[i].nx && grids[j].ny == grids[i].ny && grids[j].Lx == grids[i].Lx &&
           (grids[i].ny == 1 || grids[j].Ly == grids[i].Ly) && h0s[j] == h0s[i] && var[j] == var[i])
         sig[i] = sig[j];
     if (sig[i] < 0) {
-      sig[i] = (int)sig_count.size();
-      sig_count.push_back(0);
-      sig_pts.push_back(0);
-    }
-    rank[i] = sig_count[sig[i]]++;
-    sig_pts[sig[i]] += pts;
-  }
-  const size_t branch_cap = std::max(max_member, (total_pts + kBranchShare - 1) / kBranchShare);
-  std::vector<int> per_chunk(sig_count.size());
-  for (size_t q = 0; q < sig_count.size(); ++q) {
-    const int chunks = (int)std::min<size_t>((size_t)sig_count[q], (sig_pts[q] + branch_cap - 1) / branch_cap);
-    per_chunk[q] = (sig_count[q] + chunks - 1) / chunks;
-  }
-  std::vector<std::pair<int, int>> group_key;   // (signature, chunk) of each group
-  for (int i = 0; i < n; ++i) {
-    const std::pair<int, int> key{sig[i], rank[i] / per_chunk[sig[i]]};
-    int gi = -1;
-    for (size_t q = 0; q < group_key.size(); ++q)
-      if (group_key[q] == key) {
-        gi = (int)q;
-        break;
-      }
-    if (gi < 0) group_key.push_back(key);
-    if (gi < 0) {
+      sig[i] = (int)c->groups.size();
       Group g;
       g.nx = grids[i].nx;
       g.ny = grids[i].ny;
@@ -2232,10 +2543,10 @@ int create_impl(int n, const sbi_grid* grids, double gravity, const double* cons
       g.ky_keep = std::max(g.ky_keep, 1);
       g.W = g.kx_keep;
       c->groups.push_back(g);
-      gi = (int)c->groups.size() - 1;
     }
-    c->where[i] = {gi, (int)c->groups[gi].members.size()};
-    c->groups[gi].members.push_back(i);
+    Group& g = c->groups[sig[i]];
+    c->where[i] = {sig[i], (int)g.members.size()};
+    g.members.push_back(i);
   }
   for (auto& g : c->groups) g.n = (int)g.members.size();
 
@@ -2327,6 +2638,8 @@ void sbi_default_options(sbi_options* opt) {
   opt->check_finite = 1;
   opt->set_state_dealias = 1;
   opt->autotune = 1;
+  opt->schedule = 0;
+  opt->col_staging = 0;
 }
 
 int sbi_create(const sbi_grid* g, double gravity, const double* h, const sbi_options* opt,
@@ -2664,6 +2977,21 @@ int sbi_vertical_velocity_implicit(sbi_ctx* c, int member, int iterations, doubl
   return SBI_OK;
 }
 
+// The device flags after a step: [0] the state became non-finite, [1] a
+// bounded wait of a staged column pass gave up (cleared once reported).
+int check_flags(sbi_ctx* c, const char* what) {
+  int flag[2] = {0, 0};
+  CK(cudaMemcpyAsync(flag, c->d_flags, sizeof(flag), cudaMemcpyDeviceToHost, c->stream), "flag");
+  CK(cudaStreamSynchronize(c->stream), what);
+  if (flag[1]) {
+    CK(cudaMemsetAsync(c->d_flags + 1, 0, sizeof(int), c->stream), "flag");
+    CK(cudaStreamSynchronize(c->stream), what);
+    return fail(c, SBI_ETIMEOUT, "a bounded wait for a bulk copy of a column pass gave up");
+  }
+  if (flag[0]) return fail(c, SBI_ENONFINITE, "the state became non-finite");
+  return SBI_OK;
+}
+
 int sbi_step(sbi_ctx* c, double dt, int n) {
   if (!c) return SBI_EINVAL;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
@@ -2694,44 +3022,54 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
       c->t_host += dt;
     }
   }
-  if (c->opt.check_finite) {
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
-    CK(cudaStreamSynchronize(c->stream), "step");
-    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
-  }
+  if (c->opt.check_finite) return check_flags(c, "step");
   return SBI_OK;
 }
 
-// Upload, n steps and download of every member's state, pipelined per member
-// group: each group runs on its own stream (priority falling with the group
-// index), so the copies of one group overlap the steps of the others.  Every
-// launch and its arguments are those of sbi_set_state_all + sbi_step +
-// sbi_get_state_all (same passes, same block shapes), so the result is the
-// same bits.
+// Upload, n steps and download of every member's state, pipelined per unit of
+// the step schedule: each unit (a member range of one group) runs on its own
+// stream (priority falling with the unit index), so the copies of one unit
+// overlap the steps of the others.  Every launch and its arguments are those
+// of sbi_set_state_all + sbi_step + sbi_get_state_all restricted to the
+// unit's members (same passes, same block shapes), so the result is the same
+// bits.
 int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, double dt, int n,
                       double* eta_out, double* phi_out) {
   if (!c) return SBI_EINVAL;
   if (!eta_in || !phi_in || !eta_out || !phi_out) return fail(c, SBI_EINVAL, "state buffers must not be NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
   if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
-  const size_t G = c->groups.size();
-  // one group, the adaptive pair (host-side tables per step), the wavemaker
-  // (one clock for every group) and profiling keep the three calls in order
-  if (G < 2 || c->opt.integrator == SBI_IF_RK45 || c->wm_n > 0 || c->prof) {
+  auto three_calls = [&]() {
     int rc = sbi_set_state_all(c, eta_in, phi_in, 0);
     if (!rc) rc = sbi_step(c, dt, n);
     if (!rc) rc = sbi_get_state_all(c, eta_out, phi_out, 0);
     return rc;
+  };
+  // the adaptive pair (host-side tables per step), the wavemaker (one clock
+  // for every group) and profiling keep the three calls in order
+  if (c->opt.integrator == SBI_IF_RK45 || c->wm_n > 0 || c->prof) return three_calls();
+  // the schedule is chosen (and the whole-batch graph captured) first
+  if (n > 0) {
+    GraphEntry* ge_all = nullptr;
+    const int rc = get_step_graph(c, dt, &ge_all);
+    if (rc) return rc;
+  } else if (c->units.empty()) {
+    bool oom = false;
+    plan_step_units(c, dt, &oom);
+    if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
   }
+  const std::vector<Unit> units = c->units;
+  const size_t U = units.size();
+  if (U < 2) return three_calls();
   const std::vector<size_t> off = member_offsets(c);
   // everything that allocates, plans, tunes or synchronizes comes first
-  std::vector<GraphEntry*> ges(G, nullptr);
-  std::vector<std::vector<Pass>> entry(G);
-  for (size_t gi = 0; gi < G; ++gi) {
-    Group& g = c->groups[gi];
+  std::vector<GraphEntry*> ges(U, nullptr);
+  std::vector<std::vector<Pass>> entry(U);
+  for (size_t ui = 0; ui < U; ++ui) {
+    const Unit& u = units[ui];
+    Group& g = c->groups[u.group];
     if (n > 0) {
-      const int rc = get_step_graph(c, dt, &ges[gi], SK_STEP, (int)gi);
+      const int rc = get_step_graph(c, dt, &ges[ui], SK_STEP, (int)ui);
       if (rc) return rc;
     }
     int rc = ensure_stage(c, g);
@@ -2739,19 +3077,21 @@ int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, do
     if (!g.stage64b) g.stage64b = (double*)dalloc(c, g.phys_elems() * g.n * 8);
     if (!g.stage64b) return fail(c, SBI_ENOMEM, "device allocation failed");
     Planner pl{c, g};
-    if (c->opt.set_state_dealias) pl.plan_project(entry[gi], false);
-    else entry[gi].push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
+    std::vector<Pass> ps;
+    if (c->opt.set_state_dealias) pl.plan_project(ps, false);
+    else ps.push_back(pl.plan_rk(RK_ENTRY, 0, 0.0, 1));
     if (pl.oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+    for (const Pass& p : ps) entry[ui].push_back(slice_pass(p, g, u.m0, u.m1));
   }
   int least = 0, greatest = 0;
   CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
-  while (c->pstreams.size() < G) {
+  while (c->pstreams.size() < U) {
     cudaStream_t s2;
     const int prio = std::min(least, greatest + (int)c->pstreams.size());
     CK(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio), "stream");
     c->pstreams.push_back(s2);
   }
-  while (c->pevents.size() < G + 1) {
+  while (c->pevents.size() < U + 1) {
     cudaEvent_t e2;
     CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "event");
     c->pevents.push_back(e2);
@@ -2759,61 +3099,70 @@ int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, do
   CK(cudaEventRecord(c->pevents[0], c->stream), "event");   // after the caller's earlier work
   const double* in[2] = {eta_in, phi_in};
   double* outp[2] = {eta_out, phi_out};
-  for (size_t gi = 0; gi < G; ++gi) {
-    Group& g = c->groups[gi];
-    cudaStream_t st = c->pstreams[gi];
+  // runs of members of a unit that are consecutive in the caller's buffers
+  auto for_runs = [&](const Unit& u, const Group& g, auto&& f) -> int {
+    for (int li = u.m0; li < u.m1;) {
+      int run = 1;
+      while (li + run < u.m1 && g.members[li + run] == g.members[li] + run) ++run;
+      const int rc = f(li, run);
+      if (rc) return rc;
+      li += run;
+    }
+    return SBI_OK;
+  };
+  for (size_t ui = 0; ui < U; ++ui) {
+    const Unit& u = units[ui];
+    Group& g = c->groups[u.group];
+    cudaStream_t st = c->pstreams[ui];
     const size_t np = g.phys_elems();
+    const size_t first = (size_t)u.m0 * np, cnt = (size_t)(u.m1 - u.m0) * np;
     double* stage[2] = {g.stage64, g.stage64b};
-    double* state[2] = {g.eta0, g.phi0};
+    char* state[2] = {reinterpret_cast<char*>(g.eta0), reinterpret_cast<char*>(g.phi0)};
     CK(cudaStreamWaitEvent(st, c->pevents[0], 0), "wait");
     for (int q = 0; q < 2; ++q) {
-      for (int li = 0; li < g.n;) {   // one copy per run of consecutive members
-        int run = 1;
-        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+      int rc = for_runs(u, g, [&](int li, int run) -> int {
         CK(cudaMemcpyAsync(stage[q] + (size_t)li * np, in[q] + off[g.members[li]], np * 8 * run,
                            cudaMemcpyDefault, st), "copy state");
-        li += run;
-      }
-      const cudaError_t e = !c->state_ds ? state_convert<double>(stage[q], state[q], (long long)(np * g.n), false, st)
-                                         : state_convert<float>(stage[q], state[q], (long long)(np * g.n), false, st);
+        return SBI_OK;
+      });
+      if (rc) return rc;
+      void* to = state[q] + first * 8;   // 8 bytes per stored value
+      const cudaError_t e = !c->state_ds ? state_convert<double>(stage[q] + first, to, (long long)cnt, false, st)
+                                         : state_convert<float>(stage[q] + first, to, (long long)cnt, false, st);
       CK(e, "state conversion");
     }
-    int rc = run_passes(c, entry[gi], st);
+    int rc = run_passes(c, entry[ui], st);
     if (rc) return rc;
-    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(ges[gi]->exec, st), "graph launch");
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(ges[ui]->exec, st), "graph launch");
     for (int q = 0; q < 2; ++q) {
-      const cudaError_t e = !c->state_ds ? state_convert<double>(state[q], stage[q], (long long)(np * g.n), true, st)
-                                         : state_convert<float>(state[q], stage[q], (long long)(np * g.n), true, st);
+      const void* from = state[q] + first * 8;
+      const cudaError_t e = !c->state_ds ? state_convert<double>(from, stage[q] + first, (long long)cnt, true, st)
+                                         : state_convert<float>(from, stage[q] + first, (long long)cnt, true, st);
       CK(e, "state conversion");
     }
   }
-  // the downloads are queued after every group's work: a copy into pageable
-  // memory returns only when it is done and would hold back the next group
-  for (size_t gi = 0; gi < G; ++gi) {
-    Group& g = c->groups[gi];
-    cudaStream_t st = c->pstreams[gi];
+  // the downloads are queued after every unit's work: a copy into pageable
+  // memory returns only when it is done and would hold back the next unit
+  for (size_t ui = 0; ui < U; ++ui) {
+    const Unit& u = units[ui];
+    Group& g = c->groups[u.group];
+    cudaStream_t st = c->pstreams[ui];
     const size_t np = g.phys_elems();
     double* stage[2] = {g.stage64, g.stage64b};
     for (int q = 0; q < 2; ++q) {
-      for (int li = 0; li < g.n;) {
-        int run = 1;
-        while (li + run < g.n && g.members[li + run] == g.members[li] + run) ++run;
+      const int rc = for_runs(u, g, [&](int li, int run) -> int {
         CK(cudaMemcpyAsync(outp[q] + off[g.members[li]], stage[q] + (size_t)li * np, np * 8 * run,
                            cudaMemcpyDefault, st), "copy state");
-        li += run;
-      }
+        return SBI_OK;
+      });
+      if (rc) return rc;
     }
-    CK(cudaEventRecord(c->pevents[gi + 1], st), "event");
-    CK(cudaStreamWaitEvent(c->stream, c->pevents[gi + 1], 0), "wait");
+    CK(cudaEventRecord(c->pevents[ui + 1], st), "event");
+    CK(cudaStreamWaitEvent(c->stream, c->pevents[ui + 1], 0), "wait");
   }
   for (int i = 0; i < n; ++i) c->t_host += dt;
   CK(cudaStreamSynchronize(c->stream), "step_streamed");
-  if (c->opt.check_finite && n > 0) {
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
-    CK(cudaStreamSynchronize(c->stream), "step_streamed");
-    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
-  }
+  if (c->opt.check_finite && n > 0) return check_flags(c, "step_streamed");
   return SBI_OK;
 }
 
@@ -2883,12 +3232,7 @@ int sbi_step_adaptive(sbi_ctx* c, double t_end, double tol, double* h_inout, int
   *h_inout = h;
   if (accepted) *accepted = acc;
   if (rejected) *rejected = rej;
-  if (c->opt.check_finite) {
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
-    CK(cudaStreamSynchronize(c->stream), "step");
-    if (flag) return fail(c, SBI_ENONFINITE, "the state became non-finite");
-  }
+  if (c->opt.check_finite) return check_flags(c, "step");
   return SBI_OK;
 }
 
@@ -3101,10 +3445,25 @@ int sbi_autotune_report(const sbi_ctx* cc, char* buf, size_t cap, size_t* needed
   for (const auto& key : cc->tune_order) {
     const auto& t = cc->tuned.at(key);
     char line[96];
-    snprintf(line, sizeof(line), ": %s %d/%d %.4f ms\n", key.rfind("row", 0) == 0 ? "rpc" : "cpb",
-             t.choice, t.deflt, t.ms);
+    const bool row = key.rfind("row", 0) == 0;
+    // column choices: "s" marks the staged form (inputs by bulk copies)
+    snprintf(line, sizeof(line), ": %s %d%s/%d%s %.4f ms\n", row ? "rpc" : "cpb",
+             row ? t.choice : t.choice % kStagedTag, (!row && t.choice >= kStagedTag) ? "s" : "",
+             row ? t.deflt : t.deflt % kStagedTag, (!row && t.deflt >= kStagedTag) ? "s" : "", t.ms);
     out += key + line;
   }
+  *needed = out.size();
+  if (cap > 0) {
+    const size_t n = out.size() < cap - 1 ? out.size() : cap - 1;
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return SBI_OK;
+}
+
+int sbi_schedule_report(const sbi_ctx* cc, char* buf, size_t cap, size_t* needed) {
+  if (!cc || !needed || (cap > 0 && !buf)) return SBI_EINVAL;
+  const std::string& out = cc->sched_report;
   *needed = out.size();
   if (cap > 0) {
     const size_t n = out.size() < cap - 1 ? out.size() : cap - 1;

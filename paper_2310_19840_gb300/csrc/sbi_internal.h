@@ -67,7 +67,8 @@ struct BufRef {
 struct RowParams {
   int rpc;              // rows per block (runtime, <= the kernel's maximum)
   int nops;
-  int rows_total;       // members * ny
+  int row_begin;        // first row of this launch (a member range starts at member * ny)
+  int rows_total;       // end of the launch's rows: members * ny for the whole group
   int ny;
   int W;
   int nslots;
@@ -109,13 +110,16 @@ struct ColParams {
   int nin, nterms, nouts, nacc;
   int cpb;                  // columns per block (0: the size's default; see col_cpb_ok)
   int W, ny, nx;
-  int cols_total;           // members * W
+  int col_begin;            // first column of this launch (a member range starts at member * W)
+  int cols_total;           // end of the launch's columns: members * W for the whole group
   int member0;
   const int* active;
   double two_pi_over_Lx, two_pi_over_Ly, h0;
   int kx_keep, ky_keep;     // keep m < kx_keep and |n| < ky_keep
   double filt_kf, filt_beta2;
   double* norm_out;         // optional per-member FP64 partial norms of accumulator 0 (nullptr: off)
+  int staged;               // 1: inputs staged in shared memory by bulk copies (sizes >= 32)
+  int* err_flag;            // set to 1 when a bounded wait of the staged form gave up
   int npass;                // mixed buffers added unchanged to output 0 after its inverse FFT
   BufRef pass[8];
   int term_begin[kMaxColBufs + 1];   // terms sorted by input
@@ -155,7 +159,8 @@ struct RkParams {
   int mode;             // RkMode
   int stage;            // 1..4 for RK_STAGE
   int tail;             // 1: write the next stage's working copies (eta_w, mixed eta^, phi^)
-  int rows_total, ny, W;
+  int row_begin;        // first row of this launch (a member range starts at member * ny)
+  int rows_total, ny, W;  // rows_total: end of the launch's rows
   double dt;
   int state64;          // FP32 path only: the state and sums are FP64 (else double-single)
   RkScalar dt6, cdt;    // RK_STAGE: dt/6 (stage 4 update) and the stage's offset c dt
@@ -191,5 +196,7 @@ template <typename T> int row_rpc(int nx, int W, int nslots);
 // per block and threads per column of a column pass (0 for an unknown size)
 template <typename T> int row_tpr(int nx);
 template <typename T> int col_geometry(int ny, int* tpc);
+// whether columns of ny points can take the staged (bulk-copy) form
+template <typename T> bool col_stageable(int ny);
 
 }  // namespace sbi

@@ -44,7 +44,8 @@ class sbi_options(C.Structure):
                 ("set_state_dealias", C.c_int),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("autotune", C.c_int), ("integrator", C.c_int), ("diagnostic", C.c_int),
-                ("state_fp64", C.c_int)]
+                ("state_fp64", C.c_int), ("schedule", C.c_int),
+                ("col_staging", C.c_int)]
 
 
 EXPORTS = {
@@ -83,6 +84,7 @@ EXPORTS = {
     "sbi_step_adaptive": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sbi_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "sbi_schedule_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
@@ -175,7 +177,8 @@ class Context:
     def __init__(self, grids, gravity, depths=None, *, h0=math.nan, order=7, alias_frac=0.5,
                  precision=SBI_FP32, adapt_tol=0.0, filt_beta1=0.0, filt_beta2=0.0, k_ref=1.0,
                  sponge_w=None, sponge_nu=0.0, stream=None, check_finite=1, set_state_dealias=1,
-                 autotune=1, integrator=SBI_RK4, diagnostic=SBI_DIAG_ESBI, state_fp64=0):
+                 autotune=1, integrator=SBI_RK4, diagnostic=SBI_DIAG_ESBI, state_fp64=0,
+                 schedule=0, col_staging=0):
         self.lib = load()
         if isinstance(grids, tuple):
             grids = [grids]
@@ -186,7 +189,8 @@ class Context:
                               k_ref=k_ref, sponge_nu=sponge_nu, check_finite=check_finite,
                               set_state_dealias=set_state_dealias, autotune=autotune,
                               integrator=integrator, diagnostic=diagnostic,
-                              state_fp64=state_fp64)
+                              state_fp64=state_fp64, schedule=schedule,
+                              col_staging=col_staging)
         keep = []
         if sponge_w is not None:
             w = np.ascontiguousarray(sponge_w, dtype=np.float64).ravel()
@@ -393,6 +397,15 @@ class Context:
         self._check(self.lib.sbi_autotune_report(self.ctx, None, 0, C.byref(need)))
         buf = C.create_string_buffer(need.value + 1)
         self._check(self.lib.sbi_autotune_report(self.ctx, buf, len(buf), C.byref(need)))
+        return buf.value.decode()
+
+    def schedule_report(self):
+        """Lines of sbi_schedule_report: the step schedules tried, their times
+        and the one chosen (empty before the first step)."""
+        need = C.c_size_t()
+        self._check(self.lib.sbi_schedule_report(self.ctx, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value + 1)
+        self._check(self.lib.sbi_schedule_report(self.ctx, buf, len(buf), C.byref(need)))
         return buf.value.decode()
 
     def step_transforms(self, family=-1):

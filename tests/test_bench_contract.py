@@ -54,3 +54,23 @@ def test_gb300_arm_line():
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
+    assert d["schedule"]["chosen"]
+
+
+def test_schedule_summary_parses_the_report():
+    # the step-schedule report of the library, as bench.py summarises it
+    sys.path.insert(0, ROOT)
+    import bench
+    rep = ("default 6.0500 ms per step: split total/3 [concurrent] 3 units: 256x256[0:64] "
+           "512x512[0:16] 512x512[16:32]\n"
+           "chosen 5.9000 ms per step: split total/6 [concurrent] 6 units: 256x256[0:32] "
+           "256x256[32:64] 512x512[0:8] 512x512[8:16] 512x512[16:24] 512x512[24:32]\n"
+           "tried 6.4000 ms per step: serial groups [serial] 2 units: 256x256[0:64] 512x512[0:32]\n"
+           "default split total/3 [concurrent] 3 units: 256x256[0:64] 512x512[0:16] 512x512[16:32]\n")
+    s = bench.schedule_summary(rep)
+    assert s["chosen"] == "split total/6" and s["candidates"][2]["mode"] == "serial"
+    assert [c["role"] for c in s["candidates"]] == ["default", "chosen", "tried", "default"]
+    assert s["candidates"][1]["ms_per_step"] == 5.9 and len(s["candidates"][1]["units"]) == 6
+    assert s["candidates"][3]["ms_per_step"] is None
+    only = bench.schedule_summary("default split total/3 [concurrent] 1 units: 256x1[0:1]\n")
+    assert only["chosen"] == "split total/3" and only["candidates"][0]["units"] == ["256x1[0:1]"]

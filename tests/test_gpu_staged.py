@@ -1,0 +1,64 @@
+"""Column passes whose inputs arrive by bulk copies (TMA) against the direct form.
+
+The staged form copies each column's input into shared memory with
+cp.async.bulk, the next input in flight while the current one is transformed,
+and then runs the same transforms and sums as the direct form, which loads the
+input straight into registers.  The two must agree bit for bit: V after one
+evaluation and the state after two RK4 steps, for every column length the
+staged form takes (32 to 2048 points, plain and split transforms), in both
+precisions, untuned and with the block shapes the autotuner picks.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# one member per column length; a variable bottom on two of them
+SPECS = [(64, 32, 6.0, 3.0), (32, 64, 3.0, 6.0), (64, 128, 6.0, 12.0), (32, 256, 3.0, 24.0),
+         (16, 512, 2.0, 48.0), (16, 1024, 2.0, 96.0), (16, 2048, 2.0, 192.0), (64, 8, 6.0, 0.75)]
+H0 = 0.8
+
+
+@pytest.fixture(scope="module")
+def sbi():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2310_19840_gb300 import sbi as s
+    return s
+
+
+def run(sbi, prec, staging, autotune):
+    depth = [H0 - W.random_field(nx, ny, 30 + i, amplitude=0.05) if i in (1, 4) else None
+             for i, (nx, ny, _, _) in enumerate(SPECS)]
+    ctx = sbi.Context(SPECS, 9.81, depth, h0=H0, precision=prec, autotune=autotune,
+                      col_staging=staging, filt_beta1=6.0, filt_beta2=20.0, k_ref=1.0)
+    for i, (nx, ny, _, _) in enumerate(SPECS):
+        ctx.set_state(i, W.random_field(nx, ny, 50 + i, amplitude=0.03),
+                      W.random_field(nx, ny, 60 + i, amplitude=0.2))
+    V = [ctx.vertical_velocity(i) for i in range(len(SPECS))]
+    ctx.step(0.005, 2)
+    st = [ctx.get_state(i) for i in range(len(SPECS))]
+    rep = ctx.autotune_report()
+    ctx.close()
+    return V, st, rep
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_staged_columns_give_the_same_bits(sbi, prec):
+    V0, st0, _ = run(sbi, prec, -1, 0)
+    for staging, autotune in ((1, 0), (1, 1), (0, 1)):
+        V, st, rep = run(sbi, prec, staging, autotune)
+        for i in range(len(SPECS)):
+            assert np.array_equal(V[i], V0[i]), (staging, autotune, i)
+            assert np.array_equal(st[i][0], st0[i][0]) and np.array_equal(st[i][1], st0[i][1]), \
+                (staging, autotune, i)
+        cols = [ln for ln in rep.splitlines() if ln.startswith("col ")]
+        if staging == 1 and autotune:
+            # every column pass of a stageable length took the staged form
+            for ln in cols:
+                ny = int(ln.split()[1].split("=")[1])
+                assert (" cpb " in ln) and ((ln.split(": cpb ")[1].split("/")[0].endswith("s")) == (ny >= 32)), ln
+        if staging == 0 and autotune:
+            assert cols and all(" cpb " in ln for ln in cols)
