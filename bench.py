@@ -67,6 +67,12 @@ def parse():
                     help="with --accuracy: steps instead of the workload's run length")
     ap.add_argument("--state-fp64", action="store_true",
                     help="FP32 path with the RK4 state and sums in FP64 instead of double-single")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="step schedule (sbi_options.schedule): 0 chosen by timing, B > 0 "
+                         "units of at most total/B points, -1 serial groups")
+    ap.add_argument("--col-staging", type=int, default=0, choices=[-1, 0, 1],
+                    help="column-pass inputs (sbi_options.col_staging): 0 chosen by timing, "
+                         "1 bulk copies into shared memory, -1 direct loads")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU time of each oracle baseline sample (1 process and all cores)")
     return ap.parse_args()
@@ -585,8 +591,9 @@ def main():
         if rank == 0:
             print(json.dumps(accuracy_run(args, sbi, torch, stream, wl, integ, diag)), flush=True)
         return 0
+    knobs = {"schedule": args.schedule, "col_staging": args.col_staging}
     ctx = make_context(sbi, wl, prec, stream.cuda_stream, integrator=integ, diagnostic=diag,
-                       state_fp64=int(args.state_fp64))
+                       state_fp64=int(args.state_fp64), **knobs)
     for i, m in enumerate(wl.members):
         ctx.set_state(i, m.eta, m.phi)
     if args.compare_diagnostics:
@@ -691,7 +698,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         ctx_e = make_context(sbi, wl, prec, stream.cuda_stream, set_state_dealias=0,
-                             integrator=integ, diagnostic=diag)
+                             integrator=integ, diagnostic=diag, **knobs)
         # every member's eta and phi~, concatenated in member order, in pinned memory
         eta_h = torch.from_numpy(np.concatenate([np.ravel(m.eta) for m in wl.members])).pin_memory()
         phi_h = torch.from_numpy(np.concatenate([np.ravel(m.phi) for m in wl.members])).pin_memory()
@@ -741,6 +748,7 @@ def main():
             "transforms_per_point_step": ctx.step_transforms(-1) / wl.points,
             "autotune": autotune_summary(ctx.autotune_report()),
             "schedule": schedule_summary(ctx.schedule_report()),
+            "knobs": knobs,
             "model_step_GBps": step_model_gbps, "fused_step_GBps": step_gbps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_arm, "error": err}
     if gathered:
