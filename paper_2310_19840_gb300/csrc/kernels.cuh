@@ -28,10 +28,7 @@ namespace sbi {
 // threads.  In FP32 the blocks are compiled for two resident blocks per SM
 // (64 registers per thread, no spills): measured against 16 elements per
 // thread this doubles the warps per SM and runs the row passes faster at
-// every size.  FP32 rows of 4096 points (256 threads each) take blocks of up
-// to 1024 threads, one resident per SM (the same 64 registers and 32 warps):
-// four rows per block make the transposed mixed I/O move runs of 32 bytes
-// (one sector) per mode instead of 16.
+// every size.
 template <int NX>
 struct RowCfg {
   static constexpr int n = NX / 2;                         // packed complex length
@@ -39,14 +36,11 @@ struct RowCfg {
   static constexpr int TPR = n / R;                        // threads per row
   static constexpr bool WARP = TPR <= 32;
   static constexpr int RPC_MAX = cmin(256, WARP ? cmax(16, 512 / TPR) : cmax(1, 512 / TPR));
+  static constexpr int MAX_THREADS = TPR * RPC_MAX;
   static constexpr int FBUF = fft_scratch_len<n, R>();    // FFT scratch per row
   template <typename T>
-  static constexpr int rpc_max() { return (sizeof(T) == 4 && TPR >= 256) ? 1024 / TPR : RPC_MAX; }
-  template <typename T>
-  static constexpr int max_threads() { return TPR * rpc_max<T>(); }
-  template <typename T>
   // 0: no minimum, the register count is left to the compiler
-  static constexpr int min_blocks() { return sizeof(T) == 4 ? (max_threads<T>() > 512 ? 1 : 2) : 0; }
+  static constexpr int min_blocks() { return sizeof(T) == 4 ? 2 : 0; }
 };
 
 // shared memory of a row block: per row the FFT scratch (row stride fbs), the
@@ -354,7 +348,7 @@ __device__ __forceinline__ T ipow(T v, int p) {
 }
 
 template <typename T, int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::template max_threads<T>(), RowCfg<NX>::template min_blocks<T>())
+__global__ void __launch_bounds__(RowCfg<NX>::MAX_THREADS, RowCfg<NX>::template min_blocks<T>())
 k_row(const __grid_constant__ RowParams p) {
   using V = cx<T>;
   using C = RowCfg<NX>;
@@ -1134,7 +1128,7 @@ cudaError_t prepare_ny() {
 template <typename T, int NX>
 cudaError_t launch_row_n(const RowParams& p, cudaStream_t st) {
   using C = RowCfg<NX>;
-  if (p.rpc < 1 || p.rpc > C::template rpc_max<T>() || p.row_begin < 0 || p.row_begin >= p.rows_total)
+  if (p.rpc < 1 || p.rpc > C::RPC_MAX || p.row_begin < 0 || p.row_begin >= p.rows_total)
     return cudaErrorInvalidValue;
   const int blocks = (p.rows_total - p.row_begin + p.rpc - 1) / p.rpc;
   RowParams q = p;
@@ -1245,7 +1239,7 @@ int row_rpc_impl(int nx, int W, int nslots) {
   switch (nx) {
 #define SBI_CASE(N)                                                         \
   case N:                                                                   \
-    maxr = RowCfg<N>::template rpc_max<T>();                                \
+    maxr = RowCfg<N>::RPC_MAX;                                              \
     per = row_smem_bound<T, N>(W, nslots);                                  \
     if (RowCfg<N>::template min_blocks<T>() == 2) budget = 113 * 1024;      \
     break;
