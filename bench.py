@@ -227,10 +227,17 @@ def measured_peaks():
         return None
 
 
+# the sources of the row, column and RK kernels whose DRAM traffic the
+# committed ncu summary records (host code and the other kernels live in
+# sbi_host.cu and sbi_noalloc.cu)
+KERNEL_SOURCES = ("bank_model.h", "fft.cuh", "kernels.cuh", "sbi_internal.h", "inst_col_f32.cu",
+                  "inst_col_f64.cu", "inst_row_f32.cu", "inst_row_f64.cu")
+
+
 def source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2310_19840_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
