@@ -168,7 +168,8 @@ struct GraphEntry {
   double dt;
   bool prof;
   int kind = 0;                      // StepKind
-  int group = -1;                    // -1: every unit of the schedule; else that unit alone
+  int group = -1;                    // -1: every unit of the schedule; else the members
+  int m0 = 0, m1 = 0;                //   [m0, m1) of that group alone (the streamed step)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
@@ -206,6 +207,7 @@ struct sbi_ctx {
   bool serial = false;
   bool sched_done = false;
   std::string sched_report;
+  int stream_k = 0;   // streamed step: each schedule unit cut into stream_k member ranges (0: not chosen)
   std::vector<void*> allocs;
   void* tw = nullptr;
   void* wgt = nullptr;  // shared sponge weight (working precision) or null
@@ -1997,16 +1999,21 @@ void free_graphs(sbi_ctx* c) {
   c->graphs.clear();
 }
 
-// Capture the step graph of the current schedule (unit < 0: every unit; else
-// that unit alone, for the streamed step).
-int build_step_graph(sbi_ctx* c, double dt, int kind, int unit, GraphEntry& ge) {
+// Capture the step graph of the current schedule (only == nullptr: every
+// unit), or of one member range alone (the streamed step).
+int build_step_graph(sbi_ctx* c, double dt, int kind, const Unit* only, GraphEntry& ge) {
   bool oom = false;
-  std::vector<std::vector<Pass>> gps = plan_step_units(c, dt, &oom, kind);
-  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
-  if (unit >= 0) {   // one unit's passes alone (the streamed step)
-    std::vector<Pass> one = gps.at((size_t)unit);
-    gps.assign(1, one);
+  std::vector<std::vector<Pass>> gps;
+  if (only) {
+    const std::vector<std::vector<Pass>> all = plan_step_groups(c, dt, &oom, kind);
+    std::vector<Pass> one;
+    for (const Pass& p : all.at((size_t)only->group))
+      one.push_back(slice_pass(p, c->groups[only->group], only->m0, only->m1));
+    gps.push_back(std::move(one));
+  } else {
+    gps = plan_step_units(c, dt, &oom, kind);
   }
+  if (oom) return fail(c, SBI_ENOMEM, "device allocation failed while planning the step");
   CK(cudaStreamSynchronize(c->cap), "sync before capture");
   CK(cudaStreamSynchronize(c->stream), "sync before capture");
   // block shapes are tuned (or taken from earlier tuning) before capture
@@ -2020,7 +2027,9 @@ int build_step_graph(sbi_ctx* c, double dt, int kind, int unit, GraphEntry& ge) 
   ge.dt = dt;
   ge.prof = c->prof;
   ge.kind = kind;
-  ge.group = unit;
+  ge.group = only ? only->group : -1;
+  ge.m0 = only ? only->m0 : 0;
+  ge.m1 = only ? only->m1 : 0;
   if (c->prof) {   // the profiled graph owns one event pair per pass
     for (size_t gi = 0; gi < gps.size(); ++gi)
       for (size_t i = 0; i < gps[gi].size(); ++i) {
@@ -2066,7 +2075,7 @@ int build_step_graph(sbi_ctx* c, double dt, int kind, int unit, GraphEntry& ge) 
     }
   }
   // the simulation time of the next step (read by the wavemaker passes)
-  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP && unit < 0) {
+  if (rc == SBI_OK && c->wm_n > 0 && kind == SK_STEP && !only) {
     k_advance_time<<<1, 32, 0, c->cap>>>(c->d_time, dt);
     const cudaError_t el = cudaGetLastError();
     if (el != cudaSuccess) rc = cuda_fail(c, el, "kernel launch");
@@ -2221,7 +2230,7 @@ int choose_schedule(sbi_ctx* c, double dt, int kind) {
     c->units = cands[i].units;
     c->serial = cands[i].serial;
     GraphEntry ge;
-    rc = build_step_graph(c, dt, kind, -1, ge);
+    rc = build_step_graph(c, dt, kind, nullptr, ge);
     if (rc) break;
     auto replay = [&]() { return cudaGraphLaunch(ge.exec, c->cap); };
     cudaError_t e = replay();   // warm-up
@@ -2255,7 +2264,7 @@ int choose_schedule(sbi_ctx* c, double dt, int kind) {
   return SBI_OK;
 }
 
-int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, int unit = -1) {
+int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, const Unit* only = nullptr) {
   if (!c->sched_done) {
     const int rc = choose_schedule(c, dt, kind);
     if (rc) return rc;
@@ -2263,9 +2272,13 @@ int get_step_graph(sbi_ctx* c, double dt, GraphEntry** out, int kind = SK_STEP, 
     if (c->sched_done) free_graphs(c);
   }
   for (auto& ge : c->graphs)
-    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind && ge.group == unit) { *out = &ge; return SBI_OK; }
+    if (ge.dt == dt && ge.prof == c->prof && ge.kind == kind && ge.group == (only ? only->group : -1) &&
+        (!only || (ge.m0 == only->m0 && ge.m1 == only->m1))) {
+      *out = &ge;
+      return SBI_OK;
+    }
   GraphEntry ge;
-  const int rc = build_step_graph(c, dt, kind, unit, ge);
+  const int rc = build_step_graph(c, dt, kind, only, ge);
   if (rc) return rc;
   c->graphs.push_back(ge);
   *out = &c->graphs.back();
@@ -3026,41 +3039,23 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
   return SBI_OK;
 }
 
-// Upload, n steps and download of every member's state, pipelined per unit of
-// the step schedule: each unit (a member range of one group) runs on its own
-// stream (priority falling with the unit index), so the copies of one unit
-// overlap the steps of the others.  Every launch and its arguments are those
-// of sbi_set_state_all + sbi_step + sbi_get_state_all restricted to the
-// unit's members (same passes, same block shapes), so the result is the same
-// bits.
-int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, double dt, int n,
-                      double* eta_out, double* phi_out) {
-  if (!c) return SBI_EINVAL;
-  if (!eta_in || !phi_in || !eta_out || !phi_out) return fail(c, SBI_EINVAL, "state buffers must not be NULL");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
-  if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
-  auto three_calls = [&]() {
-    int rc = sbi_set_state_all(c, eta_in, phi_in, 0);
-    if (!rc) rc = sbi_step(c, dt, n);
-    if (!rc) rc = sbi_get_state_all(c, eta_out, phi_out, 0);
-    return rc;
-  };
-  // the adaptive pair (host-side tables per step), the wavemaker (one clock
-  // for every group) and profiling keep the three calls in order
-  if (c->opt.integrator == SBI_IF_RK45 || c->wm_n > 0 || c->prof) return three_calls();
-  // the schedule is chosen (and the whole-batch graph captured) first
-  if (n > 0) {
-    GraphEntry* ge_all = nullptr;
-    const int rc = get_step_graph(c, dt, &ge_all);
-    if (rc) return rc;
-  } else if (c->units.empty()) {
-    bool oom = false;
-    plan_step_units(c, dt, &oom);
-    if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+// The schedule's units, each cut into k nearly equal member ranges (at most one
+// member each).
+std::vector<Unit> split_units(const std::vector<Unit>& units, int k) {
+  std::vector<Unit> out;
+  for (const Unit& u : units) {
+    const int n = u.m1 - u.m0, kk = std::max(1, std::min(k, n));
+    for (int q = 0; q < kk; ++q)
+      out.push_back(Unit{u.group, u.m0 + (int)((long long)q * n / kk), u.m0 + (int)((long long)(q + 1) * n / kk)});
   }
-  const std::vector<Unit> units = c->units;
+  return out;
+}
+
+// Enqueue the upload, n steps and download of every member's state, one
+// stream per unit (no synchronisation; the caller's stream waits for all).
+int streamed_run(sbi_ctx* c, const double* eta_in, const double* phi_in, double dt, int n, double* eta_out,
+                 double* phi_out, const std::vector<Unit>& units) {
   const size_t U = units.size();
-  if (U < 2) return three_calls();
   const std::vector<size_t> off = member_offsets(c);
   // everything that allocates, plans, tunes or synchronizes comes first
   std::vector<GraphEntry*> ges(U, nullptr);
@@ -3069,7 +3064,7 @@ int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, do
     const Unit& u = units[ui];
     Group& g = c->groups[u.group];
     if (n > 0) {
-      const int rc = get_step_graph(c, dt, &ges[ui], SK_STEP, (int)ui);
+      const int rc = get_step_graph(c, dt, &ges[ui], SK_STEP, &units[ui]);
       if (rc) return rc;
     }
     int rc = ensure_stage(c, g);
@@ -3160,6 +3155,101 @@ int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, do
     CK(cudaEventRecord(c->pevents[ui + 1], st), "event");
     CK(cudaStreamWaitEvent(c->stream, c->pevents[ui + 1], 0), "wait");
   }
+  return SBI_OK;
+}
+
+// do [a, a + n) and [b, b + m) doubles overlap
+bool overlaps(const double* a, size_t n, const double* b, size_t m) {
+  const uintptr_t a0 = (uintptr_t)a, a1 = a0 + n * 8, b0 = (uintptr_t)b, b1 = b0 + m * 8;
+  return a0 < b1 && b0 < a1;
+}
+
+// Upload, n steps and download of every member's state, pipelined per unit:
+// each unit (a member range of one group) runs on its own stream (priority
+// falling with the unit index), so the copies of one unit overlap the steps
+// of the others.  The units are the step schedule's, each cut into k member
+// ranges; smaller units start computing and finish copying out sooner, more
+// of them make smaller launches.  On the first call (with autotuning, n > 0
+// and outputs that overlap no input) k = 1, 2 and 3 are timed on whole
+// one-step calls (each writes the outputs, which the call itself then
+// overwrites) and the fastest is kept; k = 1 stays unless another is 3 %
+// faster.  Every launch and its arguments are those of sbi_set_state_all +
+// sbi_step + sbi_get_state_all restricted to a unit's members (same passes,
+// same block shapes), so the result is the same bits for every k.
+int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, double dt, int n,
+                      double* eta_out, double* phi_out) {
+  if (!c) return SBI_EINVAL;
+  if (!eta_in || !phi_in || !eta_out || !phi_out) return fail(c, SBI_EINVAL, "state buffers must not be NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SBI_EINVAL, "dt must be finite and > 0");
+  if (n < 0) return fail(c, SBI_EINVAL, "n must be >= 0");
+  auto three_calls = [&]() {
+    int rc = sbi_set_state_all(c, eta_in, phi_in, 0);
+    if (!rc) rc = sbi_step(c, dt, n);
+    if (!rc) rc = sbi_get_state_all(c, eta_out, phi_out, 0);
+    return rc;
+  };
+  // the adaptive pair (host-side tables per step), the wavemaker (one clock
+  // for every group) and profiling keep the three calls in order
+  if (c->opt.integrator == SBI_IF_RK45 || c->wm_n > 0 || c->prof) return three_calls();
+  // the schedule is chosen (and the whole-batch graph captured) first
+  if (n > 0) {
+    GraphEntry* ge_all = nullptr;
+    const int rc = get_step_graph(c, dt, &ge_all);
+    if (rc) return rc;
+  } else if (c->units.empty()) {
+    bool oom = false;
+    plan_step_units(c, dt, &oom);
+    if (oom) return fail(c, SBI_ENOMEM, "device allocation failed");
+  }
+  const std::vector<Unit> units = c->units;
+  if (units.size() < 2) return three_calls();
+  if (c->stream_k == 0) {
+    size_t total = 0;
+    for (const auto& g : c->groups) total += g.phys_elems() * (size_t)g.n;
+    const bool alias = overlaps(eta_in, total, eta_out, total) || overlaps(eta_in, total, phi_out, total) ||
+                       overlaps(phi_in, total, eta_out, total) || overlaps(phi_in, total, phi_out, total);
+    std::vector<int> ks = {1};
+    for (int k : {2, 3})
+      if (split_units(units, k).size() > split_units(units, ks.back()).size()) ks.push_back(k);
+    if (!c->opt.autotune || n == 0 || alias || ks.size() < 2) {
+      if (n > 0 || !c->opt.autotune) c->stream_k = 1;
+    } else {
+      if (!c->tune_ev[0]) {
+        CK(cudaEventCreate(&c->tune_ev[0]), "event");
+        CK(cudaEventCreate(&c->tune_ev[1]), "event");
+      }
+      std::vector<double> ms(ks.size(), -1.0);
+      for (size_t i = 0; i < ks.size(); ++i) {
+        const std::vector<Unit> su = split_units(units, ks[i]);
+        int rc = streamed_run(c, eta_in, phi_in, dt, 1, eta_out, phi_out, su);   // warm-up
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(c->stream), "streamed timing");
+        CK(cudaEventRecord(c->tune_ev[0], c->stream), "event");
+        rc = streamed_run(c, eta_in, phi_in, dt, 1, eta_out, phi_out, su);
+        if (rc) return rc;
+        CK(cudaEventRecord(c->tune_ev[1], c->stream), "event");
+        CK(cudaEventSynchronize(c->tune_ev[1]), "streamed timing");
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->tune_ev[0], c->tune_ev[1]), "event time");
+        ms[i] = t;
+      }
+      size_t best = 0;
+      for (size_t i = 1; i < ks.size(); ++i)
+        if (ms[i] < ms[best]) best = i;
+      if (best != 0 && !(ms[best] < 0.97 * ms[0])) best = 0;
+      c->stream_k = ks[best];
+      for (size_t i = 0; i < ks.size(); ++i) {
+        const std::vector<Unit> su = split_units(units, ks[i]);
+        char t[96];
+        snprintf(t, sizeof(t), "%s %.4f ms per step: ", i == best ? "streamed-chosen" : "streamed-tried", ms[i]);
+        c->sched_report += std::string(t) +
+                           sched_desc(c, Sched{su, false, "streamed split x" + std::to_string(ks[i])}) + "\n";
+      }
+    }
+  }
+  const std::vector<Unit> su = split_units(units, std::max(1, c->stream_k));
+  const int rc = streamed_run(c, eta_in, phi_in, dt, n, eta_out, phi_out, su);
+  if (rc) return rc;
   for (int i = 0; i < n; ++i) c->t_host += dt;
   CK(cudaStreamSynchronize(c->stream), "step_streamed");
   if (c->opt.check_finite && n > 0) return check_flags(c, "step_streamed");

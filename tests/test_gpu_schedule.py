@@ -98,3 +98,29 @@ def test_untimed_default_and_bad_schedule(sbi):
     assert rep.startswith("default split total/3"), rep
     with pytest.raises(sbi.SbiError):
         make(sbi, 0, -2, 0)
+
+
+def test_streamed_split_is_timed_and_gives_the_same_bits(sbi):
+    # The streamed step cuts each schedule unit into k member ranges (k = 1, 2,
+    # 3 timed on the first call when the outputs overlap no input); every k
+    # gives the bits of the three calls.  An in-place call is not timed.
+    (e0, p0), _, _ = run(sbi, 0, 3, 0, False)
+    eta, phi = initial()
+    ctx = make(sbi, 0, 3, 1)
+    eo, po = np.empty_like(eta), np.empty_like(phi)
+    ctx.step_streamed(eta, phi, 0.01, 3, eo, po)
+    rep = ctx.schedule_report()
+    ks = [ln for ln in rep.splitlines() if ln.startswith("streamed-")]
+    assert sum(ln.startswith("streamed-chosen ") for ln in ks) == 1 and len(ks) >= 2, rep
+    assert np.array_equal(eo, e0) and np.array_equal(po, p0)
+    # later calls reuse the choice (no new report lines) and give the same bits
+    ctx.step_streamed(eta, phi, 0.01, 3, eo, po)
+    assert ctx.schedule_report() == rep
+    assert np.array_equal(eo, e0) and np.array_equal(po, p0)
+    ctx.close()
+    ctx = make(sbi, 0, 3, 1)
+    e, p = eta.copy(), phi.copy()
+    ctx.step_streamed(e, p, 0.01, 3, e, p)
+    assert not any(ln.startswith("streamed-") for ln in ctx.schedule_report().splitlines())
+    assert np.array_equal(e, e0) and np.array_equal(p, p0)
+    ctx.close()
