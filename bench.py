@@ -307,6 +307,17 @@ def schedule_summary(report):
     return out
 
 
+def streamed_split(report):
+    """The member-range splits the streamed step timed (the "streamed-" lines
+    of sbi_schedule_report): per candidate its units and ms per step, and the
+    number of units of the one kept."""
+    cands = [c for c in schedule_summary(report)["candidates"] if c["role"].startswith("streamed-")]
+    kept = [c for c in cands if c["role"] == "streamed-chosen"]
+    return {"candidates": [{"schedule": c["schedule"], "ms_per_step": c["ms_per_step"],
+                            "units": len(c["units"])} for c in cands],
+            "chosen_units": len(kept[0]["units"]) if kept else None}
+
+
 def make_context(sbi, wl, precision, stream, **extra):
     grids = [(m.nx, m.ny, m.Lx, m.Ly) for m in wl.members]
     depths = [(m.h0 - m.delta) if m.delta is not None else None for m in wl.members]
@@ -736,6 +747,7 @@ def main():
         e2e = {"value": job_points * ke / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ke,
                "api": "sbi_step_streamed(pinned host in, dt, 1, pinned host out)",
+               "streamed_split": streamed_split(ctx_e.schedule_report()),
                "three_calls": {"value": job_points * kc / tc, "steps": kc,
                                "api": "sbi_set_state_all(pinned host) + sbi_step(dt, 1) + "
                                       "sbi_get_state_all(pinned host)"}}

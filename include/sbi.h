@@ -229,22 +229,28 @@ int sbi_step(sbi_ctx* ctx, double dt, int n);
  * same result, bit for bit, as
  *   sbi_set_state_all(ctx, eta_in, phi_in, 0); sbi_step(ctx, dt, n);
  *   sbi_get_state_all(ctx, eta_out, phi_out, 0);
- * (Sec. 2.2 steps between the copies), with the copies of one member group
- * overlapping the steps of the others.  Each group runs on a stream of its
- * own: copy of its eta and phi~ in (copy engine, into a device staging
- * buffer), conversion, the entry pass of sbi_set_state_all, n replays of the
- * group's step graph, conversion out and copy out; the first group's stream
- * has the highest priority, so the groups finish one after another and the
- * last copies out overlap the remaining steps.  The paper has no counterpart
- * (it holds one problem's state on one device).
+ * (Sec. 2.2 steps between the copies), with the copies of one unit
+ * overlapping the steps of the others.  The units are those of the step
+ * schedule (member ranges of one group, see sbi_schedule_report), each cut
+ * into k member ranges.  Each unit runs on a stream of its own: copy of its
+ * eta and phi~ in (copy engine, into a device staging buffer), conversion,
+ * the entry pass of sbi_set_state_all, n replays of the unit's step graph,
+ * conversion out and copy out; the first unit's stream has the highest
+ * priority, so the units finish one after another and the last copies out
+ * overlap the remaining steps.  With opt.autotune = 1, the first call whose
+ * n > 0 and whose outputs overlap no input times k = 1, 2 and 3 on whole
+ * one-step calls (these write eta_out and phi_out, which the call then
+ * overwrites with its result) and keeps the fastest (k = 1 unless another is
+ * 3 % faster; sbi_schedule_report lists the "streamed-" times).  The paper
+ * has no counterpart (it holds one problem's state on one device).
  *   eta_in, phi_in    sum over members of nx*ny doubles each, member order as
  *                     in sbi_set_state_all; host (pinned memory for the
  *                     overlap; pageable memory works but its copies block) or
  *                     device memory.
  *   eta_out, phi_out  the same sizes, written after the n steps; they may be
- *                     eta_in, phi_in themselves.
+ *                     eta_in, phi_in themselves (k is then not timed).
  *   dt, n             as in sbi_step; n = 0 copies the entry state out.
- * Contexts with one member group, the adaptive pair (SBI_IF_RK45), a
+ * Contexts whose schedule has one unit, the adaptive pair (SBI_IF_RK45), a
  * wavemaker or profiling on run the three calls one after another.  Two
  * device staging buffers per group (the group's points x 8 bytes each) are
  * allocated on first use and kept.  Synchronizes the stream.  SBI_EINVAL for

@@ -74,3 +74,18 @@ def test_schedule_summary_parses_the_report():
     assert s["candidates"][3]["ms_per_step"] is None
     only = bench.schedule_summary("default split total/3 [concurrent] 1 units: 256x1[0:1]\n")
     assert only["chosen"] == "split total/3" and only["candidates"][0]["units"] == ["256x1[0:1]"]
+
+
+def test_streamed_split_summary():
+    sys.path.insert(0, ROOT)
+    import bench
+    rep = ("chosen 6.0300 ms per step: split total/3 [concurrent] 3 units: 256x256[0:64] "
+           "512x512[0:16] 512x512[16:32]\n"
+           "streamed-tried 7.6000 ms per step: streamed split x1 [concurrent] 3 units: 256x256[0:64] "
+           "512x512[0:16] 512x512[16:32]\n"
+           "streamed-chosen 7.2000 ms per step: streamed split x2 [concurrent] 6 units: 256x256[0:32] "
+           "256x256[32:64] 512x512[0:8] 512x512[8:16] 512x512[16:24] 512x512[24:32]\n")
+    s = bench.streamed_split(rep)
+    assert s["chosen_units"] == 6 and [c["units"] for c in s["candidates"]] == [3, 6]
+    assert bench.schedule_summary(rep)["chosen"] == "split total/3"
+    assert bench.streamed_split("")["chosen_units"] is None
