@@ -238,7 +238,7 @@ int sbi_step(sbi_ctx* ctx, double dt, int n);
  * conversion out and copy out; the first unit's stream has the highest
  * priority, so the units finish one after another and the last copies out
  * overlap the remaining steps.  With opt.autotune = 1, the first call whose
- * n > 0 and whose outputs overlap no input times k = 1, 2 and 3 on whole
+ * n > 0 and whose outputs overlap no input times k = 1, 2, 3, 4 and 6 on whole
  * one-step calls (these write eta_out and phi_out, which the call then
  * overwrites with its result) and keeps the fastest (k = 1 unless another is
  * 3 % faster; sbi_schedule_report lists the "streamed-" times).  The paper

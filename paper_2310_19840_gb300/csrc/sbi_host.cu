@@ -3170,7 +3170,7 @@ bool overlaps(const double* a, size_t n, const double* b, size_t m) {
 // of the others.  The units are the step schedule's, each cut into k member
 // ranges; smaller units start computing and finish copying out sooner, more
 // of them make smaller launches.  On the first call (with autotuning, n > 0
-// and outputs that overlap no input) k = 1, 2 and 3 are timed on whole
+// and outputs that overlap no input) k = 1, 2, 3, 4 and 6 are timed on whole
 // one-step calls (each writes the outputs, which the call itself then
 // overwrites) and the fastest is kept; k = 1 stays unless another is 3 %
 // faster.  Every launch and its arguments are those of sbi_set_state_all +
@@ -3209,7 +3209,7 @@ int sbi_step_streamed(sbi_ctx* c, const double* eta_in, const double* phi_in, do
     const bool alias = overlaps(eta_in, total, eta_out, total) || overlaps(eta_in, total, phi_out, total) ||
                        overlaps(phi_in, total, eta_out, total) || overlaps(phi_in, total, phi_out, total);
     std::vector<int> ks = {1};
-    for (int k : {2, 3})
+    for (int k : {2, 3, 4, 6})
       if (split_units(units, k).size() > split_units(units, ks.back()).size()) ks.push_back(k);
     if (!c->opt.autotune || n == 0 || alias || ks.size() < 2) {
       if (n > 0 || !c->opt.autotune) c->stream_k = 1;

@@ -102,7 +102,7 @@ def test_untimed_default_and_bad_schedule(sbi):
 
 def test_streamed_split_is_timed_and_gives_the_same_bits(sbi):
     # The streamed step cuts each schedule unit into k member ranges (k = 1, 2,
-    # 3 timed on the first call when the outputs overlap no input); every k
+    # 3, 4, 6 timed on the first call when the outputs overlap no input); every k
     # gives the bits of the three calls.  An in-place call is not timed.
     (e0, p0), _, _ = run(sbi, 0, 3, 0, False)
     eta, phi = initial()
