@@ -378,6 +378,15 @@ int sbi_autotune_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* neede
  * no counterpart (its runs are one problem at a time). */
 int sbi_schedule_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
+/* Test hook for the bounded waits of the staged column pass (col_staging =
+ * 1): with on = 1, each column's mbarrier is armed for 16 bytes more than its
+ * bulk copy delivers, so every wait runs out (after about a second), the
+ * device flag is set and the next sbi_step returns SBI_ETIMEOUT; the copies
+ * themselves complete normally.  on = 0 restores normal operation; the
+ * context stays usable.  Drops the captured step graphs.  The paper has no
+ * counterpart. */
+int sbi_test_stall_staged_copies(sbi_ctx* ctx, int on);
+
 /* Mass and energy of one state without any device allocation.  (This entry
  * point has no counterpart in the paper; it serves callers that may not
  * allocate device memory.)

@@ -894,7 +894,7 @@ k_col(const __grid_constant__ ColParams p) {
     // the column's earlier reads of the staging run (generic proxy) come
     // before the copy that overwrites it (async proxy)
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, kColBytes);
+    mbar_expect_tx(bar, kColBytes + (unsigned)p.stall_tx);
     bulk_copy_g2s(stg, src, kColBytes, bar);
   };
   // live: the column's copies are issued and waited for; a launch that finds

@@ -208,6 +208,7 @@ struct sbi_ctx {
   bool sched_done = false;
   std::string sched_report;
   int stream_k = 0;   // streamed step: each schedule unit cut into stream_k member ranges (0: not chosen)
+  int stall_tx = 0;   // test hook of the staged column pass (sbi_test_stall_staged_copies)
   std::vector<void*> allocs;
   void* tw = nullptr;
   void* wgt = nullptr;  // shared sponge weight (working precision) or null
@@ -529,6 +530,7 @@ struct Planner {
     p.nacc = nacc;
     p.tw = c->tw;
     p.err_flag = c->d_flags + 1;
+    p.stall_tx = c->stall_tx;
     p.staged = (c->opt.col_staging == 1 &&
                 (c->fp64 ? col_stageable<double>(g.ny) : col_stageable<float>(g.ny))) ? 1 : 0;
     const double scale = 1.0 / ((double)g.nx * g.ny);
@@ -3548,6 +3550,14 @@ int sbi_autotune_report(const sbi_ctx* cc, char* buf, size_t cap, size_t* needed
     std::memcpy(buf, out.data(), n);
     buf[n] = '\0';
   }
+  return SBI_OK;
+}
+
+int sbi_test_stall_staged_copies(sbi_ctx* c, int on) {
+  if (!c) return SBI_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  free_graphs(c);   // the captured passes carry the old setting
+  c->stall_tx = on ? 16 : 0;
   return SBI_OK;
 }
 

@@ -127,6 +127,8 @@ struct ColParams {
   ColTerm outs[kMaxColOuts];
   BufRef buf[kMaxColBufs];
   const void* tw;
+  int stall_tx;             // test hook: bytes a staged copy's barrier expects beyond the copy
+                            // (0; > 0 makes every wait run out, to test the timeout path)
 };
 
 // Parameters of one multiplier table (see ColTerm).

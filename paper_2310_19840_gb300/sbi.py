@@ -85,6 +85,7 @@ EXPORTS = {
                                     C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sbi_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sbi_schedule_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "sbi_test_stall_staged_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "sbi_invariants_noalloc": (C.c_int, [C.POINTER(sbi_grid), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
@@ -398,6 +399,11 @@ class Context:
         buf = C.create_string_buffer(need.value + 1)
         self._check(self.lib.sbi_autotune_report(self.ctx, buf, len(buf), C.byref(need)))
         return buf.value.decode()
+
+    def test_stall_staged_copies(self, on=True):
+        """Test hook (sbi_test_stall_staged_copies): make the staged column
+        pass's bounded waits run out, or restore normal operation."""
+        self._check(self.lib.sbi_test_stall_staged_copies(self.ctx, int(on)))
 
     def schedule_report(self):
         """Lines of sbi_schedule_report: the step schedules tried, their times

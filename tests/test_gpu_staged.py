@@ -62,3 +62,33 @@ def test_staged_columns_give_the_same_bits(sbi, prec):
                 assert (" cpb " in ln) and ((ln.split(": cpb ")[1].split("/")[0].endswith("s")) == (ny >= 32)), ln
         if staging == 0 and autotune:
             assert cols and all(" cpb " in ln for ln in cols)
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_context_stays_usable(sbi):
+    # The staged column pass waits for its bulk copies on mbarriers, each wait
+    # bounded by about a second of polling.  With the barriers armed for more
+    # bytes than the copies deliver (the test hook), every wait runs out: the
+    # device flag is set, later launches move no data, and sbi_step returns
+    # SBI_ETIMEOUT after a few seconds instead of hanging.  With the hook off
+    # the same context steps on and matches a fresh context bit for bit.
+    import time
+    spec = [(32, 32, 3.0, 3.0)]
+    eta = W.random_field(32, 32, 5, amplitude=0.03)
+    phi = W.random_field(32, 32, 6, amplitude=0.2)
+    ctx = sbi.Context(spec, 9.81, None, h0=0.8, col_staging=1, autotune=0)
+    ctx.test_stall_staged_copies(True)
+    t0 = time.time()
+    with pytest.raises(sbi.SbiError) as err:
+        ctx.step(0.005, 1)          # the state is zero: what the passes skip stays finite
+    assert err.value.code == sbi.SBI_ETIMEOUT and time.time() - t0 < 60
+    ctx.test_stall_staged_copies(False)
+    ctx.set_state(0, eta, phi)
+    ctx.step(0.005, 2)
+    a = ctx.get_state(0)
+    ref = sbi.Context(spec, 9.81, None, h0=0.8, col_staging=1, autotune=0)
+    ref.set_state(0, eta, phi)
+    ref.step(0.005, 2)
+    b = ref.get_state(0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    ctx.close()
+    ref.close()
