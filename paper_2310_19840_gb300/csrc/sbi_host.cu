@@ -36,6 +36,7 @@
 #include "../../include/sbi.h"
 #include "fft.cuh"
 #include "sbi_internal.h"
+#include "schedule.h"
 
 using namespace sbi;
 
@@ -155,14 +156,11 @@ struct Group {
   size_t mixed_elems() const { return (size_t)ny * W; }
 };
 
-// One branch of a step schedule: the members [m0, m1) (local indices) of one
-// group.  Every pass of a step covers whole rows and columns of each member, so
-// a group's passes restricted to a member range are the same launches over
-// fewer rows or columns, with the same arithmetic per member.
-struct Unit {
-  int group, m0, m1;
-  bool operator==(const Unit& o) const { return group == o.group && m0 == o.m0 && m1 == o.m1; }
-};
+// One branch of a step schedule is a Unit (schedule.h): the members [m0, m1)
+// (local indices) of one group.  Every pass of a step covers whole rows and
+// columns of each member, so a group's passes restricted to a member range are
+// the same launches over fewer rows or columns, with the same arithmetic per
+// member.
 
 struct GraphEntry {
   double dt;
@@ -1870,16 +1868,13 @@ struct Sched {
 // Units with at most cap points each (cap 0: one unit per group); only
 // groups whose passes can all be sliced are split.
 std::vector<Unit> units_for_cap(const sbi_ctx* c, size_t cap, const std::vector<bool>& sliceable) {
-  std::vector<Unit> u;
-  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
-    const Group& g = c->groups[gi];
-    const size_t pts = g.phys_elems() * (size_t)g.n;
-    int k = 1;
-    if (sliceable[gi] && cap > 0) k = (int)std::min<size_t>((size_t)g.n, (pts + cap - 1) / cap);
-    for (int q = 0; q < k; ++q)
-      u.push_back(Unit{(int)gi, (int)((long long)q * g.n / k), (int)((long long)(q + 1) * g.n / k)});
+  std::vector<size_t> pts;
+  std::vector<int> n;
+  for (const Group& g : c->groups) {
+    pts.push_back(g.phys_elems() * (size_t)g.n);
+    n.push_back(g.n);
   }
-  return u;
+  return sbi::units_for_cap(pts, n, cap, sliceable);
 }
 
 // which groups' step passes can all be restricted to member ranges
@@ -3039,18 +3034,6 @@ int sbi_step(sbi_ctx* c, double dt, int n) {
   }
   if (c->opt.check_finite) return check_flags(c, "step");
   return SBI_OK;
-}
-
-// The schedule's units, each cut into k nearly equal member ranges (at most one
-// member each).
-std::vector<Unit> split_units(const std::vector<Unit>& units, int k) {
-  std::vector<Unit> out;
-  for (const Unit& u : units) {
-    const int n = u.m1 - u.m0, kk = std::max(1, std::min(k, n));
-    for (int q = 0; q < kk; ++q)
-      out.push_back(Unit{u.group, u.m0 + (int)((long long)q * n / kk), u.m0 + (int)((long long)(q + 1) * n / kk)});
-  }
-  return out;
 }
 
 // Enqueue the upload, n steps and download of every member's state, one
