@@ -88,7 +88,6 @@ def test_units_tile_every_group_and_respect_the_cap(driver):
         assert len(split) == sum(min(k, b - a) for _, a, b in units)
 
 
-
 def test_known_batches(driver):
     # 64 x 256^2 and 32 x 512^2 (the crossing-sea batch): total/3 keeps the
     # 256^2 group whole and halves the 512^2 group; the streamed step's k = 4
