@@ -370,7 +370,11 @@ int sbi_autotune_report(const sbi_ctx* ctx, char* buf, size_t cap, size_t* neede
  * captures and times each candidate (one branch per group, the serial order,
  * and splits into member ranges of at most total/B points for B = 2, 3, 4, 6)
  * on the real buffers, the state saved before and restored exactly after, and
- * keeps the fastest (the default, B = 3, unless another is 3 % faster).
+ * keeps the fastest (the default, B = 3, unless another is 3 % faster).  The
+ * saved copy (the state, its working copies, the time and the device flags:
+ * about 24 bytes per point in FP32) is a temporary device allocation through
+ * opt.dev_alloc or cudaMalloc, freed before the call returns; when it cannot
+ * be made, nothing is timed and the default is kept.
  * Report lines:
  *   "chosen|default|tried <ms> ms per step: <name> [serial|concurrent] <U> units: <nx>x<ny>[m0:m1] ..."
  * ("default ..." alone, without a time, when nothing was timed).  Empty before
