@@ -193,10 +193,10 @@ struct sbi_ctx {
   int nmembers = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t cap = nullptr;     // internal stream for graph capture
-  std::vector<cudaStream_t> gstreams;  // one capture branch per member group
+  std::vector<cudaStream_t> gstreams;  // one capture branch per unit of the schedule
   std::vector<cudaEvent_t> gevents;    // fork / join events of the branches
-  std::vector<cudaStream_t> pstreams;  // streamed step: one stream per group, by falling priority
-  std::vector<cudaEvent_t> pevents;    // streamed step: start, then one per group
+  std::vector<cudaStream_t> pstreams;  // streamed step: one stream per unit, by falling priority
+  std::vector<cudaEvent_t> pevents;    // streamed step: start, then one per unit
   std::vector<Group> groups;
   std::vector<std::pair<int, int>> where;  // member -> (group, local index)
   // step schedule: the branches of a step graph (concurrent, or one after
